@@ -1,0 +1,188 @@
+/*
+ * align.h -- C ABI of the GB300 CTC forced-alignment library (libalign.so).
+ *
+ * The operation (TorchAudio 2.1 paper, Sec. 4, paragraph "CTC-based forced
+ * alignment"): given the frame log-probabilities log_probs[T][C] of a
+ * CTC-trained model, a transcript targets[L] and the blank id, compute the
+ * frame-level alignment, i.e. the label per frame of the best-scoring CTC path
+ * whose collapse (merge repeats, drop blanks) equals the transcript, and the
+ * per-frame scores along it.
+ *
+ * Method: the Viterbi max-plus recursion over the trellis of S = 2L+1
+ * blank-interleaved states of the CTC work the paper cites, followed by a
+ * backtrack. Conventions fixed by this library where the paper is silent:
+ *   - inside the max, ties keep the earlier candidate in the order
+ *     stay (s), advance (s-1), skip (s-2);
+ *   - a skip enters only an odd (label) state s >= 3 whose label differs from
+ *     the label of state s-2;
+ *   - the final state is S-1 (trailing blank) unless alpha_{T-1}(S-2) is
+ *     strictly greater;
+ *   - scores[t] = log_probs[t][path[t]]; total = alpha_{T-1}(final), which is
+ *     the left-to-right binary32 sum of scores[0..T-1];
+ *   - arithmetic is IEEE binary32, one round-to-nearest add per trellis cell
+ *     after an exact max, no flush-to-zero, so results are deterministic and
+ *     independent of the launch configuration.
+ *
+ * Threading: one align_ctx must be used by one host thread at a time.
+ * Every call returns 0 (ALIGN_OK) or a status code below.
+ */
+#ifndef GB300_ALIGN_H
+#define GB300_ALIGN_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define ALIGN_OK 0
+#define ALIGN_PENDING 1          /* align_poll: request not finished within the timeout */
+#define ALIGN_E_INVAL (-1)       /* NULL pointer, T < 1, C < 2, L < 0, blank not in [0, C), bad config */
+#define ALIGN_E_TARGET (-2)      /* a target outside [0, C) or equal to the blank */
+#define ALIGN_E_INFEASIBLE (-3)  /* T < L + R, R = number of adjacent equal targets */
+#define ALIGN_E_TOO_LARGE (-4)   /* the request cannot fit the memory budget even checkpointed */
+#define ALIGN_E_AGAIN (-5)       /* too many requests in flight (max_inflight) */
+#define ALIGN_E_NOPATH (-6)      /* feasible, but every path scores -inf (log 0 emissions) */
+#define ALIGN_E_TIMEOUT (-7)     /* a device-side wait hit its time limit; the context stays usable */
+#define ALIGN_E_CUDA (-8)        /* a CUDA runtime call failed (align_last_error has the text) */
+#define ALIGN_E_NOTFOUND (-9)    /* unknown request id (never submitted or already polled) */
+#define ALIGN_E_NOMEM (-10)      /* device or pinned allocation failed at create time */
+
+/* ---- configuration ----------------------------------------------------- */
+#define ALIGN_F_BATCHED 0x1u          /* submit only queues; align_flush (or poll) launches the
+                                         queued requests together as one ragged batch */
+#define ALIGN_F_FORCE_CHECKPOINT 0x2u /* always use checkpointed recompute (no full backpointers) */
+#define ALIGN_F_NO_GRAPHS 0x4u        /* batched launches without CUDA-graph capture */
+
+typedef struct align_ctx align_ctx;   /* opaque */
+
+typedef struct {
+    int32_t device;            /* CUDA device ordinal */
+    int32_t max_inflight;      /* requests submitted and not yet polled; 0 -> 8192 */
+    uint64_t bp_budget_bytes;  /* device arena for backpointers and checkpoints; 0 -> 1 GiB.
+                                  Requests are admitted while their footprint fits; a request
+                                  whose full backpointers do not fit runs checkpointed */
+    uint64_t staging_bytes;    /* device staging for align_submit_host inputs/outputs; 0 -> 64 MiB */
+    void *cuda_stream;         /* cudaStream_t all work is ordered after/on; NULL -> own stream */
+    uint32_t flags;            /* ALIGN_F_* */
+    uint32_t wait_limit_ms;    /* limit of every device-side spin wait; 0 -> 2000 */
+} align_config;
+
+/* Outputs, caller-owned. For align_submit they are DEVICE pointers, for
+   align_submit_host HOST pointers. path and scores: T elements; total: 1;
+   states (optional, may be NULL): T trellis state indices. */
+typedef struct {
+    int32_t *path;
+    float *scores;
+    float *total;
+    int32_t *states;
+} align_out;
+
+/* Create a context on cfg->device: allocates the backpointer arena, the staging
+   buffers and descriptor tables once; no later call allocates device memory.
+   cfg may be NULL (all defaults). Errors: ALIGN_E_INVAL, ALIGN_E_NOMEM, ALIGN_E_CUDA. */
+int align_create(align_ctx **out, const align_config *cfg);
+
+/* Finish all work in flight, then free everything the context owns.
+   NULL is accepted (no-op). */
+int align_destroy(align_ctx *ctx);
+
+/* Submit one alignment.
+   log_probs: DEVICE pointer, FP32 [T][C] row-major, contiguous.
+   targets:   HOST pointer, int32 [L]; copied before return (may be freed after).
+   out:       DEVICE pointers (see align_out).
+   Ownership: log_probs and out.* must stay valid and unmodified until
+   align_poll reports the request done (same rule as cudaMemcpyAsync).
+   Validation (ALIGN_E_INVAL / ALIGN_E_TARGET / ALIGN_E_INFEASIBLE /
+   ALIGN_E_TOO_LARGE) happens here on the host; on such an error no request is
+   created. In plain mode the work is launched before return; with
+   ALIGN_F_BATCHED it is queued until align_flush / align_poll. Work is ordered
+   after everything already enqueued on cfg->cuda_stream at submit time.
+   On success *request_id identifies the request for align_poll. */
+int align_submit(align_ctx *ctx, const float *log_probs, int64_t T, int64_t C,
+                 const int32_t *targets, int64_t L, int32_t blank, align_out out,
+                 uint64_t *request_id);
+
+/* Same as align_submit, but log_probs and out.* are HOST pointers. The library
+   copies the emissions host->device and the results device->host itself
+   (asynchronously when the host memory is page-locked). The host buffers must
+   stay valid until align_poll reports the request done. */
+int align_submit_host(align_ctx *ctx, const float *log_probs, int64_t T, int64_t C,
+                      const int32_t *targets, int64_t L, int32_t blank, align_out out,
+                      uint64_t *request_id);
+
+/* Launch every queued request that fits the memory budget (batched mode).
+   Requests that do not fit yet stay queued and are launched by later calls
+   once memory is released. No-op in plain mode when nothing is queued. */
+int align_flush(align_ctx *ctx);
+
+/* Wait up to timeout_ms (0 = just check, < 0 = forever) for a request.
+   Returns ALIGN_OK when it is done, writing its result code to
+   *request_status (ALIGN_OK, ALIGN_E_NOPATH or ALIGN_E_TIMEOUT); the id is
+   then released. Returns ALIGN_PENDING if it is still running, or
+   ALIGN_E_NOTFOUND. Polling also launches queued work. */
+int align_poll(align_ctx *ctx, uint64_t request_id, int32_t timeout_ms, int32_t *request_status);
+
+/* Make `stream` (a cudaStream_t; NULL = the context's stream) wait on the GPU
+   for every batch launched so far, without blocking the host. Batches are not
+   otherwise ordered before later work on the context's stream, so that new
+   batches can overlap running ones; use this to time or order after them. */
+int align_join(align_ctx *ctx, void *stream);
+
+/* Counters of the context since creation (or the last reset). */
+typedef struct {
+    uint64_t kernel_launches;   /* kernels this library launched */
+    uint64_t graph_launches;    /* CUDA graph replays */
+    uint64_t requests_done;
+    uint64_t cells;             /* sum of T * S over finished requests */
+    uint64_t checkpointed;      /* requests that ran with checkpointed recompute */
+    uint64_t bp_bytes_peak;     /* peak arena use */
+} align_stats;
+
+int align_get_stats(align_ctx *ctx, align_stats *out, int32_t reset);
+
+/* Human-readable name of a status code (static string). */
+const char *align_status_string(int32_t code);
+
+/* Text of the last CUDA error seen by this thread (static buffer). */
+const char *align_last_error(void);
+
+/* Tuning of the trellis kernel: states per lane (2, 4, 8 or 16) and the
+   maximum thread-block cluster size for long transcripts (1..16). Values of 0
+   leave the current choice. The defaults come from the built-in autotuned
+   table; align_autotune replaces it with measurements on this GPU. */
+int align_set_tuning(align_ctx *ctx, int32_t states_per_lane, int32_t max_cluster);
+
+/* ---- host-only helpers (no GPU needed) -------------------------------- */
+
+/* Step A1 alone: checks T >= 1, C >= 2, 0 <= blank < C, every target in [0, C)
+   and != blank, and feasibility T >= L + R. Writes R (adjacent equal targets)
+   to *repeats when non-NULL. Returns ALIGN_OK or the error of align_submit. */
+int align_validate(const int32_t *targets, int64_t L, int64_t C, int32_t blank, int64_t T,
+                   int64_t *repeats);
+
+/* Kernel shape and memory footprint align_submit would choose. */
+typedef struct {
+    int32_t states_per_lane;    /* K: trellis states held by one lane */
+    int32_t warps_per_cta;
+    int32_t cluster_ctas;       /* 1: a single CTA */
+    int32_t frames_per_stage;   /* emission rows per shared-memory stage */
+    int32_t checkpointed;       /* 1: backpointers recomputed per segment */
+    int32_t checkpoint_every;   /* frames between alpha checkpoints */
+    int32_t checkpoints;        /* number of segments */
+    int32_t pad;
+    uint64_t backpointer_bytes; /* footprint of full backpointers */
+    uint64_t checkpoint_bytes;  /* footprint of the checkpointed form */
+} align_plan_info;
+
+/* Plan a request of T frames, C classes and L targets for a context with the
+   given budget (0 = default), flags and tuning (0 = defaults).
+   Returns ALIGN_OK, ALIGN_E_INVAL or ALIGN_E_TOO_LARGE. */
+int align_plan(int64_t T, int64_t C, int64_t L, uint64_t bp_budget_bytes, uint32_t flags,
+               int32_t states_per_lane, int32_t max_cluster, align_plan_info *out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GB300_ALIGN_H */

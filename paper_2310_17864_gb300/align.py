@@ -1,0 +1,309 @@
+"""Thin ctypes binding of libalign.so (C ABI in include/align.h).
+
+The functions named like the C entry points (``align_create``, ``align_submit``,
+``align_poll`` ...) only marshal arguments; every step of the alignment runs in
+the CUDA library. There is no CPU fallback: if libalign.so is missing or cannot
+be loaded, ``lib()`` raises.
+
+``Aligner`` is a convenience wrapper that owns a context and output tensors
+(PyTorch is used only for device memory and streams).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libalign.so")
+
+ALIGN_OK = 0
+ALIGN_PENDING = 1
+ALIGN_E_INVAL = -1
+ALIGN_E_TARGET = -2
+ALIGN_E_INFEASIBLE = -3
+ALIGN_E_TOO_LARGE = -4
+ALIGN_E_AGAIN = -5
+ALIGN_E_NOPATH = -6
+ALIGN_E_TIMEOUT = -7
+ALIGN_E_CUDA = -8
+ALIGN_E_NOTFOUND = -9
+ALIGN_E_NOMEM = -10
+
+ALIGN_F_BATCHED = 0x1
+ALIGN_F_FORCE_CHECKPOINT = 0x2
+ALIGN_F_NO_GRAPHS = 0x4
+
+# Every entry point declared in include/align.h.
+EXPORTS = ("align_create", "align_destroy", "align_submit", "align_submit_host", "align_flush",
+           "align_poll", "align_join", "align_get_stats", "align_status_string", "align_last_error",
+           "align_set_tuning", "align_validate", "align_plan")
+
+
+class AlignConfig(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int32), ("max_inflight", ctypes.c_int32),
+                ("bp_budget_bytes", ctypes.c_uint64), ("staging_bytes", ctypes.c_uint64),
+                ("cuda_stream", ctypes.c_void_p), ("flags", ctypes.c_uint32),
+                ("wait_limit_ms", ctypes.c_uint32)]
+
+
+class AlignOut(ctypes.Structure):
+    _fields_ = [("path", ctypes.c_void_p), ("scores", ctypes.c_void_p), ("total", ctypes.c_void_p),
+                ("states", ctypes.c_void_p)]
+
+
+class AlignStats(ctypes.Structure):
+    _fields_ = [("kernel_launches", ctypes.c_uint64), ("graph_launches", ctypes.c_uint64),
+                ("requests_done", ctypes.c_uint64), ("cells", ctypes.c_uint64),
+                ("checkpointed", ctypes.c_uint64), ("bp_bytes_peak", ctypes.c_uint64)]
+
+
+class AlignPlanInfo(ctypes.Structure):
+    _fields_ = [("states_per_lane", ctypes.c_int32), ("warps_per_cta", ctypes.c_int32),
+                ("cluster_ctas", ctypes.c_int32), ("frames_per_stage", ctypes.c_int32),
+                ("checkpointed", ctypes.c_int32), ("checkpoint_every", ctypes.c_int32),
+                ("checkpoints", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("backpointer_bytes", ctypes.c_uint64), ("checkpoint_bytes", ctypes.c_uint64)]
+
+
+class AlignError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        self.code = code
+        msg = status_string(code)
+        if code == ALIGN_E_CUDA:
+            msg += ": " + last_error()
+        super().__init__(f"{what}: {msg}" if what else msg)
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libalign.so (built by paper_2310_17864_gb300.build); raise if absent."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libalign.so not built at {LIB_PATH}; run paper_2310_17864_gb300/build.py")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i64, i32, u32, u64 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint32, ctypes.c_uint64
+        L.align_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(AlignConfig)]
+        L.align_destroy.argtypes = [vp]
+        L.align_submit.argtypes = [vp, vp, i64, i64, vp, i64, i32, AlignOut, ctypes.POINTER(u64)]
+        L.align_submit_host.argtypes = [vp, vp, i64, i64, vp, i64, i32, AlignOut, ctypes.POINTER(u64)]
+        L.align_flush.argtypes = [vp]
+        L.align_poll.argtypes = [vp, u64, i32, ctypes.POINTER(i32)]
+        L.align_join.argtypes = [vp, vp]
+        L.align_get_stats.argtypes = [vp, ctypes.POINTER(AlignStats), i32]
+        L.align_status_string.argtypes = [i32]
+        L.align_status_string.restype = ctypes.c_char_p
+        L.align_last_error.argtypes = []
+        L.align_last_error.restype = ctypes.c_char_p
+        L.align_set_tuning.argtypes = [vp, i32, i32]
+        L.align_validate.argtypes = [vp, i64, i64, i32, i64, ctypes.POINTER(i64)]
+        L.align_plan.argtypes = [i64, i64, i64, u64, u32, i32, i32, ctypes.POINTER(AlignPlanInfo)]
+        for name in EXPORTS:
+            fn = getattr(L, name)
+            if fn.restype is ctypes.c_int or fn.restype is None:
+                fn.restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def status_string(code: int) -> str:
+    return lib().align_status_string(int(code)).decode()
+
+
+def last_error() -> str:
+    return lib().align_last_error().decode()
+
+
+def _check(rc: int, what: str) -> int:
+    if rc < 0:
+        raise AlignError(rc, what)
+    return rc
+
+
+def _i32(targets) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(targets, dtype=np.int32).reshape(-1))
+
+
+# --------------------------------------------------------- same-named calls --
+
+def align_create(cfg: AlignConfig | None = None) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    _check(lib().align_create(ctypes.byref(h), ctypes.byref(cfg) if cfg is not None else None), "align_create")
+    return h
+
+
+def align_destroy(ctx) -> None:
+    _check(lib().align_destroy(ctx), "align_destroy")
+
+
+def align_submit(ctx, log_probs_ptr: int, T: int, C: int, targets, blank: int, out: AlignOut) -> int:
+    tg = _i32(targets)
+    rid = ctypes.c_uint64()
+    _check(lib().align_submit(ctx, ctypes.c_void_p(log_probs_ptr), T, C, tg.ctypes.data_as(ctypes.c_void_p),
+                              tg.size, blank, out, ctypes.byref(rid)), "align_submit")
+    return rid.value
+
+
+def align_submit_host(ctx, log_probs_ptr: int, T: int, C: int, targets, blank: int, out: AlignOut) -> int:
+    tg = _i32(targets)
+    rid = ctypes.c_uint64()
+    _check(lib().align_submit_host(ctx, ctypes.c_void_p(log_probs_ptr), T, C, tg.ctypes.data_as(ctypes.c_void_p),
+                                   tg.size, blank, out, ctypes.byref(rid)), "align_submit_host")
+    return rid.value
+
+
+def align_flush(ctx) -> None:
+    _check(lib().align_flush(ctx), "align_flush")
+
+
+def align_poll(ctx, request_id: int, timeout_ms: int = -1) -> tuple[int, int]:
+    """Returns (ALIGN_OK or ALIGN_PENDING, request status)."""
+    st = ctypes.c_int32(ALIGN_PENDING)
+    rc = _check(lib().align_poll(ctx, request_id, timeout_ms, ctypes.byref(st)), "align_poll")
+    return rc, st.value
+
+
+def align_join(ctx, stream_ptr: int | None = None) -> None:
+    _check(lib().align_join(ctx, ctypes.c_void_p(stream_ptr) if stream_ptr else None), "align_join")
+
+
+def align_get_stats(ctx, reset: bool = False) -> dict:
+    s = AlignStats()
+    _check(lib().align_get_stats(ctx, ctypes.byref(s), int(reset)), "align_get_stats")
+    return {k: getattr(s, k) for k, _ in AlignStats._fields_}
+
+
+def align_set_tuning(ctx, states_per_lane: int = 0, max_cluster: int = 0) -> None:
+    _check(lib().align_set_tuning(ctx, states_per_lane, max_cluster), "align_set_tuning")
+
+
+def align_validate(targets, C: int, blank: int, T: int) -> tuple[int, int]:
+    tg = _i32(targets)
+    rep = ctypes.c_int64(0)
+    rc = lib().align_validate(tg.ctypes.data_as(ctypes.c_void_p), tg.size, C, blank, T, ctypes.byref(rep))
+    return rc, rep.value
+
+
+def align_plan(T: int, C: int, L: int, budget: int = 0, flags: int = 0, states_per_lane: int = 0,
+               max_cluster: int = 0) -> dict:
+    info = AlignPlanInfo()
+    _check(lib().align_plan(T, C, L, budget, flags, states_per_lane, max_cluster, ctypes.byref(info)),
+           "align_plan")
+    return {k: getattr(info, k) for k, _ in AlignPlanInfo._fields_ if k != "pad"}
+
+
+# ------------------------------------------------------------ convenience --
+
+@dataclass
+class Result:
+    request_id: int
+    path: object      # torch tensor (device or host)
+    scores: object
+    total: object
+    states: object
+    status: int = ALIGN_PENDING
+
+
+class Aligner:
+    """Owns one context. Device submits take CUDA tensors and return CUDA tensors."""
+
+    def __init__(self, device: int = 0, batched: bool = False, bp_budget_bytes: int = 0,
+                 staging_bytes: int = 0, stream=None, force_checkpoint: bool = False,
+                 wait_limit_ms: int = 0, max_inflight: int = 0, graphs: bool = True):
+        import torch
+        self.torch = torch
+        self.device = device
+        flags = (ALIGN_F_BATCHED if batched else 0) | (ALIGN_F_FORCE_CHECKPOINT if force_checkpoint else 0)
+        flags |= 0 if graphs else ALIGN_F_NO_GRAPHS
+        cfg = AlignConfig(device=device, max_inflight=max_inflight, bp_budget_bytes=bp_budget_bytes,
+                          staging_bytes=staging_bytes,
+                          cuda_stream=(stream.cuda_stream if stream is not None else None), flags=flags,
+                          wait_limit_ms=wait_limit_ms)
+        self.ctx = align_create(cfg)
+        self._live: dict[int, tuple] = {}
+
+    def close(self) -> None:
+        if self.ctx is not None:
+            align_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, log_probs, targets, blank: int = 0, want_states: bool = False, out=None) -> Result:
+        torch = self.torch
+        if not (log_probs.is_cuda and log_probs.dtype == torch.float32 and log_probs.dim() == 2
+                and log_probs.is_contiguous()):
+            raise ValueError("log_probs must be a contiguous CUDA float32 [T, C] tensor")
+        T, C = log_probs.shape
+        dev = log_probs.device
+        if out is None:
+            path = torch.empty(T, dtype=torch.int32, device=dev)
+            scores = torch.empty(T, dtype=torch.float32, device=dev)
+            total = torch.empty(1, dtype=torch.float32, device=dev)
+            states = torch.empty(T, dtype=torch.int32, device=dev) if want_states else None
+        else:
+            path, scores, total, states = out
+        o = AlignOut(path.data_ptr(), scores.data_ptr(), total.data_ptr(),
+                     states.data_ptr() if states is not None else None)
+        rid = align_submit(self.ctx, log_probs.data_ptr(), T, C, targets, blank, o)
+        res = Result(rid, path, scores, total, states)
+        self._live[rid] = (log_probs, res)
+        return res
+
+    def submit_host(self, log_probs, targets, blank: int = 0, want_states: bool = False, out=None) -> Result:
+        """log_probs: CPU float32 [T, C] tensor (pinned for asynchronous copies)."""
+        torch = self.torch
+        if log_probs.is_cuda or log_probs.dtype != torch.float32 or not log_probs.is_contiguous():
+            raise ValueError("log_probs must be a contiguous CPU float32 [T, C] tensor")
+        T, C = log_probs.shape
+        if out is None:
+            pin = log_probs.is_pinned()
+            path = torch.empty(T, dtype=torch.int32, pin_memory=pin)
+            scores = torch.empty(T, dtype=torch.float32, pin_memory=pin)
+            total = torch.empty(1, dtype=torch.float32, pin_memory=pin)
+            states = torch.empty(T, dtype=torch.int32, pin_memory=pin) if want_states else None
+        else:
+            path, scores, total, states = out
+        o = AlignOut(path.data_ptr(), scores.data_ptr(), total.data_ptr(),
+                     states.data_ptr() if states is not None else None)
+        rid = align_submit_host(self.ctx, log_probs.data_ptr(), T, C, targets, blank, o)
+        res = Result(rid, path, scores, total, states)
+        self._live[rid] = (log_probs, res)
+        return res
+
+    def flush(self) -> None:
+        align_flush(self.ctx)
+
+    def poll(self, res: Result, timeout_ms: int = -1) -> bool:
+        rc, st = align_poll(self.ctx, res.request_id, timeout_ms)
+        if rc == ALIGN_OK:
+            res.status = st
+            self._live.pop(res.request_id, None)
+            return True
+        return False
+
+    def align(self, log_probs, targets, blank: int = 0, want_states: bool = False) -> Result:
+        res = self.submit(log_probs, targets, blank, want_states)
+        self.flush()
+        self.poll(res)
+        return res
+
+    def join(self, stream=None) -> None:
+        """Make a torch CUDA stream (default: current) wait for every launched batch."""
+        st = stream if stream is not None else self.torch.cuda.current_stream(self.device)
+        align_join(self.ctx, st.cuda_stream)
+
+    def stats(self, reset: bool = False) -> dict:
+        return align_get_stats(self.ctx, reset)
+
+    def set_tuning(self, states_per_lane: int = 0, max_cluster: int = 0) -> None:
+        align_set_tuning(self.ctx, states_per_lane, max_cluster)

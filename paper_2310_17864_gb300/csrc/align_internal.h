@@ -1,0 +1,46 @@
+// Host-only planning and validation shared by the runtime and the C ABI.
+#pragma once
+#include <cstdint>
+
+#include "trellis.cuh"
+
+namespace gb300_align {
+
+// Kernel-shape choices (replaced by measurements through align_set_tuning).
+struct TuneTable {
+  int K = 4;             // states per lane for single-CTA teams
+  int max_warps = 32;    // warps per CTA
+  int max_cluster = 16;  // CTAs per cluster for long transcripts
+};
+TuneTable default_tune_table();
+
+struct Plan {
+  LaunchShape shape{};
+  int frames_per_stage = 16;
+  uint64_t bp_bytes = 0;      // full backpointers: warps * (T-1) * words * 4
+  bool checkpointed = false;
+  int ck_every = 0;           // frames between alpha checkpoints
+  int nck = 0;                // number of checkpoints (segments)
+  int ck_stride = 0;          // floats per checkpoint row
+  uint64_t ckpt_bytes = 0;    // nck * ck_stride * 4
+  uint64_t seg_bp_bytes = 0;  // backpointers of one segment
+};
+
+// Step A1: 0, ALIGN_E_INVAL, ALIGN_E_TARGET or ALIGN_E_INFEASIBLE; *repeats = R.
+int validate_request(const int32_t* targets, int64_t L, int64_t C, int32_t blank, int64_t T, int64_t* repeats);
+
+// Shape and footprint of a request; ALIGN_E_TOO_LARGE if it cannot run within budget.
+int make_plan(const TuneTable& tune, int64_t T, int64_t C, int64_t L, uint64_t budget, bool force_checkpoint,
+              Plan* out);
+
+// Device staging of a host-I/O request: emissions, then outputs.
+struct HostStage {
+  uint64_t lp, path, scores, states, total, bytes;
+};
+HostStage host_stage_layout(int64_t T, int64_t C);
+inline uint64_t host_stage_bytes(int64_t T, int64_t C) { return host_stage_layout(T, C).bytes; }
+
+// Emission rows may be staged with bulk copies (16-byte aligned rows).
+bool rows_bulk_ok(const float* lp, int64_t C);
+
+}  // namespace gb300_align

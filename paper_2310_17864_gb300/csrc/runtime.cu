@@ -1,0 +1,791 @@
+// Host runtime behind the C ABI in include/align.h.
+//
+// Responsibilities:
+//   * validation of a request (step A1 of the hot path: targets in range,
+//     no blank target, T >= L + R), on the host, O(L);
+//   * planning: kernel shape (states per lane K, warps per CTA, cluster size)
+//     from the number of trellis states S = 2L+1, and the memory footprint of
+//     full backpointers or of checkpointed recompute;
+//   * memory: one device arena for backpointers / checkpoints (the budget),
+//     one for per-request metadata, one for host-I/O staging, and a pinned host
+//     arena for descriptor uploads -- all allocated once in align_create;
+//   * scheduling: requests are queued, admitted while their footprint fits,
+//     grouped by kernel shape and launched as ragged batches (one launch per
+//     shape group, longest first) on a pool of streams so batches overlap;
+//     completion is tracked by events and released memory admits more work
+//     (continuous batching);
+//   * checkpointed recompute for requests whose backpointers do not fit.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/align.h"
+#include "align_internal.h"
+#include "trellis.cuh"
+
+using namespace gb300_align;
+
+namespace {
+
+thread_local char g_last_error[512] = "";
+
+void set_error(const char* what, cudaError_t e) {
+  std::snprintf(g_last_error, sizeof(g_last_error), "%s: %s (%d)", what, cudaGetErrorString(e),
+                static_cast<int>(e));
+}
+
+#define CU(call)                         \
+  do {                                   \
+    cudaError_t e_ = (call);             \
+    if (e_ != cudaSuccess) {             \
+      set_error(#call, e_);              \
+      return ALIGN_E_CUDA;               \
+    }                                    \
+  } while (0)
+
+constexpr uint64_t kAlign = 256;
+inline uint64_t round_up(uint64_t v, uint64_t a) { return (v + a - 1) / a * a; }
+
+// First-fit allocator over [0, cap) with coalescing frees.
+class Arena {
+ public:
+  void init(uint64_t cap) {
+    cap_ = cap;
+    free_.clear();
+    if (cap) free_[0] = cap;
+    used_ = peak_ = 0;
+  }
+  bool alloc(uint64_t bytes, uint64_t* off) {
+    bytes = round_up(std::max<uint64_t>(bytes, 1), kAlign);
+    for (auto it = free_.begin(); it != free_.end(); ++it) {
+      if (it->second >= bytes) {
+        *off = it->first;
+        const uint64_t rest = it->second - bytes;
+        const uint64_t start = it->first + bytes;
+        free_.erase(it);
+        if (rest) free_[start] = rest;
+        used_ += bytes;
+        peak_ = std::max(peak_, used_);
+        return true;
+      }
+    }
+    return false;
+  }
+  void release(uint64_t off, uint64_t bytes) {
+    bytes = round_up(std::max<uint64_t>(bytes, 1), kAlign);
+    used_ -= bytes;
+    auto it = free_.emplace(off, bytes).first;
+    auto nx = std::next(it);
+    if (nx != free_.end() && it->first + it->second == nx->first) {
+      it->second += nx->second;
+      free_.erase(nx);
+    }
+    if (it != free_.begin()) {
+      auto pv = std::prev(it);
+      if (pv->first + pv->second == it->first) {
+        pv->second += it->second;
+        free_.erase(it);
+      }
+    }
+  }
+  uint64_t cap() const { return cap_; }
+  uint64_t used() const { return used_; }
+  uint64_t peak() const { return peak_; }
+  void reset_peak() { peak_ = used_; }
+
+ private:
+  uint64_t cap_ = 0, used_ = 0, peak_ = 0;
+  std::map<uint64_t, uint64_t> free_;
+};
+
+struct Alloc {
+  uint64_t off = 0, bytes = 0;
+  bool live = false;
+};
+
+enum class ReqState { Queued, Launched, Done };
+
+struct Request {
+  uint64_t id = 0;
+  ReqState state = ReqState::Queued;
+  const float* lp = nullptr;  // device emissions (or host, when host_io)
+  bool host_io = false;
+  align_out out{};            // caller outputs (device or host)
+  int64_t T = 0, C = 0, L = 0;
+  int32_t blank = 0;
+  std::vector<int32_t> targets;
+  Plan plan{};
+  Alloc bp;                   // backpointers or checkpoints + segment buffer
+  Alloc stage;                // host-I/O device staging
+  int batch = -1;
+  int meta_index = -1;        // index of its metadata block in the batch
+  int32_t status = ALIGN_PENDING;
+};
+
+struct Batch {
+  int id = 0;
+  cudaEvent_t done = nullptr;
+  Alloc meta;      // device: descriptors + per-request metadata + targets
+  Alloc pinned;    // host pinned: upload image + status download
+  std::vector<uint64_t> reqs;
+  int32_t* h_status = nullptr;  // pinned, one per request
+  bool finished = false;
+};
+
+}  // namespace
+
+struct align_ctx {
+  int device = 0;
+  cudaStream_t main = nullptr;
+  bool own_main = false;
+  std::vector<cudaStream_t> workers;
+  std::vector<cudaEvent_t> fork_events;
+  int next_worker = 0;
+  uint32_t flags = 0;
+  uint64_t wait_limit_ns = 2000000000ull;
+  int max_inflight = 8192;
+
+  char* d_bp = nullptr;
+  Arena bp_arena;
+  char* d_meta = nullptr;
+  Arena meta_arena;
+  char* d_stage = nullptr;
+  Arena stage_arena;
+  char* h_pinned = nullptr;
+  Arena pinned_arena;
+
+  std::unordered_map<uint64_t, Request> reqs;
+  std::deque<uint64_t> queued;
+  std::map<int, Batch> batches;
+  uint64_t next_id = 1;
+  int next_batch = 1;
+
+  TuneTable tune;
+  int num_sms = 0;
+  int smem_optin = 0;
+  align_stats stats{};
+};
+
+namespace {
+
+uint64_t inflight_count(const align_ctx* ctx) { return ctx->reqs.size(); }
+
+// Metadata block per request in device memory: status, state_io, final2[2].
+struct MetaBlock {
+  int32_t status;
+  int32_t state_io;
+  float final2[2];
+};
+static_assert(sizeof(MetaBlock) == 16, "meta");
+
+int finish_batch(align_ctx* ctx, Batch& b) {
+  for (size_t i = 0; i < b.reqs.size(); ++i) {
+    auto it = ctx->reqs.find(b.reqs[i]);
+    if (it == ctx->reqs.end()) continue;
+    Request& r = it->second;
+    r.state = ReqState::Done;
+    r.status = b.h_status[i];
+    if (r.status == ALIGN_PENDING) r.status = ALIGN_E_TIMEOUT;
+    if (r.bp.live) ctx->bp_arena.release(r.bp.off, r.bp.bytes), r.bp.live = false;
+    if (r.stage.live) ctx->stage_arena.release(r.stage.off, r.stage.bytes), r.stage.live = false;
+    ctx->stats.requests_done++;
+    ctx->stats.cells += static_cast<uint64_t>(r.T) * static_cast<uint64_t>(2 * r.L + 1);
+    if (r.plan.checkpointed) ctx->stats.checkpointed++;
+  }
+  if (b.meta.live) ctx->meta_arena.release(b.meta.off, b.meta.bytes), b.meta.live = false;
+  if (b.pinned.live) ctx->pinned_arena.release(b.pinned.off, b.pinned.bytes), b.pinned.live = false;
+  b.finished = true;
+  return ALIGN_OK;
+}
+
+// Retire finished batches; returns ALIGN_E_CUDA on a failed query.
+int reap(align_ctx* ctx) {
+  for (auto it = ctx->batches.begin(); it != ctx->batches.end();) {
+    Batch& b = it->second;
+    cudaError_t q = cudaEventQuery(b.done);
+    if (q == cudaSuccess) {
+      finish_batch(ctx, b);
+      cudaEventDestroy(b.done);
+      it = ctx->batches.erase(it);
+    } else if (q == cudaErrorNotReady) {
+      ++it;
+    } else {
+      set_error("cudaEventQuery", q);
+      return ALIGN_E_CUDA;
+    }
+  }
+  return ALIGN_OK;
+}
+
+uint64_t request_bp_bytes(const Plan& p) { return p.checkpointed ? p.ckpt_bytes + p.seg_bp_bytes : p.bp_bytes; }
+
+// Launch as many queued requests as fit, as one batch. Returns ALIGN_OK even
+// if nothing could be launched (they stay queued).
+int launch_queued(align_ctx* ctx) {
+  if (ctx->queued.empty()) return ALIGN_OK;
+  std::vector<Request*> take;
+  std::deque<uint64_t> keep;
+  uint64_t meta_est = 0;  // descriptor + metadata + targets bytes of the batch
+  const uint64_t meta_room = std::min(ctx->meta_arena.cap() - ctx->meta_arena.used(),
+                                      ctx->pinned_arena.cap() - ctx->pinned_arena.used());
+  while (!ctx->queued.empty()) {
+    const uint64_t id = ctx->queued.front();
+    Request& r = ctx->reqs.at(id);
+    const uint64_t m = (1 + static_cast<uint64_t>(r.plan.nck)) * sizeof(FwdJob) + 64 +
+                       static_cast<uint64_t>(r.L) * 4 + 16;
+    if (meta_est + m + 4 * kAlign > meta_room) break;  // the rest waits for the next batch
+    ctx->queued.pop_front();
+    // Admission: backpointer / checkpoint footprint, plus staging for host I/O.
+    Plan& p = r.plan;
+    uint64_t need = request_bp_bytes(p);
+    if (!p.checkpointed && !ctx->bp_arena.alloc(need, &r.bp.off)) {
+      // Full backpointers do not fit now: fall back to checkpointed recompute
+      // if that fits, otherwise wait for memory to be released.
+      if (p.ckpt_bytes + p.seg_bp_bytes <= ctx->bp_arena.cap() - ctx->bp_arena.used() &&
+          ctx->bp_arena.alloc(p.ckpt_bytes + p.seg_bp_bytes, &r.bp.off)) {
+        p.checkpointed = true;
+        need = p.ckpt_bytes + p.seg_bp_bytes;
+      } else {
+        keep.push_back(id);
+        continue;
+      }
+    } else if (p.checkpointed && !ctx->bp_arena.alloc(need, &r.bp.off)) {
+      keep.push_back(id);
+      continue;
+    }
+    r.bp.bytes = need;
+    r.bp.live = true;
+    meta_est += m;
+    if (r.host_io) {
+      const uint64_t sb = host_stage_bytes(r.T, r.C);
+      if (!ctx->stage_arena.alloc(sb, &r.stage.off)) {
+        ctx->bp_arena.release(r.bp.off, r.bp.bytes);
+        r.bp.live = false;
+        keep.push_back(id);
+        continue;
+      }
+      r.stage.bytes = sb;
+      r.stage.live = true;
+    }
+    take.push_back(&r);
+  }
+  for (auto it = keep.rbegin(); it != keep.rend(); ++it) ctx->queued.push_front(*it);
+  if (take.empty()) return ALIGN_OK;
+  ctx->stats.bp_bytes_peak = std::max(ctx->stats.bp_bytes_peak, ctx->bp_arena.peak());
+
+  // Longest first (trellis cells), then group by kernel shape.
+  std::stable_sort(take.begin(), take.end(), [](const Request* a, const Request* b) {
+    return a->T * (2 * a->L + 1) > b->T * (2 * b->L + 1);
+  });
+
+  // Descriptor image: full-mode jobs grouped by shape; checkpointed requests
+  // get 1 + nck descriptors each.
+  std::map<std::tuple<int, int, int, int>, std::vector<int>> groups;  // (K, warps, ncta, F) -> req idx
+  size_t njobs = 0;
+  for (size_t i = 0; i < take.size(); ++i) {
+    const Plan& p = take[i]->plan;
+    if (p.checkpointed) {
+      njobs += 1 + static_cast<size_t>(p.nck);
+    } else {
+      groups[{p.shape.K, p.shape.warps, p.shape.ncta, p.frames_per_stage}].push_back(static_cast<int>(i));
+      njobs += 1;
+    }
+  }
+  uint64_t tgt_words = 0;
+  for (auto* r : take) tgt_words += round_up(static_cast<uint64_t>(std::max<int64_t>(r->L, 1)), 4);
+  const uint64_t off_jobs = 0;
+  const uint64_t off_metas = round_up(njobs * sizeof(FwdJob), kAlign);
+  const uint64_t off_tgts = round_up(off_metas + take.size() * sizeof(MetaBlock), kAlign);
+  const uint64_t up_bytes = round_up(off_tgts + tgt_words * 4, kAlign);
+  const uint64_t off_status = up_bytes;  // pinned only: status download
+  const uint64_t pin_bytes = up_bytes + round_up(take.size() * 4, kAlign);
+
+  Batch b;
+  b.id = ctx->next_batch++;
+  auto unwind = [&]() {
+    for (auto* r : take) {
+      if (r->bp.live) ctx->bp_arena.release(r->bp.off, r->bp.bytes), r->bp.live = false;
+      if (r->stage.live) ctx->stage_arena.release(r->stage.off, r->stage.bytes), r->stage.live = false;
+      ctx->queued.push_front(r->id);
+    }
+  };
+  if (!ctx->meta_arena.alloc(up_bytes, &b.meta.off)) {
+    unwind();
+    return ALIGN_OK;  // retried after other batches release metadata
+  }
+  b.meta.bytes = up_bytes;
+  b.meta.live = true;
+  if (!ctx->pinned_arena.alloc(pin_bytes, &b.pinned.off)) {
+    ctx->meta_arena.release(b.meta.off, b.meta.bytes);
+    unwind();
+    return ALIGN_OK;
+  }
+  b.pinned.bytes = pin_bytes;
+  b.pinned.live = true;
+
+  char* h = ctx->h_pinned + b.pinned.off;
+  char* d = ctx->d_meta + b.meta.off;
+  FwdJob* hjobs = reinterpret_cast<FwdJob*>(h + off_jobs);
+  MetaBlock* hmeta = reinterpret_cast<MetaBlock*>(h + off_metas);
+  int32_t* htgt = reinterpret_cast<int32_t*>(h + off_tgts);
+  const FwdJob* djobs = reinterpret_cast<const FwdJob*>(d + off_jobs);
+  MetaBlock* dmeta = reinterpret_cast<MetaBlock*>(d + off_metas);
+  const int32_t* dtgt = reinterpret_cast<const int32_t*>(d + off_tgts);
+  b.h_status = reinterpret_cast<int32_t*>(h + off_status);
+
+  // Per-request metadata, targets and device views of inputs / outputs.
+  std::vector<const int32_t*> req_tgt(take.size());
+  std::vector<const float*> req_lp(take.size());
+  std::vector<align_out> req_out(take.size());
+  uint64_t tw = 0;
+  for (size_t i = 0; i < take.size(); ++i) {
+    Request& r = *take[i];
+    r.state = ReqState::Launched;
+    r.batch = b.id;
+    r.meta_index = static_cast<int>(i);
+    b.reqs.push_back(r.id);
+    hmeta[i].status = ALIGN_PENDING;
+    hmeta[i].state_io = 0;
+    hmeta[i].final2[0] = hmeta[i].final2[1] = -INFINITY;
+    b.h_status[i] = ALIGN_PENDING;
+    if (r.L) std::memcpy(htgt + tw, r.targets.data(), static_cast<size_t>(r.L) * 4);
+    req_tgt[i] = dtgt + tw;
+    tw += round_up(static_cast<uint64_t>(std::max<int64_t>(r.L, 1)), 4);
+    if (r.host_io) {
+      char* sbase = ctx->d_stage + r.stage.off;
+      HostStage hs = host_stage_layout(r.T, r.C);
+      req_lp[i] = reinterpret_cast<const float*>(sbase + hs.lp);
+      req_out[i].path = reinterpret_cast<int32_t*>(sbase + hs.path);
+      req_out[i].scores = reinterpret_cast<float*>(sbase + hs.scores);
+      req_out[i].total = reinterpret_cast<float*>(sbase + hs.total);
+      req_out[i].states = r.out.states ? reinterpret_cast<int32_t*>(sbase + hs.states) : nullptr;
+    } else {
+      req_lp[i] = r.lp;
+      req_out[i] = r.out;
+    }
+  }
+
+  auto base_job = [&](size_t i) {
+    const Request& r = *take[i];
+    FwdJob j{};
+    j.lp = req_lp[i];
+    j.tgt = req_tgt[i];
+    j.status = &dmeta[i].status;
+    j.state_io = &dmeta[i].state_io;
+    j.final2 = dmeta[i].final2;
+    j.path = req_out[i].path;
+    j.scores = req_out[i].scores;
+    j.total = req_out[i].total;
+    j.states = req_out[i].states;
+    j.T = static_cast<int32_t>(r.T);
+    j.C = static_cast<int32_t>(r.C);
+    j.blank = r.blank;
+    j.L = static_cast<int32_t>(r.L);
+    j.S = static_cast<int32_t>(2 * r.L + 1);
+    j.flags = rows_bulk_ok(j.lp, r.C) ? kJobBulkRows : 0u;
+    return j;
+  };
+
+  // Fill descriptors: shape groups first (contiguous ranges), then the
+  // checkpointed sequences.
+  struct GroupLaunch {
+    LaunchShape shape;
+    int F;
+    size_t first, count;
+  };
+  std::vector<GroupLaunch> glaunch;
+  struct CkLaunch {
+    size_t req, first;
+  };
+  std::vector<CkLaunch> cklaunch;
+  size_t jn = 0;
+  for (auto& kv : groups) {
+    GroupLaunch gl{};
+    gl.shape = LaunchShape{std::get<0>(kv.first), std::get<1>(kv.first), std::get<2>(kv.first)};
+    gl.F = std::get<3>(kv.first);
+    gl.first = jn;
+    gl.count = kv.second.size();
+    for (int i : kv.second) {
+      const Request& r = *take[static_cast<size_t>(i)];
+      FwdJob j = base_job(static_cast<size_t>(i));
+      j.bp = reinterpret_cast<uint32_t*>(ctx->d_bp + r.bp.off);
+      j.t_begin = 0;
+      j.t_end = j.T;
+      j.bp_rows = std::max(j.T - 1, 0);
+      j.flags |= kJobWriteFinal | kJobChase;
+      hjobs[jn++] = j;
+    }
+    glaunch.push_back(gl);
+  }
+  for (size_t i = 0; i < take.size(); ++i) {
+    const Request& r = *take[i];
+    const Plan& p = r.plan;
+    if (!p.checkpointed) continue;
+    CkLaunch cl{i, jn};
+    float* ck = reinterpret_cast<float*>(ctx->d_bp + r.bp.off);
+    uint32_t* seg = reinterpret_cast<uint32_t*>(ctx->d_bp + r.bp.off + p.ckpt_bytes);
+    FwdJob j = base_job(i);  // pass 1: checkpoints every Kc frames, final state, no backpointers
+    j.t_begin = 0;
+    j.t_end = j.T;
+    j.ckpt = ck;
+    j.ck_every = p.ck_every;
+    j.ck_stride = p.ck_stride;
+    j.flags |= kJobWriteFinal;
+    hjobs[jn++] = j;
+    for (int c = p.nck - 1; c >= 0; --c) {  // pass 2: segments, last first
+      FwdJob s = base_job(i);
+      const int t0 = c * p.ck_every;
+      const int e = std::min(t0 + p.ck_every, s.T - 1);
+      s.t_begin = t0;
+      s.t_end = e + 1;
+      s.alpha_in = ck + static_cast<size_t>(c) * p.ck_stride;
+      s.final2 = nullptr;
+      s.bp = seg;
+      s.bp_rows = e - t0;
+      s.flags |= kJobChase;
+      hjobs[jn++] = s;
+    }
+    cklaunch.push_back(cl);
+  }
+
+  // Streams: the batch forks from the main stream; each group / checkpointed
+  // sequence runs on its own worker stream; everything joins on the first.
+  cudaEvent_t fork = ctx->fork_events[static_cast<size_t>(b.id) % ctx->fork_events.size()];
+  CU(cudaEventRecord(fork, ctx->main));
+  const size_t nlanes = std::max<size_t>(1, glaunch.size() + cklaunch.size());
+  std::vector<cudaStream_t> used;
+  for (size_t k = 0; k < nlanes; ++k) {
+    cudaStream_t s = ctx->workers[static_cast<size_t>(ctx->next_worker++) % ctx->workers.size()];
+    if (std::find(used.begin(), used.end(), s) == used.end()) used.push_back(s);
+  }
+  cudaStream_t s0 = used[0];
+  for (cudaStream_t s : used) CU(cudaStreamWaitEvent(s, fork, 0));
+  CU(cudaMemcpyAsync(d, h, up_bytes, cudaMemcpyHostToDevice, s0));
+  for (size_t i = 0; i < take.size(); ++i) {
+    Request& r = *take[i];
+    if (r.host_io) {
+      CU(cudaMemcpyAsync(const_cast<float*>(req_lp[i]), r.lp, static_cast<size_t>(r.T * r.C) * 4,
+                         cudaMemcpyHostToDevice, s0));
+    }
+  }
+  cudaEvent_t ready;
+  CU(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
+  CU(cudaEventRecord(ready, s0));
+  size_t lane_i = 0;
+  for (const GroupLaunch& gl : glaunch) {
+    cudaStream_t s = used[lane_i++ % used.size()];
+    if (s != s0) CU(cudaStreamWaitEvent(s, ready, 0));
+    const int C = hjobs[gl.first].C;
+    const FwdParams P = plan_params(gl.shape, C, gl.F, ctx->wait_limit_ns);
+    cudaError_t e = static_cast<cudaError_t>(launch_trellis(gl.shape, P, djobs + gl.first, static_cast<int>(gl.count), s));
+    if (e != cudaSuccess) {
+      set_error("launch_trellis", e);
+      return ALIGN_E_CUDA;
+    }
+    ctx->stats.kernel_launches++;
+  }
+  for (const CkLaunch& cl : cklaunch) {
+    cudaStream_t s = used[lane_i++ % used.size()];
+    if (s != s0) CU(cudaStreamWaitEvent(s, ready, 0));
+    const Plan& p = take[cl.req]->plan;
+    const FwdParams P = plan_params(p.shape, static_cast<int>(take[cl.req]->C), p.frames_per_stage, ctx->wait_limit_ns);
+    for (int k = 0; k <= p.nck; ++k) {
+      cudaError_t e = static_cast<cudaError_t>(launch_trellis(p.shape, P, djobs + cl.first + k, 1, s));
+      if (e != cudaSuccess) {
+        set_error("launch_trellis", e);
+        return ALIGN_E_CUDA;
+      }
+      ctx->stats.kernel_launches++;
+    }
+  }
+  // Join, download statuses and host outputs, record completion.
+  cudaEvent_t joined[64];
+  int nj = 0;
+  for (cudaStream_t s : used) {
+    if (s == s0) continue;
+    CU(cudaEventCreateWithFlags(&joined[nj], cudaEventDisableTiming));
+    CU(cudaEventRecord(joined[nj], s));
+    CU(cudaStreamWaitEvent(s0, joined[nj], 0));
+    ++nj;
+  }
+  for (size_t i = 0; i < take.size(); ++i)
+    CU(cudaMemcpyAsync(b.h_status + i, &dmeta[i].status, 4, cudaMemcpyDeviceToHost, s0));
+  for (size_t i = 0; i < take.size(); ++i) {
+    Request& r = *take[i];
+    if (!r.host_io) continue;
+    const size_t T = static_cast<size_t>(r.T);
+    CU(cudaMemcpyAsync(r.out.path, req_out[i].path, T * 4, cudaMemcpyDeviceToHost, s0));
+    CU(cudaMemcpyAsync(r.out.scores, req_out[i].scores, T * 4, cudaMemcpyDeviceToHost, s0));
+    CU(cudaMemcpyAsync(r.out.total, req_out[i].total, 4, cudaMemcpyDeviceToHost, s0));
+    if (r.out.states) CU(cudaMemcpyAsync(r.out.states, req_out[i].states, T * 4, cudaMemcpyDeviceToHost, s0));
+  }
+  CU(cudaEventCreateWithFlags(&b.done, cudaEventDisableTiming));
+  CU(cudaEventRecord(b.done, s0));
+  cudaEventDestroy(ready);
+  for (int k = 0; k < nj; ++k) cudaEventDestroy(joined[k]);
+  ctx->batches.emplace(b.id, b);
+  return ALIGN_OK;
+}
+
+int pump(align_ctx* ctx, bool launch) {
+  int rc = reap(ctx);
+  if (rc != ALIGN_OK) return rc;
+  if (launch) {
+    rc = launch_queued(ctx);
+    if (rc != ALIGN_OK) return rc;
+  }
+  return ALIGN_OK;
+}
+
+int submit_common(align_ctx* ctx, const float* lp, int64_t T, int64_t C, const int32_t* targets, int64_t L,
+                  int32_t blank, align_out out, uint64_t* request_id, bool host_io) {
+  if (!ctx || !lp || !request_id || !out.path || !out.scores || !out.total) return ALIGN_E_INVAL;
+  if (L > 0 && !targets) return ALIGN_E_INVAL;
+  if (T > INT32_MAX / 2 || L > INT32_MAX / 4) return ALIGN_E_TOO_LARGE;
+  int64_t R = 0;
+  int rc = validate_request(targets, L, C, blank, T, &R);
+  if (rc != ALIGN_OK) return rc;
+  if (static_cast<int64_t>(inflight_count(ctx)) >= ctx->max_inflight) {
+    rc = pump(ctx, true);
+    if (rc != ALIGN_OK) return rc;
+    if (static_cast<int64_t>(inflight_count(ctx)) >= ctx->max_inflight) return ALIGN_E_AGAIN;
+  }
+  Plan p{};
+  rc = make_plan(ctx->tune, T, C, L, ctx->bp_arena.cap(), (ctx->flags & ALIGN_F_FORCE_CHECKPOINT) != 0, &p);
+  if (rc != ALIGN_OK) return rc;
+  if (host_io && host_stage_bytes(T, C) > ctx->stage_arena.cap()) return ALIGN_E_TOO_LARGE;
+  Request r;
+  r.id = ctx->next_id++;
+  r.lp = lp;
+  r.host_io = host_io;
+  r.out = out;
+  r.T = T;
+  r.C = C;
+  r.L = L;
+  r.blank = blank;
+  r.targets.assign(targets, targets + L);
+  r.plan = p;
+  *request_id = r.id;
+  ctx->reqs.emplace(r.id, std::move(r));
+  ctx->queued.push_back(*request_id);
+  const bool launch_now = !(ctx->flags & ALIGN_F_BATCHED);
+  return pump(ctx, launch_now);
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ C ABI --
+extern "C" {
+
+int align_create(align_ctx** out, const align_config* cfg_in) {
+  if (!out) return ALIGN_E_INVAL;
+  *out = nullptr;
+  align_config cfg{};
+  if (cfg_in) cfg = *cfg_in;
+  int ndev = 0;
+  CU(cudaGetDeviceCount(&ndev));
+  if (cfg.device < 0 || cfg.device >= ndev) return ALIGN_E_INVAL;
+  CU(cudaSetDevice(cfg.device));
+  std::unique_ptr<align_ctx> ctx(new align_ctx());
+  ctx->device = cfg.device;
+  ctx->flags = cfg.flags;
+  ctx->max_inflight = cfg.max_inflight > 0 ? cfg.max_inflight : 8192;
+  ctx->wait_limit_ns = static_cast<uint64_t>(cfg.wait_limit_ms ? cfg.wait_limit_ms : 2000) * 1000000ull;
+  CU(cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, cfg.device));
+  ctx->smem_optin = max_smem_optin(cfg.device);
+  ctx->tune = default_tune_table();
+  const uint64_t bp_bytes = cfg.bp_budget_bytes ? cfg.bp_budget_bytes : (1ull << 30);
+  const uint64_t stage_bytes = cfg.staging_bytes ? cfg.staging_bytes : (64ull << 20);
+  const uint64_t meta_bytes = 64ull << 20;
+  const uint64_t pin_bytes = 64ull << 20;
+  if (cudaMalloc(&ctx->d_bp, bp_bytes) != cudaSuccess) return ALIGN_E_NOMEM;
+  ctx->bp_arena.init(bp_bytes);
+  if (cudaMalloc(&ctx->d_meta, meta_bytes) != cudaSuccess) {
+    cudaFree(ctx->d_bp);
+    return ALIGN_E_NOMEM;
+  }
+  ctx->meta_arena.init(meta_bytes);
+  if (cudaMalloc(&ctx->d_stage, stage_bytes) != cudaSuccess) {
+    cudaFree(ctx->d_bp);
+    cudaFree(ctx->d_meta);
+    return ALIGN_E_NOMEM;
+  }
+  ctx->stage_arena.init(stage_bytes);
+  if (cudaMallocHost(&ctx->h_pinned, pin_bytes) != cudaSuccess) {
+    cudaFree(ctx->d_bp);
+    cudaFree(ctx->d_meta);
+    cudaFree(ctx->d_stage);
+    return ALIGN_E_NOMEM;
+  }
+  ctx->pinned_arena.init(pin_bytes);
+  if (cfg.cuda_stream) {
+    ctx->main = static_cast<cudaStream_t>(cfg.cuda_stream);
+  } else {
+    CU(cudaStreamCreateWithFlags(&ctx->main, cudaStreamNonBlocking));
+    ctx->own_main = true;
+  }
+  for (int i = 0; i < 16; ++i) {
+    cudaStream_t s;
+    CU(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    ctx->workers.push_back(s);
+  }
+  for (int i = 0; i < 64; ++i) {
+    cudaEvent_t e;
+    CU(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    ctx->fork_events.push_back(e);
+  }
+  *out = ctx.release();
+  return ALIGN_OK;
+}
+
+int align_destroy(align_ctx* ctx) {
+  if (!ctx) return ALIGN_OK;
+  cudaSetDevice(ctx->device);
+  for (auto& kv : ctx->batches) cudaEventSynchronize(kv.second.done);
+  for (auto& kv : ctx->batches) cudaEventDestroy(kv.second.done);
+  for (cudaStream_t s : ctx->workers) {
+    cudaStreamSynchronize(s);
+    cudaStreamDestroy(s);
+  }
+  for (cudaEvent_t e : ctx->fork_events) cudaEventDestroy(e);
+  if (ctx->own_main) {
+    cudaStreamSynchronize(ctx->main);
+    cudaStreamDestroy(ctx->main);
+  }
+  cudaFree(ctx->d_bp);
+  cudaFree(ctx->d_meta);
+  cudaFree(ctx->d_stage);
+  cudaFreeHost(ctx->h_pinned);
+  delete ctx;
+  return ALIGN_OK;
+}
+
+int align_submit(align_ctx* ctx, const float* log_probs, int64_t T, int64_t C, const int32_t* targets, int64_t L,
+                 int32_t blank, align_out out, uint64_t* request_id) {
+  if (ctx) cudaSetDevice(ctx->device);
+  return submit_common(ctx, log_probs, T, C, targets, L, blank, out, request_id, false);
+}
+
+int align_submit_host(align_ctx* ctx, const float* log_probs, int64_t T, int64_t C, const int32_t* targets,
+                      int64_t L, int32_t blank, align_out out, uint64_t* request_id) {
+  if (ctx) cudaSetDevice(ctx->device);
+  return submit_common(ctx, log_probs, T, C, targets, L, blank, out, request_id, true);
+}
+
+int align_flush(align_ctx* ctx) {
+  if (!ctx) return ALIGN_E_INVAL;
+  cudaSetDevice(ctx->device);
+  return pump(ctx, true);
+}
+
+int align_poll(align_ctx* ctx, uint64_t request_id, int32_t timeout_ms, int32_t* request_status) {
+  if (!ctx) return ALIGN_E_INVAL;
+  cudaSetDevice(ctx->device);
+  auto it = ctx->reqs.find(request_id);
+  if (it == ctx->reqs.end()) return ALIGN_E_NOTFOUND;
+  const auto t0 = std::chrono::steady_clock::now();
+  for (;;) {
+    int rc = pump(ctx, true);
+    if (rc != ALIGN_OK) return rc;
+    Request& r = ctx->reqs.at(request_id);
+    if (r.state == ReqState::Done) {
+      if (request_status) *request_status = r.status;
+      ctx->reqs.erase(request_id);
+      return ALIGN_OK;
+    }
+    if (timeout_ms == 0) return ALIGN_PENDING;
+    if (timeout_ms > 0) {
+      const auto el = std::chrono::duration_cast<std::chrono::milliseconds>(std::chrono::steady_clock::now() - t0);
+      if (el.count() >= timeout_ms) return ALIGN_PENDING;
+    }
+    if (r.state == ReqState::Launched) {
+      Batch& b = ctx->batches.at(r.batch);
+      // Block on the event for up to the remaining time (spin-sleep keeps the timeout honoured).
+      if (timeout_ms < 0) {
+        cudaError_t e = cudaEventSynchronize(b.done);
+        if (e != cudaSuccess) {
+          set_error("cudaEventSynchronize", e);
+          return ALIGN_E_CUDA;
+        }
+      } else {
+        std::this_thread::sleep_for(std::chrono::microseconds(20));
+      }
+    } else if (r.state == ReqState::Queued) {
+      // Waiting for memory held by running batches; with nothing running it can never fit.
+      if (ctx->batches.empty()) {
+        ctx->queued.erase(std::remove(ctx->queued.begin(), ctx->queued.end(), request_id), ctx->queued.end());
+        ctx->reqs.erase(request_id);
+        return ALIGN_E_TOO_LARGE;
+      }
+      if (timeout_ms < 0) {
+        cudaEventSynchronize(ctx->batches.begin()->second.done);
+      } else {
+        std::this_thread::sleep_for(std::chrono::microseconds(20));
+      }
+    }
+  }
+}
+
+int align_join(align_ctx* ctx, void* stream) {
+  if (!ctx) return ALIGN_E_INVAL;
+  cudaSetDevice(ctx->device);
+  cudaStream_t s = stream ? static_cast<cudaStream_t>(stream) : ctx->main;
+  for (auto& kv : ctx->batches) CU(cudaStreamWaitEvent(s, kv.second.done, 0));
+  return ALIGN_OK;
+}
+
+int align_get_stats(align_ctx* ctx, align_stats* out, int32_t reset) {
+  if (!ctx || !out) return ALIGN_E_INVAL;
+  ctx->stats.bp_bytes_peak = std::max(ctx->stats.bp_bytes_peak, ctx->bp_arena.peak());
+  *out = ctx->stats;
+  if (reset) {
+    ctx->stats = align_stats{};
+    ctx->bp_arena.reset_peak();
+  }
+  return ALIGN_OK;
+}
+
+const char* align_status_string(int32_t code) {
+  switch (code) {
+    case ALIGN_OK: return "ALIGN_OK";
+    case ALIGN_PENDING: return "ALIGN_PENDING";
+    case ALIGN_E_INVAL: return "ALIGN_E_INVAL";
+    case ALIGN_E_TARGET: return "ALIGN_E_TARGET";
+    case ALIGN_E_INFEASIBLE: return "ALIGN_E_INFEASIBLE";
+    case ALIGN_E_TOO_LARGE: return "ALIGN_E_TOO_LARGE";
+    case ALIGN_E_AGAIN: return "ALIGN_E_AGAIN";
+    case ALIGN_E_NOPATH: return "ALIGN_E_NOPATH";
+    case ALIGN_E_TIMEOUT: return "ALIGN_E_TIMEOUT";
+    case ALIGN_E_CUDA: return "ALIGN_E_CUDA";
+    case ALIGN_E_NOTFOUND: return "ALIGN_E_NOTFOUND";
+    case ALIGN_E_NOMEM: return "ALIGN_E_NOMEM";
+    default: return "ALIGN_E_UNKNOWN";
+  }
+}
+
+const char* align_last_error(void) { return g_last_error; }
+
+int align_set_tuning(align_ctx* ctx, int32_t states_per_lane, int32_t max_cluster) {
+  if (!ctx) return ALIGN_E_INVAL;
+  if (states_per_lane && states_per_lane != 2 && states_per_lane != 4 && states_per_lane != 8 &&
+      states_per_lane != 16)
+    return ALIGN_E_INVAL;
+  if (max_cluster < 0 || max_cluster > 16) return ALIGN_E_INVAL;
+  if (states_per_lane) ctx->tune.K = states_per_lane;
+  if (max_cluster) ctx->tune.max_cluster = max_cluster;
+  return ALIGN_OK;
+}
+
+}  // extern "C"

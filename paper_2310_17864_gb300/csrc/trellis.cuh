@@ -1,0 +1,103 @@
+// Device-side descriptors shared by the trellis kernels and the host runtime.
+//
+// Trellis (CTC, as used by the forced-alignment feature of TorchAudio 2.1,
+// paper Sec. 4): S = 2L+1 states; even states are the blank, odd state s
+// carries targets[(s-1)/2].
+//
+// Work decomposition: one alignment ("job") is owned by a team of warps that
+// are chained along the state axis. Warp g of the team holds states
+// [32*K*g, 32*K*(g+1)); lane l of it holds the K consecutive states starting
+// at 32*K*g + K*l, in registers. Information only flows towards larger s
+// (alpha_t(s) reads s, s-1, s-2 at t-1), so each warp only needs one value
+// per frame from its left neighbour: alpha_{t-1}(first state - 1). Inside a
+// warp it comes by shuffle, between warps of a CTA through a tagged ring in
+// shared memory, between CTAs of a thread-block cluster through the same
+// ring written over distributed shared memory. Warps therefore run as a
+// skewed pipeline: no barrier per frame.
+//
+// Backpointer layout (2 bits of information per cell, packed by warp ballots):
+// for warp g and stored frame row r, NW = 3K/2 32-bit words
+//   word j      (0 <= j < K): bit l = "advance won" for state 32Kg + Kl + j
+//   word K + i  (0 <= i < K/2): bit l = "skip won" for the label state
+//                               32Kg + Kl + 2i + 1
+// at bp[(g * bp_rows + r) * NW]. The predecessor is s-2 if the skip bit is
+// set, else s-1 if the advance bit is set, else s.
+#pragma once
+#include <cstdint>
+
+namespace gb300_align {
+
+constexpr int kStages = 4;            // emission ring stages per CTA
+constexpr int kBtWindow = 32;         // frames per backtrack window
+
+// Job flags.
+constexpr uint32_t kJobWriteFinal = 1u;  // pick the final state, write total/status/state_io
+constexpr uint32_t kJobChase = 2u;       // walk the backpointers from state_io and write outputs
+constexpr uint32_t kJobBulkRows = 4u;    // emission rows may be staged with cp.async.bulk
+
+struct alignas(16) FwdJob {
+  const float* lp;         // [T][C] row-major FP32
+  const int32_t* tgt;      // [L] device copy of the targets
+  uint32_t* bp;            // packed backpointers (nullptr: none stored)
+  float* ckpt;             // alpha rows at frames 0, ck_every, 2*ck_every, ... (nullptr: none)
+  const float* alpha_in;   // alpha at t_begin (S floats); nullptr: the t = 0 initialisation
+  float* final2;           // [2] alpha_{T-1}(S-2), alpha_{T-1}(S-1)
+  int32_t* status;         // request status word (see align.h codes)
+  int32_t* state_io;       // chase entry state (in) / state at t_begin (out)
+  int32_t* path;           // [T] outputs (nullptr when not chasing)
+  float* scores;           // [T]
+  float* total;            // [1]
+  int32_t* states;         // [T] or nullptr
+  int32_t T, C, blank, L;
+  int32_t S;
+  int32_t t_begin;         // first frame of this pass
+  int32_t t_end;           // one past the last frame of this pass
+  int32_t bp_rows;         // rows per warp in bp; row r holds frame t_begin + 1 + r
+  int32_t ck_every;        // checkpoint interval in frames (0: none)
+  int32_t ck_stride;       // floats between checkpoint rows
+  uint32_t flags;
+  int32_t pad0;
+};
+
+struct FwdParams {
+  int32_t rb;              // boundary ring slots per warp (power of two, >= 4*F + 2)
+  int32_t frames_per_stage;
+  int32_t stage_bytes;     // bytes per emission stage (16-byte multiple)
+  int32_t off_ring;        // shared-memory offsets
+  int32_t off_stage;
+  int32_t off_bt;
+  uint64_t wait_limit_ns;  // limit of every spin wait
+};
+
+// Result codes written to FwdJob::status (same values as align.h).
+constexpr int32_t kStOk = 0;
+constexpr int32_t kStPending = 1;
+constexpr int32_t kStNoPath = -6;
+constexpr int32_t kStTimeout = -7;
+
+// Host-side launch entry points (defined in trellis_kernels.cu).
+struct LaunchShape {
+  int K;                   // states per lane
+  int warps;               // warps per CTA
+  int ncta;                // CTAs per cluster (1: no cluster)
+};
+
+// Number of 32-bit backpointer words per warp and frame.
+#ifdef __CUDACC__
+__host__ __device__
+#endif
+constexpr int bp_words(int K) { return 3 * K / 2; }
+
+// Shared-memory plan for a launch shape and vocabulary size.
+FwdParams plan_params(const LaunchShape& shape, int C, int frames_per_stage, uint64_t wait_limit_ns);
+int smem_bytes(const LaunchShape& shape, const FwdParams& p);
+
+// Launch the fused forward (+ backtrack) kernel over njobs jobs, one cluster
+// (or CTA) per job, on the given stream. Returns a cudaError_t value.
+int launch_trellis(const LaunchShape& shape, const FwdParams& p, const FwdJob* d_jobs, int njobs,
+                   void* stream);
+
+// Largest dynamic shared memory the kernel for this shape may use.
+int max_smem_optin(int device);
+
+}  // namespace gb300_align

@@ -1,0 +1,215 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+The recursion is one FP32 add after an exact max per cell, so paths, states,
+per-frame scores and totals must match the FP32 oracle bit for bit (tolerance
+zero), for every launch shape (warp, CTA, cluster), mode (full backpointers,
+checkpointed recompute, plain, batched, host I/O) and input class.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import checks
+from paper_2310_17864_gb300 import align, build, synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def al():
+    build.build()
+    a = align.Aligner(device=0, bp_budget_bytes=8 << 30)
+    yield a
+    a.close()
+
+
+def compare(res, lp_np, targets, blank, label=""):
+    o = oracle.viterbi_f32(lp_np, targets, blank)
+    assert res.status == o["status"], (label, res.status, o["status"])
+    if o["status"] not in (0,):
+        return o
+    path = res.path.cpu().numpy()
+    scores = res.scores.cpu().numpy()
+    total = res.total.cpu().numpy()[0]
+    assert np.array_equal(path, o["path"]), (label, np.nonzero(path != o["path"])[0][:10])
+    if res.states is not None:
+        assert np.array_equal(res.states.cpu().numpy(), o["states"]), label
+    assert scores.tobytes() == o["scores"].tobytes(), label
+    assert np.float32(total).tobytes() == np.float32(o["total"]).tobytes(), (label, total, o["total"])
+    return o
+
+
+def run(al, lp, targets, blank=0, label=""):
+    lp_t = torch.as_tensor(np.ascontiguousarray(lp, dtype=np.float32))
+    res = al.align(lp_t.cuda(), targets, blank, want_states=True)
+    return compare(res, lp_t.numpy(), np.asarray(targets, np.int32), blank, label)
+
+
+def test_config1_plain_utterance(al):
+    (s,) = synth.specs(1)
+    u = synth.make_utterance(s.seed, s.T, s.C, s.L, s.repeat_frac)
+    run(al, u.lp.numpy(), u.targets, 0, "cfg1")
+
+
+@pytest.mark.parametrize("T,C,L", [
+    (1, 2, 0), (1, 4, 1), (2, 2, 1), (3, 3, 2), (7, 5, 3), (50, 2, 1), (64, 32, 0),
+    (300, 32, 63), (300, 32, 64), (300, 32, 31), (300, 32, 32),          # warp boundary (K=4: 128 states)
+    (900, 32, 127), (900, 32, 128), (900, 32, 255), (900, 32, 256),      # 1-2 / 2-3 warps
+    (3000, 32, 1023), (3000, 32, 1024), (9000, 32, 2047), (9000, 32, 2048),  # 16..32 warps, cluster edge
+    (5000, 500, 900), (400, 29, 90), (400, 31, 90), (333, 3, 100),
+])
+def test_shapes(al, T, C, L):
+    u = synth.make_utterance(T * 31 + L, T, C, L, repeat_frac=0.1)
+    run(al, u.lp.numpy(), u.targets, 0, f"T{T}C{C}L{L}")
+
+
+def test_tight_and_repeats(al):
+    rng = np.random.default_rng(5)
+    for L in (1, 5, 40, 200, 700):
+        tg = synth.make_targets(rng, L, 8, repeat_frac=0.5)
+        T = L + synth.count_repeats(tg)                    # exactly one feasible path
+        lp = rng.standard_normal((T, 8)).astype(np.float32)
+        run(al, lp, tg, 0, f"tight{L}")
+        allrep = np.full(L, 3, np.int32)                   # all-repeat targets
+        lp = rng.standard_normal((2 * L - 1 + 5, 8)).astype(np.float32)
+        run(al, lp, allrep, 0, f"allrep{L}")
+
+
+def test_integer_ties_tie_rule(al):
+    """Integer emissions: many exact ties; the tie rule decides the path."""
+    rng = np.random.default_rng(6)
+    for (T, C, L) in [(10, 3, 3), (100, 4, 30), (700, 5, 200), (2000, 4, 600), (6000, 4, 2100)]:
+        tg = synth.make_targets(rng, L, C, repeat_frac=0.2)
+        lp = -rng.integers(0, 3, size=(T, C)).astype(np.float32)
+        run(al, lp, tg, 0, f"ties{T}")
+        run(al, np.zeros((T, C), np.float32), tg, 0, f"zeros{T}")
+
+
+def test_minus_inf_and_nopath(al):
+    rng = np.random.default_rng(7)
+    u = synth.make_utterance(77, 400, 16, 100)
+    lp = u.lp.numpy().copy()
+    lp[rng.random(lp.shape) < 0.3] = -np.inf
+    ext = synth.expand_tokens(u.targets)
+    lp[np.arange(400), ext[u.planted]] = -0.5    # keep the planted path finite
+    run(al, lp, u.targets, 0, "neginf")
+    lp2 = u.lp.numpy().copy()
+    lp2[:, u.targets[3]] = -np.inf                # a target that can never be emitted
+    run(al, lp2, u.targets, 0, "nopath")
+
+
+def test_nonzero_blank(al):
+    rng = np.random.default_rng(8)
+    C, blank = 40, 39
+    tg = rng.integers(0, 39, size=120).astype(np.int32)
+    lp = torch.log_softmax(torch.randn(700, C) * 3, -1).numpy()
+    run(al, lp, tg, blank, "blank39")
+
+
+def test_validation_errors(al):
+    lp = torch.zeros(5, 4, device="cuda")
+    for tg, blank, code in [([1, 4], 0, align.ALIGN_E_TARGET), ([0], 0, align.ALIGN_E_TARGET),
+                            ([1], 4, align.ALIGN_E_INVAL), ([1, 1, 1, 1], 0, align.ALIGN_E_INFEASIBLE)]:
+        with pytest.raises(align.AlignError) as e:
+            al.submit(lp, tg, blank)
+        assert e.value.code == code
+
+
+def test_checkpointed_equals_full():
+    build.build()
+    ck = align.Aligner(device=0, force_checkpoint=True)
+    full = align.Aligner(device=0)
+    try:
+        for (T, C, L, seed) in [(1, 4, 1, 1), (2, 4, 1, 2), (17, 5, 4, 3), (400, 32, 100, 4), (401, 32, 100, 5),
+                                (2500, 32, 600, 6), (9000, 32, 2100, 7)]:
+            u = synth.make_utterance(seed, T, C, L, repeat_frac=0.1)
+            a = ck.align(u.lp.cuda(), u.targets, 0, want_states=True)
+            b = full.align(u.lp.cuda(), u.targets, 0, want_states=True)
+            assert a.status == b.status == 0
+            for x, y in [(a.path, b.path), (a.states, b.states), (a.scores, b.scores), (a.total, b.total)]:
+                assert torch.equal(x.cpu().view(torch.int32), y.cpu().view(torch.int32))
+            compare(a, u.lp.numpy(), u.targets, 0, f"ck{T}")
+        assert ck.stats()["checkpointed"] >= 7
+    finally:
+        ck.close()
+        full.close()
+
+
+def test_budget_forces_checkpoint():
+    """A request whose full backpointers exceed the budget runs checkpointed."""
+    build.build()
+    u = synth.make_utterance(9, 6000, 32, 1500)
+    p = align.align_plan(6000, 32, 1500)
+    a = align.Aligner(device=0, bp_budget_bytes=p["backpointer_bytes"] // 2)
+    try:
+        res = a.align(u.lp.cuda(), u.targets, 0)
+        compare(res, u.lp.numpy(), u.targets, 0, "budget")
+        assert a.stats()["checkpointed"] == 1
+    finally:
+        a.close()
+
+
+def test_host_io(al):
+    u = synth.make_utterance(10, 1500, 32, 375)
+    lp = u.lp.pin_memory()
+    res = al.submit_host(lp, u.targets, 0, want_states=True)
+    al.flush()
+    al.poll(res)
+    compare(res, u.lp.numpy(), u.targets, 0, "host")
+
+
+def test_config2_batched_equals_plain_and_oracle():
+    build.build()
+    b = synth.make_batch(synth.specs(2), device="cuda")
+    plain = align.Aligner(device=0)
+    batched = align.Aligner(device=0, batched=True)
+    try:
+        rp = [plain.submit(b.utt(i), b.targets[i], 0) for i in range(len(b))]
+        rb = [batched.submit(b.utt(i), b.targets[i], 0) for i in range(len(b))]
+        batched.flush()
+        for x, y in zip(rp, rb):
+            plain.poll(x)
+            batched.poll(y)
+        lp_host = b.lp.cpu().numpy()
+        for i, (x, y) in enumerate(zip(rp, rb)):
+            assert torch.equal(x.path, y.path) and torch.equal(x.scores.view(torch.int32), y.scores.view(torch.int32))
+            sl = lp_host[b.offsets[i]:b.offsets[i + 1]]
+            compare(y, sl, b.targets[i], 0, f"cfg2[{i}]")
+    finally:
+        plain.close()
+        batched.close()
+
+
+def test_cluster_long_transcript(al):
+    """S beyond one CTA: the alpha vector spread over a thread-block cluster."""
+    for (T, L) in [(12000, 3000), (40000, 17000)]:
+        u = synth.make_utterance(T + L, T, 32, L)
+        p = align.align_plan(T, 32, L, budget=8 << 30)
+        assert p["cluster_ctas"] > 1
+        run(al, u.lp.numpy(), u.targets, 0, f"cluster{L}")
+
+
+def test_invariants_on_config4_sample():
+    """Ragged batch (first 512 utterances of the C=32 workload) batched; every
+    result satisfies the invariants and a sample matches the oracle."""
+    build.build()
+    specs = synth.specs(4, C=32, n=512)
+    b = synth.make_batch(specs, device="cuda")
+    a = align.Aligner(device=0, batched=True, bp_budget_bytes=8 << 30)
+    try:
+        rs = [a.submit(b.utt(i), b.targets[i], 0) for i in range(len(b))]
+        a.flush()
+        lp_host = b.lp.cpu().numpy()
+        for i, r in enumerate(rs):
+            a.poll(r)
+            assert r.status == 0
+            path = r.path.cpu().numpy()
+            assert checks.collapse(path, 0) == b.targets[i].tolist()
+            sl = lp_host[b.offsets[i]:b.offsets[i + 1]]
+            assert (r.scores.cpu().numpy() == sl[np.arange(sl.shape[0]), path]).all()
+            assert checks.fold_f32_fast(r.scores.cpu().numpy()) == r.total.cpu().numpy()[0]
+            if i % 16 == 0:
+                compare(r, sl, b.targets[i], 0, f"cfg4[{i}]")
+    finally:
+        a.close()
