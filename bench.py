@@ -1,0 +1,342 @@
+#!/usr/bin/env python3
+"""Benchmark: CTC forced alignment (Viterbi over the CTC trellis) on GB300.
+
+Workload (default): 64 utterances, T uniform in 500..3000 frames (20 ms),
+C=32 classes, L=round(T/4) targets, FP32 synthetic log-probabilities (seeded;
+3*N(0,1) logits with +4 on a planted feasible path, log_softmax). One step =
+the whole hot path (validate, expand, forward max-plus recursion, 2-bit
+backpointers, final state, backtrack, scores) for the whole batch.
+
+Metric: trellis cells per second, cells = sum over utterances of T * (2L+1).
+  value  : batched launch through the C ABI, inputs resident in device memory,
+           device time between CUDA events on the submitting stream (L2 flushed
+           before every timed step by writing a 256 MiB buffer).
+  e2e    : same metric through align_submit_host (pinned host emissions,
+           host->device and device->host copies inside the timed region),
+           host wall clock from the first submit to the last poll.
+  plain  : one synchronous submit+poll per utterance (reported beside).
+With --gpus N > 1 (torchrun), every rank aligns its own copy of the batch (no
+data-path collective; weak scaling); value is the sum of cells over ranks
+divided by the slowest rank's time.
+
+--impl reference times the CPU oracle (plain C, FP32) on this host's cores on
+the same workload and metric.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "trellis cells/s (T*S)"
+WORKLOAD = "batch64_T500-3000_C32_L=T/4"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the CPU oracle baseline")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def cpu_oracle_rate(batch, seconds: float) -> dict:
+    """The oracle as it stands, over whole copies of the batch on all host cores
+    (one utterance per task), until about `seconds` of wall time."""
+    import concurrent.futures as cf
+
+    import oracle
+
+    lp = batch.lp.cpu().numpy()
+    items = [(lp[batch.offsets[i]:batch.offsets[i + 1]], batch.targets[i]) for i in range(len(batch))]
+    cells_per_pass = batch.cells
+    n = cores()
+    oracle.lib()
+    t0 = time.perf_counter()
+    passes = 0
+    with cf.ThreadPoolExecutor(max_workers=n) as ex:  # ctypes releases the GIL during the C call
+        while True:
+            list(ex.map(lambda it: oracle.viterbi_f32(it[0], it[1], 0), items))
+            passes += 1
+            if time.perf_counter() - t0 > seconds or passes >= 1000:
+                break
+    dt = time.perf_counter() - t0
+    return {"value": passes * cells_per_pass / dt, "unit": "cells/s", "cores": n, "kind": "oracle",
+            "sample": f"{passes} full pass(es) of the {len(batch)}-utterance batch "
+                      f"({cells_per_pass} cells each) over {n} threads, {dt:.1f} s"}
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._read, daemon=True).start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            time.sleep(0.15)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=2)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self) -> dict:
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        from paper_2310_17864_gb300 import synth
+        batch = synth.make_batch(synth.specs(2), device="cpu")
+        steps = []
+        import oracle
+        lp = batch.lp.numpy()
+        items = [(lp[batch.offsets[i]:batch.offsets[i + 1]], batch.targets[i]) for i in range(len(batch))]
+        import concurrent.futures as cf
+        n = cores()
+        with cf.ThreadPoolExecutor(max_workers=n) as ex:
+            for k in range(args.warmup + args.steps):
+                t0 = time.perf_counter()
+                list(ex.map(lambda it: oracle.viterbi_f32(it[0], it[1], 0), items))
+                if k >= args.warmup:
+                    steps.append(time.perf_counter() - t0)
+        ms = 1e3 * statistics.mean(steps)
+        value = batch.cells / (ms / 1e3)
+        print(json.dumps({
+            "impl": "reference", "metric": METRIC, "value": value, "unit": "cells/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "utterances": len(batch), "cells_per_step": batch.cells},
+            "cpu_baseline": {"value": value, "unit": "cells/s", "cores": n, "kind": "oracle",
+                             "sample": f"the whole {len(batch)}-utterance batch per step over {n} threads"},
+            "e2e": {"value": value, "unit": "cells/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        }))
+        return
+
+    import torch
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = local if world > 1 else 0
+    torch.cuda.set_device(dev)
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2310_17864_gb300 import align, synth
+
+    batch = synth.make_batch(synth.specs(2), device=f"cuda:{dev}")
+    n = len(batch)
+    cells = batch.cells
+    T_max = int(max(batch.offsets[i + 1] - batch.offsets[i] for i in range(n)))
+    utts = [batch.utt(i) for i in range(n)]
+    outs = []
+    for i in range(n):
+        T = utts[i].shape[0]
+        outs.append((torch.empty(T, dtype=torch.int32, device=dev), torch.empty(T, dtype=torch.float32, device=dev),
+                     torch.empty(1, dtype=torch.float32, device=dev), None))
+    stream = torch.cuda.Stream(dev)
+    al = align.Aligner(device=dev, batched=True, stream=stream, bp_budget_bytes=4 << 30)
+    flush_buf = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
+
+    def step_batched(timed: bool):
+        flush_buf.fill_(1)
+        with torch.cuda.stream(stream):
+            torch.cuda._sleep(2_000_000)  # hold the stream while the host enqueues the batch
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            rs = [al.submit(utts[i], batch.targets[i], 0, out=outs[i]) for i in range(n)]
+            al.flush()
+            al.join(stream)
+            ev1.record(stream)
+        for r in rs:
+            al.poll(r)
+            assert r.status == 0, r.status
+        ev1.synchronize()
+        return ev0.elapsed_time(ev1)
+
+    for _ in range(args.warmup):
+        step_batched(False)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    l0 = al.stats()["kernel_launches"]
+    times = []
+    with Clocks(dev) as clk:
+        for _ in range(args.steps):
+            times.append(step_batched(True))
+    launches = (al.stats()["kernel_launches"] - l0) // max(args.steps, 1)
+    torch.cuda.synchronize()
+    ms = statistics.mean(times)
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    value = world * cells / (ms / 1e3)
+
+    # Plain: one synchronous submit + poll per utterance.
+    plain = None
+    if not args.no_plain:
+        pl = align.Aligner(device=dev, stream=stream, bp_budget_bytes=4 << 30)
+        lat = []
+        for k in range(2):
+            flush_buf.fill_(1)
+            torch.cuda.synchronize()
+            t_all = time.perf_counter()
+            for i in range(n):
+                t0 = time.perf_counter()
+                r = pl.submit(utts[i], batch.targets[i], 0, out=outs[i])
+                pl.poll(r)
+                if k == 1:
+                    lat.append(time.perf_counter() - t0)
+            dt = time.perf_counter() - t_all
+        pl.close()
+        lat_ms = np.array(lat) * 1e3
+        plain = {"value": cells / dt, "unit": "cells/s", "p50_ms": float(np.percentile(lat_ms, 50)),
+                 "p99_ms": float(np.percentile(lat_ms, 99)), "launch": "one synchronous launch per utterance"}
+
+    # End to end through the host-buffer entry point.
+    e2e = None
+    if not args.no_e2e:
+        host_lp = [u.cpu().pin_memory() for u in utts]
+        host_out = [(torch.empty(u.shape[0], dtype=torch.int32).pin_memory(),
+                     torch.empty(u.shape[0], dtype=torch.float32).pin_memory(),
+                     torch.empty(1, dtype=torch.float32).pin_memory(), None) for u in utts]
+        h2d = sum(x.numel() * 4 for x in host_lp) + sum(t.size * 4 for t in batch.targets)
+        d2h = sum(u.shape[0] * 8 + 4 for u in utts)
+        e_times = []
+        for k in range(args.warmup + max(3, args.steps // 2)):
+            flush_buf.fill_(1)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            rs = [al.submit_host(host_lp[i], batch.targets[i], 0, out=host_out[i]) for i in range(n)]
+            al.flush()
+            for r in rs:
+                al.poll(r)
+            if k >= args.warmup:
+                e_times.append(time.perf_counter() - t0)
+        e_ms = 1e3 * statistics.mean(e_times)
+        e2e = {"value": world * cells / (e_ms / 1e3), "unit": "cells/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "ms_per_step": e_ms}
+
+    if rank != 0:
+        al.close()
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        cpu = cpu_oracle_rate(batch, args.cpu_seconds)
+
+    # Roofline terms for the trellis kernel (per launch = the whole batch).
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except Exception:
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    plans = [align.align_plan(int(batch.offsets[i + 1] - batch.offsets[i]), 32, len(batch.targets[i]))
+             for i in range(n)]
+    bp_bytes = sum(p["backpointer_bytes"] for p in plans)
+    em_bytes = int(batch.lp.numel()) * 4
+    out_bytes = sum(u.shape[0] * 8 + 4 for u in utts)
+    alg_bytes = em_bytes + 2 * bp_bytes + out_bytes   # backpointers written once, read back by the walk
+    achieved_gbs = alg_bytes / (ms / 1e3) / 1e9
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "cells/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "utterances": n, "cells_per_step": cells, "T_max": T_max,
+                   "l2": "flushed (256 MiB write) before every timed step", "parallelism": f"replicas{world}"},
+        "p50_ms": ms, "p99_ms": float(np.percentile(times, 99)),
+        "plain": plain,
+        "e2e": e2e,
+        "gpu_launches": int(launches),
+        "roofline": {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": achieved_gbs / hbm_peak, "traffic": None,
+                     "alg_bytes_per_launch": alg_bytes, "peak_source": "MEASURED_PEAKS.json hbm_gbs"},
+        "cpu_baseline": cpu,
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line))
+    al.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -224,7 +224,7 @@ __global__ void __launch_bounds__(K <= 8 ? 1024 : 512)
       mbar_init(&head->empty[st], static_cast<uint32_t>(W));
     }
     head->abort = 0;
-    head->prog = 0;
+    head->prog = static_cast<uint32_t>(t_begin);  // no slot holds a frame before t_begin
     fence_barrier_init();
   }
   __syncthreads();
@@ -302,8 +302,9 @@ __global__ void __launch_bounds__(K <= 8 ? 1024 : 512)
   const uint64_t* my_ring = ring + warp * P.rb;
   uint64_t* next_ring = ring + (warp + 1) * P.rb;
   const uint32_t remote_ring = send_remote ? mapa_rank(smem_addr(ring), crank + 1) : 0u;
-  const uint32_t remote_prog = (warp == 0 && crank > 0) ? mapa_rank(smem_addr(&head->prog), crank - 1) : 0u;
-  uint32_t cached_prog = 0;
+  const bool publish_prog = (warp == 0 && crank > 0);
+  const uint32_t remote_prog = publish_prog ? mapa_rank(smem_addr(&head->prog), crank - 1) : 0u;
+  uint32_t cached_prog = static_cast<uint32_t>(t_begin);
 
   auto send = [&](int t, float v) {  // lane 31 only
     const uint64_t word = (static_cast<uint64_t>(static_cast<uint32_t>(t + 1)) << 32) | __float_as_uint(v);
@@ -357,7 +358,7 @@ __global__ void __launch_bounds__(K <= 8 ? 1024 : 512)
         issued = chunk + 3;
       }
       if (!warp_wait_phase(&head->full[chunk % kStages], (chunk / kStages) & 1, abort, limit, lane)) break;
-      if (lane == 0 && remote_prog != 0u) st_remote_u32(remote_prog, static_cast<uint32_t>(t - 1));
+      if (lane == 0 && publish_prog) st_remote_u32(remote_prog, static_cast<uint32_t>(t - 1));
       row = reinterpret_cast<const float*>(stages + (chunk % kStages) * P.stage_bytes);
     } else {
       row += C;
