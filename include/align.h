@@ -54,6 +54,11 @@ extern "C" {
                                          queued requests together as one ragged batch */
 #define ALIGN_F_FORCE_CHECKPOINT 0x2u /* always use checkpointed recompute (no full backpointers) */
 #define ALIGN_F_NO_GRAPHS 0x4u        /* batched launches without CUDA-graph capture */
+#define ALIGN_F_TEST_STALL 0x80000000u /* testing the device watchdog only: in every request whose
+                                         trellis spans more than one warp, the first warp never
+                                         hands its values on, so the next warp's bounded wait runs
+                                         out and the request ends with ALIGN_E_TIMEOUT after about
+                                         wait_limit_ms; single-warp requests are unaffected */
 
 typedef struct align_ctx align_ctx;   /* opaque */
 
@@ -112,6 +117,26 @@ int align_submit_host(align_ctx *ctx, const float *log_probs, int64_t T, int64_t
                       const int32_t *targets, int64_t L, int32_t blank, align_out out,
                       uint64_t *request_id);
 
+/* One request of a batch submission. */
+#define ALIGN_REQ_HOST 0x1u  /* log_probs and out.* are HOST pointers (as align_submit_host) */
+typedef struct {
+    const float *log_probs;   /* [T][C] FP32 row-major, device (or host with ALIGN_REQ_HOST) */
+    int64_t T, C;
+    const int32_t *targets;   /* HOST int32 [L], copied during the call */
+    int64_t L;
+    int32_t blank;
+    uint32_t flags;           /* ALIGN_REQ_* */
+    align_out out;
+} align_request;
+
+/* Submit n requests in one call; they are queued together and, unless the
+   context is in batched mode, launched together as one ragged batch before
+   return. Each request is validated like align_submit: request_ids[i] gets its
+   id (0 if rejected) and submit_status[i] (optional) its result code. Returns
+   ALIGN_OK if all were accepted, else the first rejection code. */
+int align_submit_batch(align_ctx *ctx, int32_t n, const align_request *reqs, uint64_t *request_ids,
+                       int32_t *submit_status);
+
 /* Launch every queued request that fits the memory budget (batched mode).
    Requests that do not fit yet stay queued and are launched by later calls
    once memory is released. No-op in plain mode when nothing is queued. */
@@ -148,11 +173,20 @@ const char *align_status_string(int32_t code);
 /* Text of the last CUDA error seen by this thread (static buffer). */
 const char *align_last_error(void);
 
-/* Tuning of the trellis kernel: states per lane (2, 4, 8 or 16) and the
-   maximum thread-block cluster size for long transcripts (1..16). Values of 0
-   leave the current choice. The defaults come from the built-in autotuned
-   table; align_autotune replaces it with measurements on this GPU. */
-int align_set_tuning(align_ctx *ctx, int32_t states_per_lane, int32_t max_cluster);
+/* Tuning of the trellis kernel for requests submitted after the call:
+   states per lane K (2, 4, 8 or 16), warps per CTA before a transcript is
+   split over a thread-block cluster (1..32), and the largest cluster (1..16).
+   0 leaves a value unchanged. Every choice gives bit-identical results. */
+int align_set_tuning(align_ctx *ctx, int32_t states_per_lane, int32_t cta_warps, int32_t max_cluster);
+
+/* Measurement helper: time per frame of the irreducible per-frame chain of
+   the recursion at warp scope with null work around it (shared-memory
+   emission read, neighbour shuffle, one max, one add), run by `ctas` CTAs of
+   `warps` warps for `frames` frames. Allocates a 24-byte result buffer on
+   `device` and synchronises. This is the per-frame synchronisation bound of
+   the roofline; it is not part of the alignment path. */
+int align_probe_frame_latency(int32_t device, int32_t warps, int32_t ctas, int32_t frames,
+                              double *ns_per_frame);
 
 /* ---- host-only helpers (no GPU needed) -------------------------------- */
 
@@ -177,10 +211,10 @@ typedef struct {
 } align_plan_info;
 
 /* Plan a request of T frames, C classes and L targets for a context with the
-   given budget (0 = default), flags and tuning (0 = defaults).
+   given budget (0 = default), flags and tuning (0 = defaults, see align_set_tuning).
    Returns ALIGN_OK, ALIGN_E_INVAL or ALIGN_E_TOO_LARGE. */
 int align_plan(int64_t T, int64_t C, int64_t L, uint64_t bp_budget_bytes, uint32_t flags,
-               int32_t states_per_lane, int32_t max_cluster, align_plan_info *out);
+               int32_t states_per_lane, int32_t cta_warps, int32_t max_cluster, align_plan_info *out);
 
 #ifdef __cplusplus
 }

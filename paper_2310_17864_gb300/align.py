@@ -35,11 +35,12 @@ ALIGN_E_NOMEM = -10
 ALIGN_F_BATCHED = 0x1
 ALIGN_F_FORCE_CHECKPOINT = 0x2
 ALIGN_F_NO_GRAPHS = 0x4
+ALIGN_F_TEST_STALL = 0x80000000
 
 # Every entry point declared in include/align.h.
-EXPORTS = ("align_create", "align_destroy", "align_submit", "align_submit_host", "align_flush",
+EXPORTS = ("align_create", "align_destroy", "align_submit", "align_submit_host", "align_submit_batch", "align_flush",
            "align_poll", "align_join", "align_get_stats", "align_status_string", "align_last_error",
-           "align_set_tuning", "align_validate", "align_plan")
+           "align_set_tuning", "align_validate", "align_plan", "align_probe_frame_latency")
 
 
 class AlignConfig(ctypes.Structure):
@@ -52,6 +53,15 @@ class AlignConfig(ctypes.Structure):
 class AlignOut(ctypes.Structure):
     _fields_ = [("path", ctypes.c_void_p), ("scores", ctypes.c_void_p), ("total", ctypes.c_void_p),
                 ("states", ctypes.c_void_p)]
+
+
+ALIGN_REQ_HOST = 0x1
+
+
+class AlignRequest(ctypes.Structure):
+    _fields_ = [("log_probs", ctypes.c_void_p), ("T", ctypes.c_int64), ("C", ctypes.c_int64),
+                ("targets", ctypes.c_void_p), ("L", ctypes.c_int64), ("blank", ctypes.c_int32),
+                ("flags", ctypes.c_uint32), ("out", AlignOut)]
 
 
 class AlignStats(ctypes.Structure):
@@ -92,6 +102,8 @@ def lib() -> ctypes.CDLL:
         L.align_destroy.argtypes = [vp]
         L.align_submit.argtypes = [vp, vp, i64, i64, vp, i64, i32, AlignOut, ctypes.POINTER(u64)]
         L.align_submit_host.argtypes = [vp, vp, i64, i64, vp, i64, i32, AlignOut, ctypes.POINTER(u64)]
+        L.align_submit_batch.argtypes = [vp, i32, ctypes.POINTER(AlignRequest), ctypes.POINTER(u64),
+                                         ctypes.POINTER(i32)]
         L.align_flush.argtypes = [vp]
         L.align_poll.argtypes = [vp, u64, i32, ctypes.POINTER(i32)]
         L.align_join.argtypes = [vp, vp]
@@ -100,9 +112,10 @@ def lib() -> ctypes.CDLL:
         L.align_status_string.restype = ctypes.c_char_p
         L.align_last_error.argtypes = []
         L.align_last_error.restype = ctypes.c_char_p
-        L.align_set_tuning.argtypes = [vp, i32, i32]
+        L.align_set_tuning.argtypes = [vp, i32, i32, i32]
+        L.align_probe_frame_latency.argtypes = [i32, i32, i32, i32, ctypes.POINTER(ctypes.c_double)]
         L.align_validate.argtypes = [vp, i64, i64, i32, i64, ctypes.POINTER(i64)]
-        L.align_plan.argtypes = [i64, i64, i64, u64, u32, i32, i32, ctypes.POINTER(AlignPlanInfo)]
+        L.align_plan.argtypes = [i64, i64, i64, u64, u32, i32, i32, i32, ctypes.POINTER(AlignPlanInfo)]
         for name in EXPORTS:
             fn = getattr(L, name)
             if fn.restype is ctypes.c_int or fn.restype is None:
@@ -157,6 +170,18 @@ def align_submit_host(ctx, log_probs_ptr: int, T: int, C: int, targets, blank: i
     return rid.value
 
 
+def align_submit_batch(ctx, reqs) -> tuple[list[int], list[int]]:
+    """reqs: sequence of AlignRequest. Returns (request ids, per-request status)."""
+    n = len(reqs)
+    arr = (AlignRequest * n)(*reqs)
+    ids = (ctypes.c_uint64 * n)()
+    st = (ctypes.c_int32 * n)()
+    rc = lib().align_submit_batch(ctx, n, arr, ids, st)
+    if rc < 0 and all(x != 0 for x in st):  # a context-level failure
+        raise AlignError(rc, "align_submit_batch")
+    return list(ids), list(st)
+
+
 def align_flush(ctx) -> None:
     _check(lib().align_flush(ctx), "align_flush")
 
@@ -178,8 +203,16 @@ def align_get_stats(ctx, reset: bool = False) -> dict:
     return {k: getattr(s, k) for k, _ in AlignStats._fields_}
 
 
-def align_set_tuning(ctx, states_per_lane: int = 0, max_cluster: int = 0) -> None:
-    _check(lib().align_set_tuning(ctx, states_per_lane, max_cluster), "align_set_tuning")
+def align_set_tuning(ctx, states_per_lane: int = 0, cta_warps: int = 0, max_cluster: int = 0) -> None:
+    _check(lib().align_set_tuning(ctx, states_per_lane, cta_warps, max_cluster), "align_set_tuning")
+
+
+def align_probe_frame_latency(device: int, warps: int, ctas: int, frames: int) -> float:
+    """ns per frame of the null-work exchange pattern (see include/align.h)."""
+    ns = ctypes.c_double(0.0)
+    _check(lib().align_probe_frame_latency(device, warps, ctas, frames, ctypes.byref(ns)),
+           "align_probe_frame_latency")
+    return ns.value
 
 
 def align_validate(targets, C: int, blank: int, T: int) -> tuple[int, int]:
@@ -190,9 +223,9 @@ def align_validate(targets, C: int, blank: int, T: int) -> tuple[int, int]:
 
 
 def align_plan(T: int, C: int, L: int, budget: int = 0, flags: int = 0, states_per_lane: int = 0,
-               max_cluster: int = 0) -> dict:
+               cta_warps: int = 0, max_cluster: int = 0) -> dict:
     info = AlignPlanInfo()
-    _check(lib().align_plan(T, C, L, budget, flags, states_per_lane, max_cluster, ctypes.byref(info)),
+    _check(lib().align_plan(T, C, L, budget, flags, states_per_lane, cta_warps, max_cluster, ctypes.byref(info)),
            "align_plan")
     return {k: getattr(info, k) for k, _ in AlignPlanInfo._fields_ if k != "pad"}
 
@@ -214,12 +247,14 @@ class Aligner:
 
     def __init__(self, device: int = 0, batched: bool = False, bp_budget_bytes: int = 0,
                  staging_bytes: int = 0, stream=None, force_checkpoint: bool = False,
-                 wait_limit_ms: int = 0, max_inflight: int = 0, graphs: bool = True):
+                 wait_limit_ms: int = 0, max_inflight: int = 0, graphs: bool = True,
+                 test_stall: bool = False):
         import torch
         self.torch = torch
         self.device = device
         flags = (ALIGN_F_BATCHED if batched else 0) | (ALIGN_F_FORCE_CHECKPOINT if force_checkpoint else 0)
         flags |= 0 if graphs else ALIGN_F_NO_GRAPHS
+        flags |= ALIGN_F_TEST_STALL if test_stall else 0
         cfg = AlignConfig(device=device, max_inflight=max_inflight, bp_budget_bytes=bp_budget_bytes,
                           staging_bytes=staging_bytes,
                           cuda_stream=(stream.cuda_stream if stream is not None else None), flags=flags,
@@ -280,6 +315,28 @@ class Aligner:
         self._live[rid] = (log_probs, res)
         return res
 
+    def submit_batch(self, items, host: bool = False) -> list[Result]:
+        """items: sequence of (log_probs, targets, blank, out) with out = (path, scores, total, states)
+        tensors (device tensors, or host tensors when host=True). One C call for the whole batch."""
+        reqs, keep, results = [], [], []
+        for lp, tg, blank, out in items:
+            tg = _i32(tg)
+            path, scores, total, states = out
+            T, C = lp.shape
+            o = AlignOut(path.data_ptr(), scores.data_ptr(), total.data_ptr(),
+                         states.data_ptr() if states is not None else None)
+            reqs.append(AlignRequest(lp.data_ptr(), T, C, tg.ctypes.data, tg.size, blank,
+                                     ALIGN_REQ_HOST if host else 0, o))
+            keep.append((lp, tg))
+            results.append(Result(0, path, scores, total, states))
+        ids, st = align_submit_batch(self.ctx, reqs)
+        for r, rid, code, k in zip(results, ids, st, keep):
+            if code < 0:
+                raise AlignError(code, "align_submit_batch")
+            r.request_id = rid
+            self._live[rid] = (k, r)
+        return results
+
     def flush(self) -> None:
         align_flush(self.ctx)
 
@@ -305,5 +362,5 @@ class Aligner:
     def stats(self, reset: bool = False) -> dict:
         return align_get_stats(self.ctx, reset)
 
-    def set_tuning(self, states_per_lane: int = 0, max_cluster: int = 0) -> None:
-        align_set_tuning(self.ctx, states_per_lane, max_cluster)
+    def set_tuning(self, states_per_lane: int = 0, cta_warps: int = 0, max_cluster: int = 0) -> None:
+        align_set_tuning(self.ctx, states_per_lane, cta_warps, max_cluster)

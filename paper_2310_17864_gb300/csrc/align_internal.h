@@ -8,8 +8,9 @@ namespace gb300_align {
 
 // Kernel-shape choices (replaced by measurements through align_set_tuning).
 struct TuneTable {
-  int K = 4;             // states per lane for single-CTA teams
-  int max_warps = 32;    // warps per CTA
+  int K = 4;             // states per lane
+  int cta_warps = 4;     // warps per CTA before a team is split over a cluster
+  int max_warps = 16;    // hard limit of warps per CTA (the kernel is built for 512 threads)
   int max_cluster = 16;  // CTAs per cluster for long transcripts
 };
 TuneTable default_tune_table();
@@ -23,7 +24,10 @@ struct Plan {
   int nck = 0;                // number of checkpoints (segments)
   int ck_stride = 0;          // floats per checkpoint row
   uint64_t ckpt_bytes = 0;    // nck * ck_stride * 4
-  uint64_t seg_bp_bytes = 0;  // backpointers of one segment
+  uint64_t seg_bp_bytes = 0;  // backpointers + anchor rows of one segment
+  int zstride = 0;            // bytes per anchor row (S rounded up to 16)
+  uint64_t z_off = 0;         // offset of the anchor rows inside the full-mode allocation
+  uint64_t seg_z_off = 0;     // offset of the anchor rows inside the segment buffer
 };
 
 // Step A1: 0, ALIGN_E_INVAL, ALIGN_E_TARGET or ALIGN_E_INFEASIBLE; *repeats = R.

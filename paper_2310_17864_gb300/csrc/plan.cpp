@@ -34,42 +34,47 @@ int make_plan(const TuneTable& tune, int64_t T, int64_t C, int64_t L, uint64_t b
               Plan* out) {
   Plan p{};
   const int64_t S = 2 * L + 1;
-  // Shape: one CTA of up to max_warps warps, else a cluster of CTAs.
-  // The K = 16 kernel keeps 2x more state in registers and is built for 512 threads.
+  // Shape: one CTA of up to cta_warps warps, else a cluster of CTAs of at most
+  // cta_warps warps (portable sizes first), else wider CTAs and larger K.
   const int K = tune.K;
-  const auto warp_cap = [&](int k) { return k == 16 ? std::min(16, tune.max_warps) : tune.max_warps; };
-  const uint64_t G1 = ceil_div(static_cast<uint64_t>(S), 32ull * K);
-  if (G1 <= static_cast<uint64_t>(warp_cap(K))) {
-    p.shape = LaunchShape{K, static_cast<int>(G1), 1};
-  } else {
-    // Prefer portable clusters (<= 8 CTAs), then larger K, then non-portable sizes.
-    bool found = false;
-    const int portable = std::min(8, tune.max_cluster);
-    const std::pair<int, int> tries[] = {{K, portable}, {8, portable}, {K, tune.max_cluster},
-                                         {8, tune.max_cluster}, {16, tune.max_cluster}};
-    for (auto [k, cmax] : tries) {
-      if (k < K) continue;
-      const int wmax = warp_cap(k);
-      const uint64_t G = ceil_div(static_cast<uint64_t>(S), 32ull * k);
-      const uint64_t ncta = ceil_div(G, static_cast<uint64_t>(wmax));
-      if (ncta <= static_cast<uint64_t>(cmax)) {
-        p.shape = LaunchShape{k, static_cast<int>(ceil_div(G, ncta)), static_cast<int>(ncta)};
-        found = true;
-        break;
-      }
+  const auto warp_cap = [&](int) { return std::min(16, tune.max_warps); };
+  const int portable = std::min(8, tune.max_cluster);
+  struct Try {
+    int k, wcap, cmax;
+  };
+  const int cw = std::max(1, std::min(tune.cta_warps, warp_cap(K)));
+  const Try tries[] = {{K, cw, portable},          {K, cw, tune.max_cluster}, {K, warp_cap(K), portable},
+                       {8, warp_cap(8), portable}, {K, warp_cap(K), tune.max_cluster},
+                       {8, warp_cap(8), tune.max_cluster}, {16, warp_cap(16), tune.max_cluster}};
+  bool found = false;
+  for (const Try& tr : tries) {
+    if (tr.k < K) continue;
+    const uint64_t G = ceil_div(static_cast<uint64_t>(S), 32ull * tr.k);
+    const uint64_t ncta = ceil_div(G, static_cast<uint64_t>(tr.wcap));
+    if (ncta <= static_cast<uint64_t>(std::max(1, tr.cmax))) {
+      p.shape = LaunchShape{tr.k, static_cast<int>(ceil_div(G, ncta)), static_cast<int>(ncta)};
+      found = true;
+      break;
     }
-    if (!found) return ALIGN_E_TOO_LARGE;
   }
-  // Emission staging: stages of about 8 KB (16 frames of a 32-class row).
-  p.frames_per_stage = static_cast<int>(std::clamp<int64_t>(8192 / (4 * C), 1, 16));
+  if (!found) return ALIGN_E_TOO_LARGE;
+  // Emission staging: stages of 4 KB (32 frames of a 32-class row), up to 8 KB
+  // for wide rows.
+  const int64_t stage_budget = p.shape.warps >= 2 ? 8192 : 4096;
+  p.frames_per_stage = static_cast<int>(std::clamp<int64_t>(stage_budget / (4 * C), 1, 32));
   const uint64_t warps = static_cast<uint64_t>(p.shape.warps) * p.shape.ncta;
   const uint64_t row_bytes = warps * bp_words(p.shape.K) * 4ull;
-  p.bp_bytes = row_bytes * static_cast<uint64_t>(std::max<int64_t>(T - 1, 0));
+  // Anchor rows: one row of S bytes (rounded to 16) per kAnchorD frames.
+  p.zstride = static_cast<int>(round_up(static_cast<uint64_t>(S), 16));
+  const auto zrows = [](int64_t frames) { return static_cast<uint64_t>((frames + kAnchorD - 1) / kAnchorD); };
+  p.z_off = round_up(row_bytes * static_cast<uint64_t>(std::max<int64_t>(T - 1, 0)), 256);
+  p.bp_bytes = p.z_off + round_up(zrows(T - 1) * p.zstride, 256);
   p.ck_every = std::max(1, static_cast<int>(std::ceil(std::sqrt(static_cast<double>(T)))));
   p.nck = static_cast<int>((T - 1) / p.ck_every + 1);
   p.ck_stride = static_cast<int>(round_up(static_cast<uint64_t>(S), 4));
   p.ckpt_bytes = round_up(static_cast<uint64_t>(p.nck) * p.ck_stride * 4ull, 256);
-  p.seg_bp_bytes = row_bytes * static_cast<uint64_t>(p.ck_every);
+  p.seg_z_off = round_up(row_bytes * static_cast<uint64_t>(p.ck_every), 256);
+  p.seg_bp_bytes = p.seg_z_off + round_up(zrows(p.ck_every) * p.zstride, 256);
   p.checkpointed = force_checkpoint || p.bp_bytes > budget;
   if (p.checkpointed && p.ckpt_bytes + p.seg_bp_bytes > budget) return ALIGN_E_TOO_LARGE;
   *out = p;
@@ -103,10 +108,11 @@ int align_validate(const int32_t* targets, int64_t L, int64_t C, int32_t blank, 
 }
 
 int align_plan(int64_t T, int64_t C, int64_t L, uint64_t bp_budget_bytes, uint32_t flags, int32_t states_per_lane,
-               int32_t max_cluster, align_plan_info* out) {
+               int32_t cta_warps, int32_t max_cluster, align_plan_info* out) {
   if (!out || T < 1 || C < 2 || L < 0) return ALIGN_E_INVAL;
   TuneTable tune = default_tune_table();
   if (states_per_lane) tune.K = states_per_lane;
+  if (cta_warps) tune.cta_warps = cta_warps;
   if (max_cluster) tune.max_cluster = max_cluster;
   Plan p{};
   const int rc = make_plan(tune, T, C, L, bp_budget_bytes ? bp_budget_bytes : (1ull << 30),

@@ -115,6 +115,14 @@ struct Alloc {
   bool live = false;
 };
 
+// Metadata block per request in device memory: status, state_io, final2[2].
+struct MetaBlock {
+  int32_t status;
+  int32_t state_io;
+  float final2[2];
+};
+static_assert(sizeof(MetaBlock) == 16, "meta");
+
 enum class ReqState { Queued, Launched, Done };
 
 struct Request {
@@ -140,8 +148,9 @@ struct Batch {
   Alloc meta;      // device: descriptors + per-request metadata + targets
   Alloc pinned;    // host pinned: upload image + status download
   std::vector<uint64_t> reqs;
-  int32_t* h_status = nullptr;  // pinned, one per request
+  MetaBlock* h_meta = nullptr;  // pinned copy of the requests' metadata blocks
   bool finished = false;
+  std::vector<cudaEvent_t> events;     // pooled events used by this batch
 };
 
 }  // namespace
@@ -152,6 +161,7 @@ struct align_ctx {
   bool own_main = false;
   std::vector<cudaStream_t> workers;
   std::vector<cudaEvent_t> fork_events;
+  std::vector<cudaEvent_t> event_pool;  // reusable events for batch joins and completion
   int next_worker = 0;
   uint32_t flags = 0;
   uint64_t wait_limit_ns = 2000000000ull;
@@ -182,13 +192,17 @@ namespace {
 
 uint64_t inflight_count(const align_ctx* ctx) { return ctx->reqs.size(); }
 
-// Metadata block per request in device memory: status, state_io, final2[2].
-struct MetaBlock {
-  int32_t status;
-  int32_t state_io;
-  float final2[2];
-};
-static_assert(sizeof(MetaBlock) == 16, "meta");
+
+cudaEvent_t take_event(align_ctx* ctx) {
+  if (!ctx->event_pool.empty()) {
+    cudaEvent_t e = ctx->event_pool.back();
+    ctx->event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+  return e;
+}
 
 int finish_batch(align_ctx* ctx, Batch& b) {
   for (size_t i = 0; i < b.reqs.size(); ++i) {
@@ -196,7 +210,7 @@ int finish_batch(align_ctx* ctx, Batch& b) {
     if (it == ctx->reqs.end()) continue;
     Request& r = it->second;
     r.state = ReqState::Done;
-    r.status = b.h_status[i];
+    r.status = b.h_meta[i].status;
     if (r.status == ALIGN_PENDING) r.status = ALIGN_E_TIMEOUT;
     if (r.bp.live) ctx->bp_arena.release(r.bp.off, r.bp.bytes), r.bp.live = false;
     if (r.stage.live) ctx->stage_arena.release(r.stage.off, r.stage.bytes), r.stage.live = false;
@@ -217,7 +231,7 @@ int reap(align_ctx* ctx) {
     cudaError_t q = cudaEventQuery(b.done);
     if (q == cudaSuccess) {
       finish_batch(ctx, b);
-      cudaEventDestroy(b.done);
+      for (cudaEvent_t e : b.events) ctx->event_pool.push_back(e);
       it = ctx->batches.erase(it);
     } else if (q == cudaErrorNotReady) {
       ++it;
@@ -309,8 +323,8 @@ int launch_queued(align_ctx* ctx) {
   const uint64_t off_metas = round_up(njobs * sizeof(FwdJob), kAlign);
   const uint64_t off_tgts = round_up(off_metas + take.size() * sizeof(MetaBlock), kAlign);
   const uint64_t up_bytes = round_up(off_tgts + tgt_words * 4, kAlign);
-  const uint64_t off_status = up_bytes;  // pinned only: status download
-  const uint64_t pin_bytes = up_bytes + round_up(take.size() * 4, kAlign);
+  const uint64_t off_status = up_bytes;  // pinned only: metadata download (status of every request)
+  const uint64_t pin_bytes = up_bytes + round_up(take.size() * sizeof(MetaBlock), kAlign);
 
   Batch b;
   b.id = ctx->next_batch++;
@@ -343,7 +357,7 @@ int launch_queued(align_ctx* ctx) {
   const FwdJob* djobs = reinterpret_cast<const FwdJob*>(d + off_jobs);
   MetaBlock* dmeta = reinterpret_cast<MetaBlock*>(d + off_metas);
   const int32_t* dtgt = reinterpret_cast<const int32_t*>(d + off_tgts);
-  b.h_status = reinterpret_cast<int32_t*>(h + off_status);
+  b.h_meta = reinterpret_cast<MetaBlock*>(h + off_status);
 
   // Per-request metadata, targets and device views of inputs / outputs.
   std::vector<const int32_t*> req_tgt(take.size());
@@ -359,7 +373,7 @@ int launch_queued(align_ctx* ctx) {
     hmeta[i].status = ALIGN_PENDING;
     hmeta[i].state_io = 0;
     hmeta[i].final2[0] = hmeta[i].final2[1] = -INFINITY;
-    b.h_status[i] = ALIGN_PENDING;
+    b.h_meta[i].status = ALIGN_PENDING;
     if (r.L) std::memcpy(htgt + tw, r.targets.data(), static_cast<size_t>(r.L) * 4);
     req_tgt[i] = dtgt + tw;
     tw += round_up(static_cast<uint64_t>(std::max<int64_t>(r.L, 1)), 4);
@@ -394,7 +408,7 @@ int launch_queued(align_ctx* ctx) {
     j.blank = r.blank;
     j.L = static_cast<int32_t>(r.L);
     j.S = static_cast<int32_t>(2 * r.L + 1);
-    j.flags = rows_bulk_ok(j.lp, r.C) ? kJobBulkRows : 0u;
+    j.flags = (rows_bulk_ok(j.lp, r.C) ? kJobBulkRows : 0u) | ((ctx->flags & ALIGN_F_TEST_STALL) ? kJobTestStall : 0u);
     return j;
   };
 
@@ -421,6 +435,8 @@ int launch_queued(align_ctx* ctx) {
       const Request& r = *take[static_cast<size_t>(i)];
       FwdJob j = base_job(static_cast<size_t>(i));
       j.bp = reinterpret_cast<uint32_t*>(ctx->d_bp + r.bp.off);
+      j.ztab = reinterpret_cast<uint8_t*>(ctx->d_bp + r.bp.off + r.plan.z_off);
+      j.zstride = r.plan.zstride;
       j.t_begin = 0;
       j.t_end = j.T;
       j.bp_rows = std::max(j.T - 1, 0);
@@ -454,6 +470,8 @@ int launch_queued(align_ctx* ctx) {
       s.final2 = nullptr;
       s.bp = seg;
       s.bp_rows = e - t0;
+      s.ztab = reinterpret_cast<uint8_t*>(ctx->d_bp + r.bp.off + p.ckpt_bytes + p.seg_z_off);
+      s.zstride = p.zstride;
       s.flags |= kJobChase;
       hjobs[jn++] = s;
     }
@@ -480,8 +498,8 @@ int launch_queued(align_ctx* ctx) {
                          cudaMemcpyHostToDevice, s0));
     }
   }
-  cudaEvent_t ready;
-  CU(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
+  cudaEvent_t ready = take_event(ctx);
+  b.events.push_back(ready);
   CU(cudaEventRecord(ready, s0));
   size_t lane_i = 0;
   for (const GroupLaunch& gl : glaunch) {
@@ -511,17 +529,14 @@ int launch_queued(align_ctx* ctx) {
     }
   }
   // Join, download statuses and host outputs, record completion.
-  cudaEvent_t joined[64];
-  int nj = 0;
   for (cudaStream_t s : used) {
     if (s == s0) continue;
-    CU(cudaEventCreateWithFlags(&joined[nj], cudaEventDisableTiming));
-    CU(cudaEventRecord(joined[nj], s));
-    CU(cudaStreamWaitEvent(s0, joined[nj], 0));
-    ++nj;
+    cudaEvent_t j = take_event(ctx);
+    b.events.push_back(j);
+    CU(cudaEventRecord(j, s));
+    CU(cudaStreamWaitEvent(s0, j, 0));
   }
-  for (size_t i = 0; i < take.size(); ++i)
-    CU(cudaMemcpyAsync(b.h_status + i, &dmeta[i].status, 4, cudaMemcpyDeviceToHost, s0));
+  CU(cudaMemcpyAsync(b.h_meta, dmeta, take.size() * sizeof(MetaBlock), cudaMemcpyDeviceToHost, s0));
   for (size_t i = 0; i < take.size(); ++i) {
     Request& r = *take[i];
     if (!r.host_io) continue;
@@ -531,10 +546,9 @@ int launch_queued(align_ctx* ctx) {
     CU(cudaMemcpyAsync(r.out.total, req_out[i].total, 4, cudaMemcpyDeviceToHost, s0));
     if (r.out.states) CU(cudaMemcpyAsync(r.out.states, req_out[i].states, T * 4, cudaMemcpyDeviceToHost, s0));
   }
-  CU(cudaEventCreateWithFlags(&b.done, cudaEventDisableTiming));
+  b.done = take_event(ctx);
+  b.events.push_back(b.done);
   CU(cudaEventRecord(b.done, s0));
-  cudaEventDestroy(ready);
-  for (int k = 0; k < nj; ++k) cudaEventDestroy(joined[k]);
   ctx->batches.emplace(b.id, b);
   return ALIGN_OK;
 }
@@ -553,7 +567,8 @@ int submit_common(align_ctx* ctx, const float* lp, int64_t T, int64_t C, const i
                   int32_t blank, align_out out, uint64_t* request_id, bool host_io) {
   if (!ctx || !lp || !request_id || !out.path || !out.scores || !out.total) return ALIGN_E_INVAL;
   if (L > 0 && !targets) return ALIGN_E_INVAL;
-  if (T > INT32_MAX / 2 || L > INT32_MAX / 4) return ALIGN_E_TOO_LARGE;
+  // Frame tags in the ring words have 24 bits; 2^24 frames of 20 ms are 93 hours.
+  if (T >= (1ll << kTagBits) || L > INT32_MAX / 4) return ALIGN_E_TOO_LARGE;
   int64_t R = 0;
   int rc = validate_request(targets, L, C, blank, T, &R);
   if (rc != ALIGN_OK) return rc;
@@ -654,7 +669,9 @@ int align_destroy(align_ctx* ctx) {
   if (!ctx) return ALIGN_OK;
   cudaSetDevice(ctx->device);
   for (auto& kv : ctx->batches) cudaEventSynchronize(kv.second.done);
-  for (auto& kv : ctx->batches) cudaEventDestroy(kv.second.done);
+  for (auto& kv : ctx->batches)
+    for (cudaEvent_t e : kv.second.events) cudaEventDestroy(e);
+  for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
   for (cudaStream_t s : ctx->workers) {
     cudaStreamSynchronize(s);
     cudaStreamDestroy(s);
@@ -682,6 +699,30 @@ int align_submit_host(align_ctx* ctx, const float* log_probs, int64_t T, int64_t
                       int64_t L, int32_t blank, align_out out, uint64_t* request_id) {
   if (ctx) cudaSetDevice(ctx->device);
   return submit_common(ctx, log_probs, T, C, targets, L, blank, out, request_id, true);
+}
+
+int align_submit_batch(align_ctx* ctx, int32_t n, const align_request* reqs, uint64_t* request_ids,
+                       int32_t* submit_status) {
+  if (!ctx || n < 0 || (n > 0 && (!reqs || !request_ids))) return ALIGN_E_INVAL;
+  cudaSetDevice(ctx->device);
+  // Queue every request without launching, then launch once: one batch.
+  const uint32_t saved = ctx->flags;
+  ctx->flags |= ALIGN_F_BATCHED;
+  int first_err = ALIGN_OK;
+  for (int32_t i = 0; i < n; ++i) {
+    const align_request& q = reqs[i];
+    int rc = submit_common(ctx, q.log_probs, q.T, q.C, q.targets, q.L, q.blank, q.out, &request_ids[i],
+                           (q.flags & ALIGN_REQ_HOST) != 0);
+    if (rc != ALIGN_OK) request_ids[i] = 0;
+    if (submit_status) submit_status[i] = rc;
+    if (rc != ALIGN_OK && first_err == ALIGN_OK) first_err = rc;
+  }
+  ctx->flags = saved;
+  if (!(saved & ALIGN_F_BATCHED)) {
+    const int rc = pump(ctx, true);
+    if (rc != ALIGN_OK) return rc;
+  }
+  return first_err;
 }
 
 int align_flush(align_ctx* ctx) {
@@ -738,6 +779,24 @@ int align_poll(align_ctx* ctx, uint64_t request_id, int32_t timeout_ms, int32_t*
   }
 }
 
+int align_probe_frame_latency(int32_t device, int32_t warps, int32_t ctas, int32_t frames, double* ns_per_frame) {
+  if (!ns_per_frame || warps < 1 || warps > 32 || ctas < 1 || ctas > 16 || frames < 2) return ALIGN_E_INVAL;
+  CU(cudaSetDevice(device));
+  uint64_t* d = nullptr;
+  CU(cudaMalloc(&d, 3 * sizeof(uint64_t)));
+  uint64_t h[3] = {0, 0, 0};
+  cudaError_t e = static_cast<cudaError_t>(launch_frame_probe(warps, ctas, frames, 2000000000ull, d, nullptr));
+  if (e == cudaSuccess) e = cudaMemcpy(h, d, sizeof(h), cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  if (e != cudaSuccess) {
+    set_error("frame probe", e);
+    return ALIGN_E_CUDA;
+  }
+  if (h[1]) return ALIGN_E_TIMEOUT;
+  *ns_per_frame = static_cast<double>(h[0]) / static_cast<double>(frames);
+  return ALIGN_OK;
+}
+
 int align_join(align_ctx* ctx, void* stream) {
   if (!ctx) return ALIGN_E_INVAL;
   cudaSetDevice(ctx->device);
@@ -777,13 +836,14 @@ const char* align_status_string(int32_t code) {
 
 const char* align_last_error(void) { return g_last_error; }
 
-int align_set_tuning(align_ctx* ctx, int32_t states_per_lane, int32_t max_cluster) {
+int align_set_tuning(align_ctx* ctx, int32_t states_per_lane, int32_t cta_warps, int32_t max_cluster) {
   if (!ctx) return ALIGN_E_INVAL;
   if (states_per_lane && states_per_lane != 2 && states_per_lane != 4 && states_per_lane != 8 &&
       states_per_lane != 16)
     return ALIGN_E_INVAL;
-  if (max_cluster < 0 || max_cluster > 16) return ALIGN_E_INVAL;
+  if (cta_warps < 0 || cta_warps > 32 || max_cluster < 0 || max_cluster > 16) return ALIGN_E_INVAL;
   if (states_per_lane) ctx->tune.K = states_per_lane;
+  if (cta_warps) ctx->tune.cta_warps = cta_warps;
   if (max_cluster) ctx->tune.max_cluster = max_cluster;
   return ALIGN_OK;
 }

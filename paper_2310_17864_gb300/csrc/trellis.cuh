@@ -22,18 +22,35 @@
 //                               32Kg + Kl + 2i + 1
 // at bp[(g * bp_rows + r) * NW]. The predecessor is s-2 if the skip bit is
 // set, else s-1 if the advance bit is set, else s.
+//
+// Anchors (for a parallel backtrack): frames t_begin + m*D (D = kAnchorD) are
+// anchor frames. Along the forward pass every state also carries anchor(s),
+// the state at the last anchor frame on its best path (selected with the same
+// predicates as the max). At the end of window m (frame t_begin + (m+1)*D, or
+// the last frame) row m of ztab stores s - anchor(s) in [0, 2D] as a byte;
+// the anchors are then reset to s. The backtrack hops from window to window
+// through these rows, then walks every window's 32 frames in parallel.
+//
+// Ring word (one per frame and warp boundary): bits 63..40 frame tag
+// (t + 1 mod 2^24), bits 39..32 anchor offset of the sent state, bits 31..0
+// alpha as FP32 bits.
 #pragma once
 #include <cstdint>
 
 namespace gb300_align {
 
-constexpr int kStages = 4;            // emission ring stages per CTA
+constexpr int kStages = 10;           // emission ring stages per CTA
+constexpr int kLead = 4;              // stages in flight ahead of the consumer
 constexpr int kBtWindow = 32;         // frames per backtrack window
+constexpr int kAnchorD = 32;          // frames between anchor rows (== kBtWindow)
+constexpr int kHopBatch = 8;          // anchor rows fetched per batch while hopping back
+constexpr int kTagBits = 24;          // frame tag bits in a ring word
 
 // Job flags.
 constexpr uint32_t kJobWriteFinal = 1u;  // pick the final state, write total/status/state_io
 constexpr uint32_t kJobChase = 2u;       // walk the backpointers from state_io and write outputs
 constexpr uint32_t kJobBulkRows = 4u;    // emission rows may be staged with cp.async.bulk
+constexpr uint32_t kJobTestStall = 8u;   // test hook: warp 0 of the team never sends (waits run out)
 
 struct alignas(16) FwdJob {
   const float* lp;         // [T][C] row-major FP32
@@ -56,11 +73,14 @@ struct alignas(16) FwdJob {
   int32_t ck_every;        // checkpoint interval in frames (0: none)
   int32_t ck_stride;       // floats between checkpoint rows
   uint32_t flags;
-  int32_t pad0;
+  int32_t zstride;         // bytes per anchor row (multiple of 16, >= S)
+  uint8_t* ztab;           // anchor rows: row m holds s - anchor(s) at the end of window m
+  void* pad1;
 };
 
 struct FwdParams {
-  int32_t rb;              // boundary ring slots per warp (power of two, >= 4*F + 2)
+  int32_t rb;              // boundary ring slots per warp (power of two, >= 2*block + 2)
+  int32_t block;           // frames per ring wait / progress publication (<= 32)
   int32_t frames_per_stage;
   int32_t stage_bytes;     // bytes per emission stage (16-byte multiple)
   int32_t off_ring;        // shared-memory offsets
@@ -96,6 +116,10 @@ int smem_bytes(const LaunchShape& shape, const FwdParams& p);
 // (or CTA) per job, on the given stream. Returns a cudaError_t value.
 int launch_trellis(const LaunchShape& shape, const FwdParams& p, const FwdJob* d_jobs, int njobs,
                    void* stream);
+
+// Null-work frame-latency probe (warp-scope chain of one frame); d_out[0] =
+// ns for `frames` frames measured by CTA 0, d_out[1] = 0.
+int launch_frame_probe(int warps, int ncta, int frames, uint64_t limit_ns, uint64_t* d_out, void* stream);
 
 // Largest dynamic shared memory the kernel for this shape may use.
 int max_smem_optin(int device);

@@ -20,6 +20,7 @@
 // ring filled by cp.async.bulk (TMA bulk copies) completing on mbarriers.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 
@@ -57,9 +58,6 @@ __device__ __forceinline__ uint32_t mapa_rank(uint32_t addr, uint32_t rank) {
   asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
   return r;
 }
-__device__ __forceinline__ void st_remote_u64(uint32_t addr, uint64_t v) {
-  asm volatile("st.relaxed.cluster.shared::cluster.u64 [%0], %1;" ::"r"(addr), "l"(v) : "memory");
-}
 __device__ __forceinline__ void st_remote_u32(uint32_t addr, uint32_t v) {
   asm volatile("st.relaxed.cluster.shared::cluster.u32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
 }
@@ -77,11 +75,12 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t by
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
                : "memory");
 }
+// Non-blocking test of an mbarrier phase (polling; never suspends the thread).
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
       "selp.u32 %0, 1, 0, p;\n\t}"
       : "=r"(ok)
       : "r"(smem_addr(bar)), "r"(parity)
@@ -107,10 +106,11 @@ struct SmemHead {
   uint64_t full[kStages];   // emission stage filled
   uint64_t empty[kStages];  // emission stage released by every warp
   int32_t abort;            // set by any thread of this CTA whose wait hit the limit
-  uint32_t prog;            // boundary frames consumed by the next CTA of the cluster (remote writes)
-  int32_t pad[14];
+  uint32_t unused;
+  uint64_t sink;            // scratch slot written by the last warp of the team
+  int32_t pad[(256 - 16 * kStages - 16) / 4];
 };
-static_assert(sizeof(SmemHead) == 128, "head size");
+static_assert(sizeof(SmemHead) == 256, "head size");
 
 // Bounded wait on an mbarrier phase, done by one lane. Returns false on
 // timeout (and raises the CTA abort flag) or when another warp aborted.
@@ -139,27 +139,6 @@ __device__ __forceinline__ bool warp_wait_phase(uint64_t* bar, uint32_t parity, 
   return ok != 0;
 }
 
-// Receive alpha_{t}(first state - 1) of this warp from its left neighbour's
-// tagged ring slot (tag = frame + 1, value = FP32 bits). One lane.
-__device__ __forceinline__ float ring_recv(const uint64_t* ring, int t, int rb_mask, volatile int32_t* abort,
-                                           uint64_t limit, bool& ok) {
-  const volatile uint64_t* p = ring + (t & rb_mask);
-  const uint32_t want = static_cast<uint32_t>(t + 1);
-  uint64_t v = *p;
-  if (static_cast<uint32_t>(v >> 32) != want) {
-    const uint64_t t0 = gtimer();
-    for (;;) {
-      v = *p;
-      if (static_cast<uint32_t>(v >> 32) == want) break;
-      if (*abort || gtimer() - t0 > limit) {
-        *abort = 1;
-        ok = false;
-        return -INFINITY;
-      }
-    }
-  }
-  return __uint_as_float(static_cast<uint32_t>(v));
-}
 
 template <int K>
 __device__ __forceinline__ void store_bp_words(uint32_t* dst, const uint32_t (&adv)[K], const uint32_t (&skp)[K / 2]) {
@@ -182,12 +161,103 @@ __device__ __forceinline__ void store_bp_words(uint32_t* dst, const uint32_t (&a
   }
 }
 
+// Slow path of a block read: lane i waits (bounded) until its slot carries
+// the tag of frame t0 + i; returns the value bits. Uniform across the warp.
+__device__ __noinline__ uint64_t ring_block_spin(const volatile uint64_t* ring, int t0, int nb, int rb_mask,
+                                                 int lane, volatile int32_t* abort, uint64_t limit) {
+  const uint64_t t_start = gtimer();
+  const int f = t0 + (lane < nb ? lane : 0);
+  const uint32_t want = (static_cast<uint32_t>(f) + 1u) & ((1u << kTagBits) - 1u);
+  const volatile uint64_t* p = ring + (f & rb_mask);
+  for (;;) {
+    const uint64_t v = *p;
+    const bool mine = static_cast<uint32_t>(v >> 40) == want;  // tag field of the ring word
+    if (__all_sync(kFull, mine)) return v;
+    const bool give_up = (*abort != 0) || (gtimer() - t_start > limit);
+    if (__any_sync(kFull, give_up)) {
+      if (lane == 0) *abort = 1;
+      return static_cast<uint64_t>(__float_as_uint(-INFINITY));
+    }
+  }
+}
+
+// Slow path of the cross-CTA flow control: wait until the next CTA has
+// consumed frame `need` (its published progress exceeds it).
+__device__ __noinline__ uint32_t prog_spin(const volatile uint32_t* prog, int need, volatile int32_t* abort,
+                                           uint64_t limit) {
+  const uint64_t t0 = gtimer();
+  for (;;) {
+    const uint32_t v = *prog;
+    if (static_cast<int>(v) > need) return v;
+    if (*abort || gtimer() - t0 > limit) {
+      *abort = 1;
+      return v;
+    }
+  }
+}
+
+// Stores executed by one lane, written as predicated PTX so the frame loop has
+// no lane-dependent branch.
+__device__ __forceinline__ void st_global_v4_if(uint32_t* p, uint32_t x, uint32_t y, uint32_t z, uint32_t w,
+                                                bool pred) {
+  asm volatile(
+      "{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %5, 0;\n\t@q st.global.v4.u32 [%0], {%1, %2, %3, %4};\n\t}" ::"l"(p),
+      "r"(x), "r"(y), "r"(z), "r"(w), "r"(static_cast<uint32_t>(pred))
+      : "memory");
+}
+__device__ __forceinline__ void st_cluster_u64_if(uint32_t addr, uint64_t v, bool pred) {
+  asm volatile(
+      "{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t@q st.relaxed.cluster.shared::cluster.u64 [%0], %1;\n\t}" ::"r"(
+          addr),
+      "l"(v), "r"(static_cast<uint32_t>(pred))
+      : "memory");
+}
+// All backpointer words of one warp and frame, stored by lane 0 under a single
+// predicate (one setp per frame).
+template <int K>
+__device__ __forceinline__ void store_bp_words_if(uint32_t* dst, const uint32_t (&adv)[K],
+                                                  const uint32_t (&skp)[K / 2], bool pred) {
+  const uint32_t pr = static_cast<uint32_t>(pred);
+  if constexpr (K == 2) {  // 3 words: 4-byte aligned only
+    asm volatile(
+        "{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %4, 0;\n\t"
+        "@q st.global.u32 [%0], %1;\n\t@q st.global.u32 [%0+4], %2;\n\t@q st.global.u32 [%0+8], %3;\n\t}" ::"l"(dst),
+        "r"(adv[0]), "r"(adv[1]), "r"(skp[0]), "r"(pr)
+        : "memory");
+  } else if constexpr (K == 4) {  // 6 words: 8-byte aligned
+    asm volatile(
+        "{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %7, 0;\n\t"
+        "@q st.global.v2.u32 [%0], {%1, %2};\n\t@q st.global.v2.u32 [%0+8], {%3, %4};\n\t"
+        "@q st.global.v2.u32 [%0+16], {%5, %6};\n\t}" ::"l"(dst),
+        "r"(adv[0]), "r"(adv[1]), "r"(adv[2]), "r"(adv[3]), "r"(skp[0]), "r"(skp[1]), "r"(pr)
+        : "memory");
+  } else if constexpr (K == 8) {  // 12 words: 16-byte aligned
+    asm volatile(
+        "{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %13, 0;\n\t"
+        "@q st.global.v4.u32 [%0], {%1, %2, %3, %4};\n\t@q st.global.v4.u32 [%0+16], {%5, %6, %7, %8};\n\t"
+        "@q st.global.v4.u32 [%0+32], {%9, %10, %11, %12};\n\t}" ::"l"(dst),
+        "r"(adv[0]), "r"(adv[1]), "r"(adv[2]), "r"(adv[3]), "r"(adv[4]), "r"(adv[5]), "r"(adv[6]), "r"(adv[7]),
+        "r"(skp[0]), "r"(skp[1]), "r"(skp[2]), "r"(skp[3]), "r"(pr)
+        : "memory");
+  } else {  // K == 16: 24 words
+    constexpr int NW = bp_words(K);
+    uint32_t w[NW];
+#pragma unroll
+    for (int j = 0; j < K; ++j) w[j] = adv[j];
+#pragma unroll
+    for (int i = 0; i < K / 2; ++i) w[K + i] = skp[i];
+#pragma unroll
+    for (int i = 0; i < NW; i += 4) st_global_v4_if(dst + i, w[i], w[i + 1], w[i + 2], w[i + 3], pred);
+  }
+}
+
 // ------------------------------------------------------------------ kernel --
 template <int K>
-__global__ void __launch_bounds__(K <= 8 ? 1024 : 512)
+__global__ void __launch_bounds__(512)
     trellis_kernel(const FwdJob* __restrict__ jobs, const FwdParams P) {
   static_assert(K % 2 == 0 && K >= 2 && K <= 16, "K must be even, 2..16");
   constexpr int NW = bp_words(K);
+  constexpr int GS = 32 * K;  // states per warp
   extern __shared__ __align__(128) unsigned char smem[];
   SmemHead* head = reinterpret_cast<SmemHead*>(smem);
   uint64_t* ring = reinterpret_cast<uint64_t*>(smem + P.off_ring);
@@ -200,7 +270,7 @@ __global__ void __launch_bounds__(K <= 8 ? 1024 : 512)
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
   const FwdJob& J = jobs[blockIdx.x / ncta];
-  const int g = static_cast<int>(crank) * W + warp;   // warp index in the team
+  const int g = static_cast<int>(crank) * W + warp;  // warp index in the team
   const int S = J.S, C = J.C, blank = J.blank;
   const int t_begin = J.t_begin, t_end = J.t_end;
   const int s0 = (g * 32 + lane) * K;               // first state of this lane
@@ -224,7 +294,6 @@ __global__ void __launch_bounds__(K <= 8 ? 1024 : 512)
       mbar_init(&head->empty[st], static_cast<uint32_t>(W));
     }
     head->abort = 0;
-    head->prog = static_cast<uint32_t>(t_begin);  // no slot holds a frame before t_begin
     fence_barrier_init();
   }
   __syncthreads();
@@ -267,16 +336,17 @@ __global__ void __launch_bounds__(K <= 8 ? 1024 : 512)
     }
   };
   if (warp == 0) {
-    for (int c = 0; c < min(kStages - 1, nchunks); ++c) issue_chunk(c);
-    issued = min(kStages - 1, nchunks);
+    for (int c = 0; c < min(kLead, nchunks); ++c) issue_chunk(c);
+    issued = min(kLead, nchunks);
   }
 
   // ---- frame t_begin: initialisation ----
   float a[K];
+  int A[K];  // anchors: state at the last anchor frame on the best path to each state
   int chunk = 0;
   bool ok = warp_wait_phase(&head->full[0], 0, abort, limit, lane);
-  const float* row = reinterpret_cast<const float*>(stages);
   if (ok) {
+    const float* row = reinterpret_cast<const float*>(stages);
     if (J.alpha_in == nullptr) {
       const float eb = row[blank];
 #pragma unroll
@@ -295,118 +365,205 @@ __global__ void __launch_bounds__(K <= 8 ? 1024 : 512)
 #pragma unroll
     for (int j = 0; j < K; ++j) a[j] = -INFINITY;
   }
+#pragma unroll
+  for (int j = 0; j < K; ++j) A[j] = s0 + j;
 
+  // Ring endpoints. Each warp receives alpha(first state - 1) of frame t-1
+  // from its own ring (written by the previous warp of the team, in this CTA
+  // or over DSMEM from the previous CTA) and sends alpha(last state) of
+  // frame t to the next warp's ring; the last warp of the team writes a sink.
+  // Frames are processed in blocks of up to P.block frames: a receiver waits
+  // once per block (lane i holds the word of frame t-1+i), publishes its
+  // progress once per block, and a sender checks that progress once per block
+  // before reusing ring slots. Lane 0 / lane 31 stores are predicated PTX, so
+  // inside a block the only branch is the loop's own.
+  uint32_t* prog_w = reinterpret_cast<uint32_t*>(smem + sizeof(SmemHead));  // [32]: progress of my consumer
   const bool recv_left = (g > 0);
   const bool send_local = warp < W - 1;
   const bool send_remote = (warp == W - 1) && (crank + 1 < ncta);
+  const bool has_next = send_local || send_remote;
+  if (threadIdx.x < 32) prog_w[threadIdx.x] = static_cast<uint32_t>(t_begin);
+  __syncthreads();
+  if (ncta > 1) cluster_sync();  // progress words initialised before any remote publish
+  const uint32_t send_base = send_local    ? smem_addr(ring + (warp + 1) * P.rb)
+                             : send_remote ? mapa_rank(smem_addr(ring), crank + 1)
+                                           : smem_addr(&head->sink);
+  const uint32_t send_mask = has_next ? static_cast<uint32_t>(rb_mask) : 0u;
+  // Where this warp publishes how far it has read its ring (its producer's prog_w slot).
+  const uint32_t prog_dst = !recv_left ? 0u
+                            : (warp > 0) ? smem_addr(prog_w + (warp - 1))
+                                         : mapa_rank(smem_addr(prog_w + (W - 1)), crank - 1);
+  const volatile uint32_t* my_prog = prog_w + warp;  // progress of the warp this one sends to
+  int prog_seen = t_begin;                           // consumer has read every frame < prog_seen
+  const bool is_l0 = (lane == 0);
+  const bool is_l31 = (lane == 31) && !((J.flags & kJobTestStall) && g == 0);
   const uint64_t* my_ring = ring + warp * P.rb;
-  uint64_t* next_ring = ring + (warp + 1) * P.rb;
-  const uint32_t remote_ring = send_remote ? mapa_rank(smem_addr(ring), crank + 1) : 0u;
-  const bool publish_prog = (warp == 0 && crank > 0);
-  const uint32_t remote_prog = publish_prog ? mapa_rank(smem_addr(&head->prog), crank - 1) : 0u;
-  uint32_t cached_prog = static_cast<uint32_t>(t_begin);
+  constexpr uint32_t kTagMask = (1u << kTagBits) - 1u;
+  const int s_last = s0 + K - 1;
 
-  auto send = [&](int t, float v) {  // lane 31 only
-    const uint64_t word = (static_cast<uint64_t>(static_cast<uint32_t>(t + 1)) << 32) | __float_as_uint(v);
-    if (send_local) {
-      *reinterpret_cast<volatile uint64_t*>(next_ring + (t & rb_mask)) = word;
-    } else if (send_remote) {
-      // The next CTA must have consumed frame t - rb before its slot is reused.
-      if (t - P.rb >= static_cast<int>(cached_prog)) {
-        const uint64_t t0 = gtimer();
-        for (;;) {
-          cached_prog = *reinterpret_cast<volatile uint32_t*>(&head->prog);
-          if (t - P.rb < static_cast<int>(cached_prog)) break;
-          if (*abort || gtimer() - t0 > limit) {
-            *abort = 1;
-            return;
-          }
-        }
-      }
-      st_remote_u64(remote_ring + static_cast<uint32_t>(t & rb_mask) * 8u, word);
-    }
-  };
   auto store_ckpt = [&](int t) {
-    if (ckpt != nullptr && (t % ck_every) == 0) {
-      float* dst = ckpt + static_cast<size_t>(t / ck_every) * ck_stride;
+    float* dst = ckpt + static_cast<size_t>(t / ck_every) * ck_stride;
 #pragma unroll
-      for (int j = 0; j < K; ++j)
-        if (s0 + j < S) dst[s0 + j] = a[j];
+    for (int j = 0; j < K; ++j)
+      if (s0 + j < S) dst[s0 + j] = a[j];
+  };
+  auto send_one = [&](int t, float v, int anc) {
+    const uint64_t word = (static_cast<uint64_t>((static_cast<uint32_t>(t) + 1u) & kTagMask) << 40) |
+                          (static_cast<uint64_t>(static_cast<uint32_t>(s_last - anc) & 0xffu) << 32) |
+                          __float_as_uint(v);
+    st_cluster_u64_if(send_base + (static_cast<uint32_t>(t) & send_mask) * 8u, word, is_l31);
+  };
+  // Anchor row of window m: s - anchor(s) of this lane's states, one store.
+  uint8_t* const ztab = J.ztab;
+  const int zstride = J.zstride;
+  auto store_anchor_row = [&](int m) {
+    if (ztab == nullptr || s0 >= zstride) return;
+    uint8_t* dst = ztab + static_cast<size_t>(m) * zstride + s0;
+    uint32_t packed[(K + 3) / 4];
+#pragma unroll
+    for (int q = 0; q < (K + 3) / 4; ++q) packed[q] = 0u;
+#pragma unroll
+    for (int j = 0; j < K; ++j)
+      packed[j / 4] |= (static_cast<uint32_t>(s0 + j - A[j]) & 0xffu) << (8 * (j % 4));
+    if constexpr (K == 2) {
+      *reinterpret_cast<uint16_t*>(dst) = static_cast<uint16_t>(packed[0]);
+    } else if constexpr (K == 4) {
+      *reinterpret_cast<uint32_t*>(dst) = packed[0];
+    } else if constexpr (K == 8) {
+      *reinterpret_cast<uint2*>(dst) = make_uint2(packed[0], packed[1]);
+    } else {
+      *reinterpret_cast<uint4*>(dst) = make_uint4(packed[0], packed[1], packed[2], packed[3]);
     }
   };
   if (ok) {
-    store_ckpt(t_begin);
-    if (lane == 31) send(t_begin, a[K - 1]);
+    if (ckpt != nullptr && (t_begin % ck_every) == 0) store_ckpt(t_begin);
+    send_one(t_begin, a[K - 1], A[K - 1]);  // slot of t_begin is fresh: no flow check needed
   }
 
   // ---- frames t_begin+1 .. t_end-1 ----
-  for (int t = t_begin + 1; t < t_end; ++t) {
+  // Frame of the next checkpoint row; without checkpoints a value beyond any
+  // frame count that still leaves next_ck + 1 - t positive.
+  int next_ck = (ckpt != nullptr) ? (t_begin / ck_every + 1) * ck_every : (1 << 30);
+  int next_anchor = t_begin + kAnchorD;
+  uint32_t* bpw = bp + static_cast<size_t>(g) * bp_rows * NW;  // row 0 of this warp (unused if bp == nullptr)
+  const bool write_bp = (bp != nullptr) && is_l0;
+  const float* stage_f = reinterpret_cast<const float*>(stages);
+  const int stage_floats = P.stage_bytes / 4;
+  int t = t_begin + 1;
+  while (ok && t < t_end) {
     const int ft = t - t_begin;
-    if (ft % F == 0) {  // entering the next stage of emission rows
+    const int c = ft / F;
+    if (c != chunk) {  // entering the next stage of emission rows
       __syncwarp();
       if (lane == 0) mbar_arrive(&head->empty[chunk % kStages]);
-      ++chunk;
+      chunk = c;
       if (__any_sync(kFull, *abort != 0)) break;
-      if (warp == 0 && chunk + 2 < nchunks) {
-        // Refill the stage that held chunk - 2 once every warp has released it.
-        const int old = chunk - 2;
-        bool free_ok = true;
-        if (old >= 0)
-          free_ok = warp_wait_phase(&head->empty[old % kStages], (old / kStages) & 1, abort, limit, lane);
-        if (!free_ok) break;
-        issue_chunk(chunk + 2);
-        issued = chunk + 3;
+      if (warp == 0 && chunk + kLead - 1 < nchunks) {
+        // Load chunk + kLead - 1 into the stage that held chunk + kLead - 1 - kStages,
+        // once every warp has released it.
+        const int old = chunk + kLead - 1 - kStages;
+        if (old >= 0 && !warp_wait_phase(&head->empty[old % kStages], (old / kStages) & 1, abort, limit, lane))
+          break;
+        issue_chunk(chunk + kLead - 1);
+        issued = chunk + kLead;
       }
       if (!warp_wait_phase(&head->full[chunk % kStages], (chunk / kStages) & 1, abort, limit, lane)) break;
-      if (lane == 0 && publish_prog) st_remote_u32(remote_prog, static_cast<uint32_t>(t - 1));
-      row = reinterpret_cast<const float*>(stages + (chunk % kStages) * P.stage_bytes);
-    } else {
-      row += C;
+    }
+    const int in_chunk = ft - c * F;
+    int ridx = (c % kStages) * stage_floats + in_chunk * C;  // row of frame t in the stage ring
+    const int n = min(min(min(F - in_chunk, t_end - t), min(next_ck, next_anchor) + 1 - t), P.block);
+
+    // Block receive: lane i takes the word of frame t-1+i (i < n).
+    float rv = -INFINITY;
+    int roff = 0;
+    if (recv_left) {
+      const int f = t - 1 + (lane < n ? lane : 0);
+      const uint64_t v = *reinterpret_cast<const volatile uint64_t*>(my_ring + (f & rb_mask));
+      const bool mine = static_cast<uint32_t>(v >> 40) == ((static_cast<uint32_t>(f) + 1u) & kTagMask);
+      uint64_t vv = v;
+      if (!__all_sync(kFull, mine)) vv = ring_block_spin(my_ring, t - 1, n, rb_mask, lane, abort, limit);
+      rv = __uint_as_float(static_cast<uint32_t>(vv));
+      roff = static_cast<int>((vv >> 32) & 0xffu);
+      // Frames < t + n - 1 are read after this block: tell the producer.
+      if (is_l0) st_remote_u32(prog_dst, static_cast<uint32_t>(t + n - 1));
+    }
+    // Frame t-1 may be an anchor frame: the sender's anchors were reset after it sent.
+    if (is_l0 && ((t - 1 - t_begin) % kAnchorD) == 0) roff = 0;
+    // Block send: slots t .. t+n-1 reuse those of frames t-rb .. t+n-1-rb.
+    if (has_next && t + n - 1 - P.rb >= prog_seen) {
+      prog_seen = static_cast<int>(prog_spin(my_prog, t + n - 1 - P.rb, abort, limit));
     }
 
-    // Emissions of this lane's states (blank column shared by the even states).
-    const float eb = row[blank];
-    float el[K / 2];
+    // Emissions of this lane's states (blank column shared by the even states),
+    // loaded one frame ahead of their use.
+    float eb_n = stage_f[ridx + blank];
+    float el_n[K / 2];
 #pragma unroll
-    for (int i = 0; i < K / 2; ++i) el[i] = row[col[i]];
-
-    // alpha_{t-1}(s0 - 1): from the lane below, or from the previous warp's ring.
-    float left = __shfl_up_sync(kFull, a[K - 1], 1);
-    if (lane == 0) {
-      if (recv_left) {
-        bool rok = true;
-        left = ring_recv(my_ring, t - 1, rb_mask, abort, limit, rok);
-      } else {
-        left = -INFINITY;
-      }
-    }
-
-    uint32_t adv[K];
-    uint32_t skp[K / 2];
+    for (int q = 0; q < K / 2; ++q) el_n[q] = stage_f[ridx + col[q]];
+#pragma unroll 2
+    for (int i = 0; i < n; ++i, ++t) {
+      const float eb = eb_n;
+      float el[K / 2];
 #pragma unroll
-    for (int j = K - 1; j >= 0; --j) {  // descending: a[j-1], a[j-2] still hold frame t-1
-      const float p1 = (j == 0) ? left : a[j - 1];
-      if ((j & 1) == 0) {  // blank state: stay or advance
-        const bool b1 = p1 > a[j];
-        const float m = b1 ? p1 : a[j];
-        adv[j] = __ballot_sync(kFull, b1);
-        a[j] = m + eb;
-      } else {  // label state: stay, advance, or skip when allowed
-        const float p2 = fminf((j == 1) ? left : a[j - 2], cap[j >> 1]);
-        const bool b1 = p1 > a[j];
-        float m = b1 ? p1 : a[j];
-        const bool b2 = p2 > m;
-        m = b2 ? p2 : m;
-        adv[j] = __ballot_sync(kFull, b1);
-        skp[j >> 1] = __ballot_sync(kFull, b2);
-        a[j] = m + el[j >> 1];
+      for (int q = 0; q < K / 2; ++q) el[q] = el_n[q];
+      ridx += (i + 1 < n) ? C : 0;
+      eb_n = stage_f[ridx + blank];
+#pragma unroll
+      for (int q = 0; q < K / 2; ++q) el_n[q] = stage_f[ridx + col[q]];
+
+      // alpha_{t-1}(s0 - 1) and its anchor: lane below by shuffle, lane 0 from the block.
+      const float shf = __shfl_up_sync(kFull, a[K - 1], 1);
+      const int shA = __shfl_up_sync(kFull, A[K - 1], 1);
+      const float blk = __shfl_sync(kFull, rv, i);
+      const int blko = __shfl_sync(kFull, roff, i);
+      const float left = is_l0 ? blk : shf;
+      const int Aleft = is_l0 ? (s0 - 1 - blko) : shA;
+
+      uint32_t adv[K];
+      uint32_t skp[K / 2];
+#pragma unroll
+      for (int j = K - 1; j >= 0; --j) {  // descending: a[j-1], a[j-2] still hold frame t-1
+        const float p1 = (j == 0) ? left : a[j - 1];
+        const int q1 = (j == 0) ? Aleft : A[j - 1];
+        if ((j & 1) == 0) {  // blank state: stay or advance
+          const bool b1 = p1 > a[j];
+          const float m = b1 ? p1 : a[j];
+          A[j] = b1 ? q1 : A[j];
+          adv[j] = __ballot_sync(kFull, b1);
+          a[j] = m + eb;
+        } else {  // label state: stay, advance, or skip when allowed
+          const float p2 = fminf((j == 1) ? left : a[j - 2], cap[j >> 1]);
+          const int q2 = (j == 1) ? Aleft : A[j - 2];
+          const bool b1 = p1 > a[j];
+          float m = b1 ? p1 : a[j];
+          int an = b1 ? q1 : A[j];
+          const bool b2 = p2 > m;
+          m = b2 ? p2 : m;
+          A[j] = b2 ? q2 : an;
+          adv[j] = __ballot_sync(kFull, b1);
+          skp[j >> 1] = __ballot_sync(kFull, b2);
+          a[j] = m + el[j >> 1];
+        }
       }
+      store_bp_words_if<K>(bpw, adv, skp, write_bp);
+      bpw += NW;
+      send_one(t, a[K - 1], A[K - 1]);
     }
-    if (bp != nullptr && lane == 0)
-      store_bp_words<K>(bp + (static_cast<size_t>(g) * bp_rows + (ft - 1)) * NW, adv, skp);
-    if (lane == 31) send(t, a[K - 1]);
-    store_ckpt(t);
+    if (t - 1 == next_ck) {
+      store_ckpt(next_ck);
+      next_ck += ck_every;
+    }
+    if (t - 1 == next_anchor) {
+      store_anchor_row((next_anchor - t_begin) / kAnchorD - 1);
+#pragma unroll
+      for (int j = 0; j < K; ++j) A[j] = s0 + j;
+      next_anchor += kAnchorD;
+    }
   }
+  // Last, partial window.
+  const int nwin = (t_end - 1 - t_begin + kAnchorD - 1) / kAnchorD;  // anchor rows of this pass
+  if (ok && *abort == 0 && t_end - 1 > t_begin && ((t_end - 1 - t_begin) % kAnchorD) != 0)
+    store_anchor_row(nwin - 1);
 
   // ---- alpha_{T-1} of the two final states ----
   const bool aborted_here = (*abort != 0);
@@ -427,81 +584,153 @@ __global__ void __launch_bounds__(K <= 8 ? 1024 : 512)
   }
   __threadfence();
   __syncthreads();
-  if (ncta > 1) cluster_sync();  // all backpointers / final values written; no remote access follows
+  if (ncta > 1) cluster_sync();  // all backpointers / anchor rows / final values written
   const bool aborted = (*abort != 0);
   if (aborted && threadIdx.x == 0) atomicExch(J.status, kStTimeout);
+  if (aborted) return;  // uniform across the CTA (read after the barrier)
 
-  // ---- tail: final state, total, and the backtrack (warp 0 of CTA 0) ----
-  if (crank != 0 || warp != 0 || aborted) return;
-  int s_cur;
-  if (J.flags & kJobWriteFinal) {
-    const float f_blank = __ldcg(J.final2 + 1);
-    const float f_lab = (S > 1) ? __ldcg(J.final2 + 0) : -INFINITY;
-    s_cur = (S > 1 && f_lab > f_blank) ? S - 2 : S - 1;
-    const float tot = (S > 1 && f_lab > f_blank) ? f_lab : f_blank;
-    if (lane == 0) {
-      if (J.total) *J.total = tot;
-      atomicCAS(J.status, kStPending, tot == -INFINITY ? kStNoPath : kStOk);
-      if (!(J.flags & kJobChase)) *J.state_io = s_cur;
+  // ---- tail 1 (warp 0 of CTA 0): final state, total, hops back through the anchor rows ----
+  // Boundary states go to path[t_begin + m*D] (m < nwin) and path[t_end - 1];
+  // the window walks below read them before overwriting path with tokens.
+  const bool chase = (J.flags & kJobChase) != 0;
+  unsigned char* tail = smem + P.off_ring;  // the rings and stages are free now
+  if (crank == 0 && warp == 0) {
+    int s_cur;
+    if (J.flags & kJobWriteFinal) {
+      const float f_blank = __ldcg(J.final2 + 1);
+      const float f_lab = (S > 1) ? __ldcg(J.final2 + 0) : -INFINITY;
+      s_cur = (S > 1 && f_lab > f_blank) ? S - 2 : S - 1;
+      const float tot = (S > 1 && f_lab > f_blank) ? f_lab : f_blank;
+      if (lane == 0) {
+        if (J.total) *J.total = tot;
+        atomicCAS(J.status, kStPending, tot == -INFINITY ? kStNoPath : kStOk);
+        if (!chase) *J.state_io = s_cur;
+      }
+    } else {
+      s_cur = __ldcg(J.state_io);
     }
-  } else {
-    s_cur = __ldcg(J.state_io);
+    if (chase) {
+      if (lane == 0) J.path[t_end - 1] = s_cur;
+      // Batches of kHopBatch rows: the states of the next kHopBatch window
+      // starts lie in [s - 2*kHopBatch*D, s]; lanes copy that byte range of
+      // each row into shared memory, then lane 0 hops.
+      uint8_t* zb = tail;  // [kHopBatch][span]
+      constexpr int kSpan = ((2 * kHopBatch * kAnchorD + 16) + 15) / 16 * 16 + 16;
+      for (int m = nwin - 1; m >= 0; m -= kHopBatch) {
+        const int nb = min(kHopBatch, m + 1);
+        const int lo = max(0, s_cur - 2 * kHopBatch * kAnchorD) & ~15;
+        const int hi = min(zstride, (s_cur + 16) & ~15);  // exclusive, 16-aligned
+        const int nchunk = (hi - lo) / 16;
+        for (int k = lane; k < nb * nchunk; k += 32) {
+          const int r = k / nchunk, q = k % nchunk;
+          const uint4 v = __ldcg(reinterpret_cast<const uint4*>(ztab + static_cast<size_t>(m - r) * zstride + lo) + q);
+          *reinterpret_cast<uint4*>(zb + r * kSpan + q * 16) = v;
+        }
+        __syncwarp();
+        if (lane == 0) {
+          for (int r = 0; r < nb; ++r) {
+            s_cur -= zb[r * kSpan + (s_cur - lo)];
+            J.path[t_begin + (m - r) * kAnchorD] = s_cur;
+          }
+        }
+        s_cur = __shfl_sync(kFull, s_cur, 0);
+        __syncwarp();
+      }
+      if (lane == 0) *J.state_io = s_cur;  // state at t_begin
+    }
   }
-  if (!(J.flags & kJobChase)) return;
+  if (!chase) return;
+  __threadfence();
+  __syncthreads();
+  if (ncta > 1) cluster_sync();  // boundary states visible to every warp of the team
 
-  // Windowed walk back: per window of 32 frames the states stay within
-  // [s - 62, s], i.e. inside at most two warp groups of 32K >= 64 states.
-  // Lanes fetch those backpointer words for one frame each, then lane 0
-  // follows the codes in shared memory and all lanes write the outputs.
-  constexpr int GS = 32 * K;
-  uint32_t* wbuf = reinterpret_cast<uint32_t*>(smem + P.off_bt);          // [32][2][NW]
-  int32_t* sbuf = reinterpret_cast<int32_t*>(smem + P.off_bt + kBtWindow * 2 * NW * 4);  // [32]
-  const int t_lo = t_begin;
-  for (int top = t_end - 1; top >= t_lo; top -= kBtWindow) {
-    const int n = min(kBtWindow, top - t_lo + 1);
-    const int g_hi = s_cur / GS;
-    const int g_lo = max(0, s_cur - 2 * (n - 1)) / GS;
-    if (lane < n) {
-      const int f = top - lane;
-      if (f > t_lo) {
-        for (int gi = 0; gi <= g_hi - g_lo; ++gi) {
-          const uint32_t* src = bp + (static_cast<size_t>(g_lo + gi) * bp_rows + (f - t_begin - 1)) * NW;
-          uint32_t* dst = wbuf + (lane * 2 + gi) * NW;
+  // ---- tail 2 (every warp of the team): walk the windows in parallel ----
+  // Window m covers frames (t_begin + m*D, e] with e = min(t_begin + (m+1)*D,
+  // t_end - 1); its top state is path[e]. Its states lie in [s_e - 2D + 2, s_e],
+  // at most two warp groups: lanes fetch the backpointer words of those groups
+  // for the window's frames, lane 0 follows them, all lanes write the outputs.
+  constexpr int kG = 2;
+  uint32_t* wbuf = reinterpret_cast<uint32_t*>(tail + warp * (kBtWindow * kG * NW * 4 + kBtWindow * 4));
+  int32_t* sbuf = reinterpret_cast<int32_t*>(reinterpret_cast<unsigned char*>(wbuf) + kBtWindow * kG * NW * 4);
+  const int G = static_cast<int>(ncta) * W;
+  const int nwalk = max(nwin, 1);
+  for (int m = g; m < nwalk; m += G) {
+    const int b = t_begin + m * kAnchorD;                      // bottom frame (exclusive unless m == 0)
+    const int e = (nwin == 0) ? t_begin : min(b + kAnchorD, t_end - 1);
+    const int s_top = __ldcg(J.path + e);
+    const int n = e - b;  // frames b+1 .. e (<= 32); window 0 also writes frame b = t_begin
+    const int glo = max(0, s_top - 2 * (kBtWindow - 1)) / GS;
+    const int ng = s_top / GS - glo + 1;
+    const int f = e - lane;
+    if (lane < e - b) {  // frames b+1 .. e have codes
+      uint32_t* dst = wbuf + lane * kG * NW;
+      for (int gi = 0; gi < ng; ++gi) {
+        const uint32_t* src = bp + (static_cast<size_t>(glo + gi) * bp_rows + (f - t_begin - 1)) * NW;
 #pragma unroll
-          for (int w = 0; w < NW; ++w) dst[w] = __ldcg(src + w);
-        }
+        for (int w = 0; w < NW; ++w) dst[gi * NW + w] = __ldcg(src + w);
       }
     }
     __syncwarp();
     if (lane == 0) {
+      int sc = s_top;
       for (int i = 0; i < n; ++i) {
-        const int f = top - i;
-        sbuf[i] = s_cur;
-        if (f > t_lo) {
-          const int gi = s_cur / GS - g_lo;
-          const int r = s_cur % GS;
-          const int ln = r / K;
-          const int j = r % K;
-          const uint32_t* wd = wbuf + (i * 2 + gi) * NW;
-          const uint32_t av = (wd[j] >> ln) & 1u;
-          const uint32_t sk = (j & 1) ? ((wd[K + (j >> 1)] >> ln) & 1u) : 0u;
-          s_cur -= sk ? 2 : static_cast<int>(av);
-        }
+        sbuf[i] = sc;  // state at frame e - i
+        const int gi = sc / GS - glo;
+        const int r = sc % GS;
+        const int ln = r / K;
+        const int j = r % K;
+        const uint32_t* wd = wbuf + (i * kG + gi) * NW;
+        const uint32_t av = (wd[j] >> ln) & 1u;
+        const uint32_t sk = (j & 1) ? ((wd[K + (j >> 1)] >> ln) & 1u) : 0u;
+        sc -= sk ? 2 : static_cast<int>(av);
+      }
+      if (m == 0) {  // frame t_begin itself
+        const int tok = (sc & 1) ? __ldg(J.tgt + (sc >> 1)) : blank;
+        J.path[b] = tok;
+        if (J.states) J.states[b] = sc;
+        J.scores[b] = __ldg(lp + static_cast<size_t>(b) * C + tok);
       }
     }
     __syncwarp();
-    s_cur = __shfl_sync(kFull, s_cur, 0);
     if (lane < n) {
-      const int f = top - lane;
       const int st = sbuf[lane];
-      const int tok = (st & 1) ? J.tgt[st >> 1] : blank;
+      const int tok = (st & 1) ? __ldg(J.tgt + (st >> 1)) : blank;
       J.path[f] = tok;
-      J.scores[f] = __ldg(lp + static_cast<size_t>(f) * C + tok);
       if (J.states) J.states[f] = st;
+      J.scores[f] = __ldg(lp + static_cast<size_t>(f) * C + tok);
     }
     __syncwarp();
   }
-  if (lane == 0) *J.state_io = s_cur;
+}
+
+// ------------------------------------------------------- frame-latency probe --
+// Per-frame synchronisation bound of the roofline: the irreducible dependent
+// chain of one frame of the recursion at warp scope, with null work around it.
+// Every lane holds one state; per frame it reads its emission from shared
+// memory, takes its left neighbour's previous value by shuffle, and does one
+// max and one add. Between warps and CTAs the trellis kernel exchanges values
+// once per block of frames, which adds pipeline fill but no per-frame cost, so
+// this chain bounds the time per frame of any team shape. Warp 0 of CTA 0
+// measures the time per frame with %globaltimer; other warps run the same loop.
+__global__ void __launch_bounds__(1024) frame_probe_kernel(int frames, uint64_t limit_ns, uint64_t* out) {
+  __shared__ float rows[64 * 32];
+  const int lane = threadIdx.x & 31;
+  for (int i = threadIdx.x; i < 64 * 32; i += blockDim.x) rows[i] = -0.001f * static_cast<float>(i % 97);
+  __syncthreads();
+  float a = (lane == 0) ? 0.0f : -INFINITY;
+  const uint64_t t0 = gtimer();
+  for (int t = 0; t < frames; ++t) {
+    const float e = rows[(t & 63) * 32 + lane];
+    const float left = __shfl_up_sync(kFull, a, 1);
+    a = fmaxf(a, lane == 0 ? -INFINITY : left) + e;
+  }
+  const uint64_t t1 = gtimer();
+  (void)limit_ns;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    out[0] = t1 - t0;
+    out[1] = 0ull;
+    out[2] = __float_as_uint(a);
+  }
 }
 
 template <int K>
@@ -537,20 +766,31 @@ cudaError_t launch_k(const LaunchShape& shape, const FwdParams& p, const FwdJob*
 FwdParams plan_params(const LaunchShape& shape, int C, int frames_per_stage, uint64_t wait_limit_ns) {
   FwdParams p{};
   const int F = frames_per_stage < 1 ? 1 : frames_per_stage;
+  // Block of frames per ring wait: the warps of a CTA lag each other by about
+  // one block per hop, and the emission ring tolerates (kStages - kLead) * F
+  // frames of lag between its first and last warp.
+  const int lag_room = (kStages - kLead) * F;
+  p.block = std::max(1, std::min(32, lag_room / std::max(1, shape.warps - 1)));
   int rb = 8;
-  while (rb < 4 * F + 2) rb <<= 1;
+  while (rb < 2 * p.block + 2) rb <<= 1;
   p.rb = rb;
   p.frames_per_stage = F;
   p.stage_bytes = ((F * C * 4) + 15) & ~15;
-  p.off_ring = static_cast<int>(sizeof(SmemHead));
+  p.off_ring = static_cast<int>(sizeof(SmemHead)) + 32 * 4;
   p.off_stage = (p.off_ring + shape.warps * rb * 8 + 127) & ~127;
-  p.off_bt = (p.off_stage + kStages * p.stage_bytes + 127) & ~127;
+  p.off_bt = (p.off_stage + kStages * p.stage_bytes + 127) & ~127;  // end of the forward region
   p.wait_limit_ns = wait_limit_ns;
   return p;
 }
 
 int smem_bytes(const LaunchShape& shape, const FwdParams& p) {
-  return p.off_bt + kBtWindow * 2 * bp_words(shape.K) * 4 + kBtWindow * 4;
+  // The backtrack reuses the ring / stage region: per warp a window of
+  // backpointer words (2 groups) and 32 states; warp 0 first needs the hop
+  // buffer of kHopBatch anchor-row slices.
+  const int per_warp = kBtWindow * 2 * bp_words(shape.K) * 4 + kBtWindow * 4;
+  const int span = ((2 * kHopBatch * kAnchorD + 16) + 15) / 16 * 16 + 16;
+  const int tail = std::max(shape.warps * per_warp, kHopBatch * span);
+  return std::max(p.off_bt, p.off_ring + tail);
 }
 
 int launch_trellis(const LaunchShape& shape, const FwdParams& p, const FwdJob* d_jobs, int njobs,
@@ -564,6 +804,11 @@ int launch_trellis(const LaunchShape& shape, const FwdParams& p, const FwdJob* d
     case 16: return launch_k<16>(shape, p, d_jobs, njobs, s);
     default: return cudaErrorInvalidValue;
   }
+}
+
+int launch_frame_probe(int warps, int ncta, int frames, uint64_t limit_ns, uint64_t* d_out, void* stream) {
+  frame_probe_kernel<<<ncta, warps * 32, 0, static_cast<cudaStream_t>(stream)>>>(frames, limit_ns, d_out);
+  return cudaGetLastError();
 }
 
 int max_smem_optin(int device) {

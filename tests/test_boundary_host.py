@@ -60,10 +60,13 @@ def test_plan_shapes_and_footprints():
     # Config-1 sized: S = 81 fits one warp of K=4 lanes.
     p = align.align_plan(200, 32, 40)
     assert (p["states_per_lane"], p["warps_per_cta"], p["cluster_ctas"]) == (4, 1, 1)
-    assert p["backpointer_bytes"] == 1 * 6 * 4 * 199
+    # 199 rows of 6 words, padded to 256 B, plus 7 anchor rows of 96 B (S=81 -> 96) padded to 256 B.
+    assert p["backpointer_bytes"] == 4864 + 768
     assert p["checkpointed"] == 0
-    # S = 1501: 12 warps of 128 states.
+    # S = 1501: 12 warps of 128 states; by default 4 warps per CTA, a cluster of 3.
     p = align.align_plan(3000, 32, 750)
+    assert p["warps_per_cta"] == 4 and p["cluster_ctas"] == 3
+    p = align.align_plan(3000, 32, 750, cta_warps=16)
     assert p["warps_per_cta"] == 12 and p["cluster_ctas"] == 1
     # Hour-long: S = 90001 needs a cluster.
     p = align.align_plan(180000, 32, 45000, budget=8 << 30)
@@ -82,9 +85,11 @@ def test_plan_shapes_and_footprints():
     with pytest.raises(align.AlignError) as e:
         align.align_plan(180000, 32, 45000, budget=1 << 20)
     assert e.value.code == align.ALIGN_E_TOO_LARGE
-    # Stage depth: 16 rows of C=32, fewer rows of C=500.
-    assert align.align_plan(100, 32, 10)["frames_per_stage"] == 16
-    assert align.align_plan(100, 500, 10)["frames_per_stage"] == 4
+    # Stage depth: 32 rows of C=32, fewer rows of C=500.
+    assert align.align_plan(100, 32, 10)["frames_per_stage"] == 32       # one warp: 4 KB stages
+    assert align.align_plan(3000, 32, 750)["frames_per_stage"] == 32     # 12 warps
+    assert align.align_plan(3000, 500, 750)["frames_per_stage"] == 4     # 8 KB cap
+    assert align.align_plan(100, 500, 10)["frames_per_stage"] == 2       # 4 KB stages of 2 KB rows
 
 
 @pytest.mark.parametrize("K", [2, 4, 8, 16])
@@ -99,9 +104,7 @@ def test_plan_capacity_covers_states(K):
             continue
         cap = p["states_per_lane"] * 32 * p["warps_per_cta"] * p["cluster_ctas"]
         assert cap >= 2 * L + 1
-        assert p["cluster_ctas"] <= 16 and p["warps_per_cta"] <= 32
-        if p["states_per_lane"] == 16:
-            assert p["warps_per_cta"] <= 16
+        assert p["cluster_ctas"] <= 16 and p["warps_per_cta"] <= 16
         # No empty warp group: the last warp holds at least one state.
         assert cap - 2 * L - 1 < p["states_per_lane"] * 32 * p["cluster_ctas"]
 

@@ -213,3 +213,55 @@ def test_invariants_on_config4_sample():
                 compare(r, sl, b.targets[i], 0, f"cfg4[{i}]")
     finally:
         a.close()
+
+
+def test_submit_batch_equals_single_and_host_batch():
+    build.build()
+    specs = synth.specs(2)[:24]
+    b = synth.make_batch(specs, device="cuda")
+    a = align.Aligner(device=0)
+    try:
+        outs = [(torch.empty(s.T, dtype=torch.int32, device="cuda"), torch.empty(s.T, device="cuda"),
+                 torch.empty(1, device="cuda"), torch.empty(s.T, dtype=torch.int32, device="cuda")) for s in specs]
+        rb = a.submit_batch([(b.utt(i), b.targets[i], 0, outs[i]) for i in range(len(b))])
+        for r in rb:
+            a.poll(r)
+        lp_host = b.lp.cpu()
+        hout = [(torch.empty(s.T, dtype=torch.int32).pin_memory(), torch.empty(s.T).pin_memory(),
+                 torch.empty(1).pin_memory(), torch.empty(s.T, dtype=torch.int32).pin_memory()) for s in specs]
+        hl = [lp_host[b.offsets[i]:b.offsets[i + 1]].contiguous().pin_memory() for i in range(len(b))]
+        rh = a.submit_batch([(hl[i], b.targets[i], 0, hout[i]) for i in range(len(b))], host=True)
+        for r in rh:
+            a.poll(r)
+        for i in range(len(b)):
+            compare(rb[i], lp_host[b.offsets[i]:b.offsets[i + 1]].numpy(), b.targets[i], 0, f"batch[{i}]")
+            assert torch.equal(rb[i].path.cpu(), rh[i].path) and torch.equal(rb[i].states.cpu(), rh[i].states)
+            assert rb[i].scores.cpu().numpy().tobytes() == rh[i].scores.numpy().tobytes()
+        # A rejected request in a batch does not stop the others.
+        bad = [(b.utt(0), b.targets[0], 0, outs[0]), (b.utt(1), np.array([0], np.int32), 0, outs[1])]
+        with pytest.raises(align.AlignError):
+            a.submit_batch(bad)
+    finally:
+        a.close()
+
+
+def test_watchdog_timeout_keeps_context_usable():
+    """A device-side wait that never completes ends with ALIGN_E_TIMEOUT after
+    the configured limit; nothing faults and later work runs normally."""
+    build.build()
+    u = synth.make_utterance(3, 400, 32, 150)   # S = 301: several warps
+    v = synth.make_utterance(4, 100, 32, 20)    # S = 41: a single warp
+    st = align.Aligner(device=0, wait_limit_ms=50, test_stall=True)
+    try:
+        r = st.align(u.lp.cuda(), u.targets, 0)
+        assert r.status == align.ALIGN_E_TIMEOUT
+        r1 = st.align(v.lp.cuda(), v.targets, 0)   # one warp: no hand-off, unaffected
+        compare(r1, v.lp.numpy(), v.targets, 0, "single-warp under stall flag")
+    finally:
+        st.close()
+    ok = align.Aligner(device=0)
+    try:
+        r = ok.align(u.lp.cuda(), u.targets, 0)
+        compare(r, u.lp.numpy(), u.targets, 0, "after timeout")
+    finally:
+        ok.close()
