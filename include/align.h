@@ -188,6 +188,31 @@ int align_set_tuning(align_ctx *ctx, int32_t states_per_lane, int32_t cta_warps,
 int align_probe_frame_latency(int32_t device, int32_t warps, int32_t ctas, int32_t frames,
                               double *ns_per_frame);
 
+/* ---- allocation-free entry point ---------------------------------------- */
+
+/* Align one utterance without allocating any memory, for callers that cannot
+   allocate device memory when they need an alignment (a real-time thread that
+   must not risk the device-wide synchronisation of cudaMalloc, or a host that
+   gives the library a fixed device-memory budget up front). The paper has no
+   counterpart; this is an interface choice of this library.
+   log_probs: DEVICE FP32 [T][C]; targets: HOST int32 [L]; out: DEVICE pointers;
+   cuda_stream: stream to run on (NULL = legacy default stream). Same results
+   as align_submit. All scratch (descriptor, status, targets copy, backpointers,
+   anchor rows) lives in one fixed 32 MiB device array built into the library,
+   held on every device where the library is loaded until the process exits.
+   Requests needing more scratch than that return ALIGN_E_TOO_LARGE (message
+   in align_noalloc_last_error). The first call on a device looks up the
+   array's address; make it before any stream capture on that device. Every
+   call shares the array and keeps the previous call's contents: calls that
+   overlap on the GPU race, so never issue two at once. The call synchronises
+   `cuda_stream` before it returns and writes the request's result code
+   (ALIGN_OK, ALIGN_E_NOPATH or ALIGN_E_TIMEOUT) to *request_status. */
+int align_forced_noalloc(const float *log_probs, int64_t T, int64_t C, const int32_t *targets, int64_t L,
+                         int32_t blank, align_out out, void *cuda_stream, int32_t *request_status);
+
+/* Text of the last align_forced_noalloc failure on this thread (static buffer). */
+const char *align_noalloc_last_error(void);
+
 /* ---- host-only helpers (no GPU needed) -------------------------------- */
 
 /* Step A1 alone: checks T >= 1, C >= 2, 0 <= blank < C, every target in [0, C)

@@ -40,7 +40,8 @@ ALIGN_F_TEST_STALL = 0x80000000
 # Every entry point declared in include/align.h.
 EXPORTS = ("align_create", "align_destroy", "align_submit", "align_submit_host", "align_submit_batch", "align_flush",
            "align_poll", "align_join", "align_get_stats", "align_status_string", "align_last_error",
-           "align_set_tuning", "align_validate", "align_plan", "align_probe_frame_latency")
+           "align_set_tuning", "align_validate", "align_plan", "align_probe_frame_latency",
+           "align_forced_noalloc", "align_noalloc_last_error")
 
 
 class AlignConfig(ctypes.Structure):
@@ -114,6 +115,9 @@ def lib() -> ctypes.CDLL:
         L.align_last_error.restype = ctypes.c_char_p
         L.align_set_tuning.argtypes = [vp, i32, i32, i32]
         L.align_probe_frame_latency.argtypes = [i32, i32, i32, i32, ctypes.POINTER(ctypes.c_double)]
+        L.align_forced_noalloc.argtypes = [vp, i64, i64, vp, i64, i32, AlignOut, vp, ctypes.POINTER(i32)]
+        L.align_noalloc_last_error.argtypes = []
+        L.align_noalloc_last_error.restype = ctypes.c_char_p
         L.align_validate.argtypes = [vp, i64, i64, i32, i64, ctypes.POINTER(i64)]
         L.align_plan.argtypes = [i64, i64, i64, u64, u32, i32, i32, i32, ctypes.POINTER(AlignPlanInfo)]
         for name in EXPORTS:
@@ -213,6 +217,22 @@ def align_probe_frame_latency(device: int, warps: int, ctas: int, frames: int) -
     _check(lib().align_probe_frame_latency(device, warps, ctas, frames, ctypes.byref(ns)),
            "align_probe_frame_latency")
     return ns.value
+
+
+def align_forced_noalloc(log_probs_ptr: int, T: int, C: int, targets, blank: int, out: AlignOut,
+                         stream_ptr: int | None = None) -> tuple[int, int]:
+    """Allocation-free alignment (see include/align.h). Returns (call code, request status);
+    a negative call code comes with a message in align_noalloc_last_error()."""
+    tg = _i32(targets)
+    st = ctypes.c_int32(ALIGN_PENDING)
+    rc = lib().align_forced_noalloc(ctypes.c_void_p(log_probs_ptr), T, C, tg.ctypes.data_as(ctypes.c_void_p),
+                                    tg.size, blank, out, ctypes.c_void_p(stream_ptr) if stream_ptr else None,
+                                    ctypes.byref(st))
+    return rc, st.value
+
+
+def align_noalloc_last_error() -> str:
+    return lib().align_noalloc_last_error().decode()
 
 
 def align_validate(targets, C: int, blank: int, T: int) -> tuple[int, int]:
