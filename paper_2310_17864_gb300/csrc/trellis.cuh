@@ -43,7 +43,7 @@ constexpr int kStages = 10;           // emission ring stages per CTA
 constexpr int kLead = 4;              // stages in flight ahead of the consumer
 constexpr int kBtWindow = 32;         // frames per backtrack window
 constexpr int kAnchorD = 32;          // frames between anchor rows (== kBtWindow)
-constexpr int kHopBatch = 8;          // anchor rows fetched per batch while hopping back
+constexpr int kHopBatch = 16;         // anchor rows fetched per batch while hopping back
 constexpr int kTagBits = 24;          // frame tag bits in a ring word
 
 // Job flags.

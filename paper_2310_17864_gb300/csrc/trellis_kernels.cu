@@ -593,7 +593,7 @@ __global__ void __launch_bounds__(512)
   // Boundary states go to path[t_begin + m*D] (m < nwin) and path[t_end - 1];
   // the window walks below read them before overwriting path with tokens.
   const bool chase = (J.flags & kJobChase) != 0;
-  unsigned char* tail = smem + P.off_ring;  // the rings and stages are free now
+  unsigned char* tail = smem + P.off_ring;  // the rings and stages are free now (hop buffer)
   if (crank == 0 && warp == 0) {
     int s_cur;
     if (J.flags & kJobWriteFinal) {
@@ -644,62 +644,47 @@ __global__ void __launch_bounds__(512)
   __syncthreads();
   if (ncta > 1) cluster_sync();  // boundary states visible to every warp of the team
 
-  // ---- tail 2 (every warp of the team): walk the windows in parallel ----
+  // ---- tail 2 (every lane of the team): walk the windows in parallel ----
   // Window m covers frames (t_begin + m*D, e] with e = min(t_begin + (m+1)*D,
-  // t_end - 1); its top state is path[e]. Its states lie in [s_e - 2D + 2, s_e],
-  // at most two warp groups: lanes fetch the backpointer words of those groups
-  // for the window's frames, lane 0 follows them, all lanes write the outputs.
-  constexpr int kG = 2;
-  uint32_t* wbuf = reinterpret_cast<uint32_t*>(tail + warp * (kBtWindow * kG * NW * 4 + kBtWindow * 4));
-  int32_t* sbuf = reinterpret_cast<int32_t*>(reinterpret_cast<unsigned char*>(wbuf) + kBtWindow * kG * NW * 4);
+  // t_end - 1); its top state is path[e]. One lane walks one window, reading
+  // the two backpointer words of each step straight from L2 (the rows were
+  // written moments ago), and stores the state of every frame into path[]
+  // (window 0 also frame t_begin). Lanes of a warp walk 32 windows at once.
   const int G = static_cast<int>(ncta) * W;
   const int nwalk = max(nwin, 1);
-  for (int m = g; m < nwalk; m += G) {
-    const int b = t_begin + m * kAnchorD;                      // bottom frame (exclusive unless m == 0)
+  for (int m = g * 32 + lane; m < nwalk; m += G * 32) {
+    const int b = t_begin + m * kAnchorD;
     const int e = (nwin == 0) ? t_begin : min(b + kAnchorD, t_end - 1);
-    const int s_top = __ldcg(J.path + e);
-    const int n = e - b;  // frames b+1 .. e (<= 32); window 0 also writes frame b = t_begin
-    const int glo = max(0, s_top - 2 * (kBtWindow - 1)) / GS;
-    const int ng = s_top / GS - glo + 1;
-    const int f = e - lane;
-    if (lane < e - b) {  // frames b+1 .. e have codes
-      uint32_t* dst = wbuf + lane * kG * NW;
-      for (int gi = 0; gi < ng; ++gi) {
-        const uint32_t* src = bp + (static_cast<size_t>(glo + gi) * bp_rows + (f - t_begin - 1)) * NW;
-#pragma unroll
-        for (int w = 0; w < NW; ++w) dst[gi * NW + w] = __ldcg(src + w);
-      }
+    int sc = __ldcg(J.path + e);
+    for (int f = e; f > b; --f) {
+      J.path[f] = sc;
+      const int gs = sc / GS;
+      const int r = sc % GS;
+      const int ln = r / K;
+      const int j = r % K;
+      const uint32_t* wd = bp + (static_cast<size_t>(gs) * bp_rows + (f - t_begin - 1)) * NW;
+      const uint32_t av = (__ldcg(wd + j) >> ln) & 1u;
+      const uint32_t sk = (__ldcg(wd + K + (j >> 1)) >> ln) & static_cast<uint32_t>(j) & 1u;
+      sc -= sk ? 2 : static_cast<int>(av);
     }
-    __syncwarp();
-    if (lane == 0) {
-      int sc = s_top;
-      for (int i = 0; i < n; ++i) {
-        sbuf[i] = sc;  // state at frame e - i
-        const int gi = sc / GS - glo;
-        const int r = sc % GS;
-        const int ln = r / K;
-        const int j = r % K;
-        const uint32_t* wd = wbuf + (i * kG + gi) * NW;
-        const uint32_t av = (wd[j] >> ln) & 1u;
-        const uint32_t sk = (j & 1) ? ((wd[K + (j >> 1)] >> ln) & 1u) : 0u;
-        sc -= sk ? 2 : static_cast<int>(av);
-      }
-      if (m == 0) {  // frame t_begin itself
-        const int tok = (sc & 1) ? __ldg(J.tgt + (sc >> 1)) : blank;
-        J.path[b] = tok;
-        if (J.states) J.states[b] = sc;
-        J.scores[b] = __ldg(lp + static_cast<size_t>(b) * C + tok);
-      }
-    }
-    __syncwarp();
-    if (lane < n) {
-      const int st = sbuf[lane];
+    if (m == 0) J.path[b] = sc;
+  }
+  __threadfence();
+  __syncthreads();
+  if (ncta > 1) cluster_sync();  // every frame's state is in path[]
+
+  // ---- tail 3 (every thread of the team): states -> tokens, states, scores ----
+  {
+    const int tid = g * 32 + lane;
+    const int nthr = G * 32;
+#pragma unroll 4
+    for (int f = t_begin + tid; f < t_end; f += nthr) {
+      const int st = __ldcg(J.path + f);
       const int tok = (st & 1) ? __ldg(J.tgt + (st >> 1)) : blank;
       J.path[f] = tok;
       if (J.states) J.states[f] = st;
       J.scores[f] = __ldg(lp + static_cast<size_t>(f) * C + tok);
     }
-    __syncwarp();
   }
 }
 
@@ -784,13 +769,11 @@ FwdParams plan_params(const LaunchShape& shape, int C, int frames_per_stage, uin
 }
 
 int smem_bytes(const LaunchShape& shape, const FwdParams& p) {
-  // The backtrack reuses the ring / stage region: per warp a window of
-  // backpointer words (2 groups) and 32 states; warp 0 first needs the hop
-  // buffer of kHopBatch anchor-row slices.
-  const int per_warp = kBtWindow * 2 * bp_words(shape.K) * 4 + kBtWindow * 4;
+  // The backtrack reuses the ring / stage region for the hop buffer of
+  // kHopBatch anchor-row slices.
+  (void)shape;
   const int span = ((2 * kHopBatch * kAnchorD + 16) + 15) / 16 * 16 + 16;
-  const int tail = std::max(shape.warps * per_warp, kHopBatch * span);
-  return std::max(p.off_bt, p.off_ring + tail);
+  return std::max(p.off_bt, p.off_ring + kHopBatch * span);
 }
 
 int launch_trellis(const LaunchShape& shape, const FwdParams& p, const FwdJob* d_jobs, int njobs,
