@@ -53,7 +53,31 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serving-requests", type=int, default=400)
     return ap.parse_args()
+
+
+def serving_run(align, serve, synth, torch, dev: int, n: int) -> dict:
+    """Workload 5: Poisson arrivals served by the continuous-batching loop with a
+    16 GiB backpointer budget. Saturation = every request arriving at time 0;
+    then offered loads of 0.5, 0.8 and 0.95 times the saturation request rate."""
+    b = synth.make_batch(synth.specs(5, n=n), device=f"cuda:{dev}")
+    al = align.Aligner(device=dev, batched=True, bp_budget_bytes=16 << 30)
+    try:
+        warm = serve.poisson_requests(b, rate_per_s=1e9, seed=1)
+        serve.serve(al, warm)
+        sat_reqs = [serve.Request(0.0, r.log_probs, r.targets) for r in warm]
+        sat = serve.serve(al, sat_reqs)
+        rate_sat = sat.n / sat.makespan_s
+        out = {"requests": n, "saturation": {**sat.as_dict(), "requests_per_s": rate_sat}, "loads": {}}
+        for frac in (0.5, 0.8, 0.95):
+            reqs = serve.poisson_requests(b, rate_per_s=frac * rate_sat, seed=int(frac * 100))
+            st = serve.serve(al, reqs)
+            out["loads"][str(frac)] = {**st.as_dict(), "offered_requests_per_s": frac * rate_sat}
+        return out
+    finally:
+        al.close()
 
 
 def cores() -> int:
@@ -294,6 +318,11 @@ def main():
         e2e = {"value": world * cells / (e_ms / 1e3), "unit": "cells/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "ms_per_step": e_ms}
 
+    serving = None
+    if not args.no_serving:
+        from paper_2310_17864_gb300 import serve
+        serving = serving_run(align, serve, synth, torch, dev, args.serving_requests)
+
     if rank != 0:
         al.close()
         if dist:
@@ -353,6 +382,7 @@ def main():
                      "t_frame_ns": t_frame_ns, "alg_bytes_per_launch": alg_bytes,
                      "hbm_gbs": alg_bytes / (ms / 1e3) / 1e9, "hbm_peak_gbs": hbm_peak,
                      "peak_source": f"{peak_src} (HBM); null-work frame probe measured in this run (latency)"},
+        "serving": serving,
         "cpu_baseline": cpu,
         "clocks": clk.summary(),
     }

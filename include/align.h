@@ -149,6 +149,13 @@ int align_flush(align_ctx *ctx);
    ALIGN_E_NOTFOUND. Polling also launches queued work. */
 int align_poll(align_ctx *ctx, uint64_t request_id, int32_t timeout_ms, int32_t *request_status);
 
+/* Collect finished requests without waiting: launches queued work like
+   align_poll, then writes up to `max` finished request ids and their result
+   codes (ALIGN_OK, ALIGN_E_NOPATH or ALIGN_E_TIMEOUT) and releases them;
+   *count gets the number written. Serving loops call this once per tick
+   instead of polling every request. */
+int align_poll_done(align_ctx *ctx, uint64_t *ids, int32_t *statuses, int32_t max, int32_t *count);
+
 /* Make `stream` (a cudaStream_t; NULL = the context's stream) wait on the GPU
    for every batch launched so far, without blocking the host. Batches are not
    otherwise ordered before later work on the context's stream, so that new

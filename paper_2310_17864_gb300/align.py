@@ -39,7 +39,7 @@ ALIGN_F_TEST_STALL = 0x80000000
 
 # Every entry point declared in include/align.h.
 EXPORTS = ("align_create", "align_destroy", "align_submit", "align_submit_host", "align_submit_batch", "align_flush",
-           "align_poll", "align_join", "align_get_stats", "align_status_string", "align_last_error",
+           "align_poll", "align_poll_done", "align_join", "align_get_stats", "align_status_string", "align_last_error",
            "align_set_tuning", "align_validate", "align_plan", "align_probe_frame_latency",
            "align_forced_noalloc", "align_noalloc_last_error")
 
@@ -108,6 +108,7 @@ def lib() -> ctypes.CDLL:
         L.align_flush.argtypes = [vp]
         L.align_poll.argtypes = [vp, u64, i32, ctypes.POINTER(i32)]
         L.align_join.argtypes = [vp, vp]
+        L.align_poll_done.argtypes = [vp, ctypes.POINTER(u64), ctypes.POINTER(i32), i32, ctypes.POINTER(i32)]
         L.align_get_stats.argtypes = [vp, ctypes.POINTER(AlignStats), i32]
         L.align_status_string.argtypes = [i32]
         L.align_status_string.restype = ctypes.c_char_p
@@ -195,6 +196,15 @@ def align_poll(ctx, request_id: int, timeout_ms: int = -1) -> tuple[int, int]:
     st = ctypes.c_int32(ALIGN_PENDING)
     rc = _check(lib().align_poll(ctx, request_id, timeout_ms, ctypes.byref(st)), "align_poll")
     return rc, st.value
+
+
+def align_poll_done(ctx, max_n: int = 4096) -> list[tuple[int, int]]:
+    """Finished (request id, result code) pairs, released; never waits."""
+    ids = (ctypes.c_uint64 * max_n)()
+    st = (ctypes.c_int32 * max_n)()
+    n = ctypes.c_int32(0)
+    _check(lib().align_poll_done(ctx, ids, st, max_n, ctypes.byref(n)), "align_poll_done")
+    return [(ids[i], st[i]) for i in range(n.value)]
 
 
 def align_join(ctx, stream_ptr: int | None = None) -> None:
@@ -367,6 +377,17 @@ class Aligner:
             self._live.pop(res.request_id, None)
             return True
         return False
+
+    def poll_done(self, max_n: int = 4096) -> list[Result]:
+        """Results that finished since the last call (status filled in), without waiting."""
+        out = []
+        for rid, st in align_poll_done(self.ctx, max_n):
+            entry = self._live.pop(rid, None)
+            if entry is not None:
+                res = entry[1]
+                res.status = st
+                out.append(res)
+        return out
 
     def align(self, log_probs, targets, blank: int = 0, want_states: bool = False) -> Result:
         res = self.submit(log_probs, targets, blank, want_states)

@@ -56,6 +56,7 @@ void set_error(const char* what, cudaError_t e) {
   } while (0)
 
 constexpr uint64_t kAlign = 256;
+constexpr size_t kMaxStreams = 128;  // worker streams of a context
 inline uint64_t round_up(uint64_t v, uint64_t a) { return (v + a - 1) / a * a; }
 
 // First-fit allocator over [0, cap) with coalescing frees.
@@ -482,10 +483,23 @@ int launch_queued(align_ctx* ctx) {
   // sequence runs on its own worker stream; everything joins on the first.
   cudaEvent_t fork = ctx->fork_events[static_cast<size_t>(b.id) % ctx->fork_events.size()];
   CU(cudaEventRecord(fork, ctx->main));
+  // Idle streams first, so a new batch never queues behind a long kernel of an
+  // earlier batch (head-of-line blocking); the pool grows when all are busy.
   const size_t nlanes = std::max<size_t>(1, glaunch.size() + cklaunch.size());
   std::vector<cudaStream_t> used;
-  for (size_t k = 0; k < nlanes; ++k) {
-    cudaStream_t s = ctx->workers[static_cast<size_t>(ctx->next_worker++) % ctx->workers.size()];
+  for (size_t k = 0; k < ctx->workers.size() && used.size() < nlanes; ++k) {
+    cudaStream_t s = ctx->workers[(static_cast<size_t>(ctx->next_worker) + k) % ctx->workers.size()];
+    if (cudaStreamQuery(s) == cudaSuccess) used.push_back(s);
+  }
+  ctx->next_worker = static_cast<int>((static_cast<size_t>(ctx->next_worker) + 1) % ctx->workers.size());
+  while (used.size() < nlanes && ctx->workers.size() < kMaxStreams) {
+    cudaStream_t s;
+    CU(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    ctx->workers.push_back(s);
+    used.push_back(s);
+  }
+  for (size_t k = 0; used.size() < nlanes && k < ctx->workers.size(); ++k) {
+    cudaStream_t s = ctx->workers[(static_cast<size_t>(ctx->next_worker) + k) % ctx->workers.size()];
     if (std::find(used.begin(), used.end(), s) == used.end()) used.push_back(s);
   }
   cudaStream_t s0 = used[0];
@@ -794,6 +808,26 @@ int align_probe_frame_latency(int32_t device, int32_t warps, int32_t ctas, int32
   }
   if (h[1]) return ALIGN_E_TIMEOUT;
   *ns_per_frame = static_cast<double>(h[0]) / static_cast<double>(frames);
+  return ALIGN_OK;
+}
+
+int align_poll_done(align_ctx* ctx, uint64_t* ids, int32_t* statuses, int32_t max, int32_t* count) {
+  if (!ctx || !count || max < 0 || (max > 0 && (!ids || !statuses))) return ALIGN_E_INVAL;
+  cudaSetDevice(ctx->device);
+  const int rc = pump(ctx, true);
+  if (rc != ALIGN_OK) return rc;
+  int32_t n = 0;
+  for (auto it = ctx->reqs.begin(); it != ctx->reqs.end() && n < max;) {
+    if (it->second.state == ReqState::Done) {
+      ids[n] = it->first;
+      statuses[n] = it->second.status;
+      ++n;
+      it = ctx->reqs.erase(it);
+    } else {
+      ++it;
+    }
+  }
+  *count = n;
   return ALIGN_OK;
 }
 
