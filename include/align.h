@@ -144,7 +144,8 @@ int align_flush(align_ctx *ctx);
 
 /* Wait up to timeout_ms (0 = just check, < 0 = forever) for a request.
    Returns ALIGN_OK when it is done, writing its result code to
-   *request_status (ALIGN_OK, ALIGN_E_NOPATH or ALIGN_E_TIMEOUT); the id is
+   *request_status (ALIGN_OK, ALIGN_E_NOPATH, ALIGN_E_TIMEOUT, or ALIGN_E_CUDA
+   if the kernel refused launch parameters that did not fit the request); the id is
    then released. Returns ALIGN_PENDING if it is still running, or
    ALIGN_E_NOTFOUND. Polling also launches queued work. */
 int align_poll(align_ctx *ctx, uint64_t request_id, int32_t timeout_ms, int32_t *request_status);

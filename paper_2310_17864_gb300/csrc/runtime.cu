@@ -57,6 +57,7 @@ void set_error(const char* what, cudaError_t e) {
 
 constexpr uint64_t kAlign = 256;
 constexpr size_t kMaxStreams = 128;  // worker streams of a context
+constexpr size_t kMaxGraphs = 16;    // cached batch graphs of a context
 inline uint64_t round_up(uint64_t v, uint64_t a) { return (v + a - 1) / a * a; }
 
 // First-fit allocator over [0, cap) with coalescing frees.
@@ -143,8 +144,21 @@ struct Request {
   int32_t status = ALIGN_PENDING;
 };
 
+// A captured batch launch, replayed for later batches with the same launch
+// structure. Its descriptor image lives at fixed addresses (device and pinned
+// host regions taken from the context's arenas), so a replay only rewrites the
+// host image and calls cudaGraphLaunch.
+struct GraphEntry {
+  std::vector<int64_t> key;
+  Alloc meta, pinned;
+  cudaGraphExec_t exec = nullptr;
+  bool busy = false;  // a batch using the fixed image has not been reaped yet
+  int seen = 0;       // batches with this structure so far (captured on the second)
+};
+
 struct Batch {
   int id = 0;
+  int graph = -1;  // index of the GraphEntry whose image this batch uses
   cudaEvent_t done = nullptr;
   Alloc meta;      // device: descriptors + per-request metadata + targets
   Alloc pinned;    // host pinned: upload image + status download
@@ -177,6 +191,7 @@ struct align_ctx {
   char* h_pinned = nullptr;
   Arena pinned_arena;
 
+  std::vector<GraphEntry> graphs;
   std::unordered_map<uint64_t, Request> reqs;
   std::deque<uint64_t> queued;
   std::map<int, Batch> batches;
@@ -221,6 +236,7 @@ int finish_batch(align_ctx* ctx, Batch& b) {
   }
   if (b.meta.live) ctx->meta_arena.release(b.meta.off, b.meta.bytes), b.meta.live = false;
   if (b.pinned.live) ctx->pinned_arena.release(b.pinned.off, b.pinned.bytes), b.pinned.live = false;
+  if (b.graph >= 0) ctx->graphs[static_cast<size_t>(b.graph)].busy = false;
   b.finished = true;
   return ALIGN_OK;
 }
@@ -307,14 +323,17 @@ int launch_queued(align_ctx* ctx) {
 
   // Descriptor image: full-mode jobs grouped by shape; checkpointed requests
   // get 1 + nck descriptors each.
-  std::map<std::tuple<int, int, int, int>, std::vector<int>> groups;  // (K, warps, ncta, F) -> req idx
+  // (K, warps, ncta, F, C) -> request indices. C is part of the key: the launch
+  // parameters (emission stage size) depend on it.
+  std::map<std::tuple<int, int, int, int, int>, std::vector<int>> groups;
   size_t njobs = 0;
   for (size_t i = 0; i < take.size(); ++i) {
     const Plan& p = take[i]->plan;
     if (p.checkpointed) {
       njobs += 1 + static_cast<size_t>(p.nck);
     } else {
-      groups[{p.shape.K, p.shape.warps, p.shape.ncta, p.frames_per_stage}].push_back(static_cast<int>(i));
+      groups[{p.shape.K, p.shape.warps, p.shape.ncta, p.frames_per_stage, static_cast<int>(take[i]->C)}].push_back(
+          static_cast<int>(i));
       njobs += 1;
     }
   }
@@ -327,6 +346,67 @@ int launch_queued(align_ctx* ctx) {
   const uint64_t off_status = up_bytes;  // pinned only: metadata download (status of every request)
   const uint64_t pin_bytes = up_bytes + round_up(take.size() * sizeof(MetaBlock), kAlign);
 
+  // CUDA graph for this launch structure (not for host-buffer requests, whose
+  // copies have per-batch host addresses).
+  bool any_host = false;
+  for (auto* r : take) any_host = any_host || r->host_io;
+  int gi = -1;
+  bool need_capture = false;
+  uint64_t up_copy = up_bytes;
+  uint64_t off_meta_dl = off_status;
+  if (!(ctx->flags & ALIGN_F_NO_GRAPHS) && !any_host) {
+    uint64_t up_bucket = 64 << 10;
+    while (up_bucket < up_bytes) up_bucket <<= 1;
+    std::vector<int64_t> key{static_cast<int64_t>(take.size()), static_cast<int64_t>(up_bucket)};
+    for (auto& kv : groups) {
+      key.insert(key.end(), {std::get<0>(kv.first), std::get<1>(kv.first), std::get<2>(kv.first),
+                             std::get<3>(kv.first), std::get<4>(kv.first), static_cast<int64_t>(kv.second.size())});
+    }
+    for (auto* r : take) {
+      if (!r->plan.checkpointed) continue;
+      const Plan& p = r->plan;
+      key.insert(key.end(), {-1, p.shape.K, p.shape.warps, p.shape.ncta, p.frames_per_stage, p.nck, r->C});
+    }
+    for (size_t k = 0; k < ctx->graphs.size(); ++k)
+      if (ctx->graphs[k].key == key) gi = static_cast<int>(k);
+    if (gi < 0) {
+      // First batch with this structure: remember it, launch directly.
+      if (ctx->graphs.size() < kMaxGraphs) {
+        GraphEntry ge;
+        ge.key = key;
+        ge.seen = 1;
+        ctx->graphs.push_back(ge);
+      }
+    } else if (ctx->graphs[static_cast<size_t>(gi)].busy) {
+      gi = -1;  // its image is in use: launch this batch directly
+    } else if (!ctx->graphs[static_cast<size_t>(gi)].meta.live) {
+      // Second batch with this structure: fix its image regions and capture.
+      GraphEntry& ge = ctx->graphs[static_cast<size_t>(gi)];
+      const uint64_t pin_need = up_bucket + round_up(take.size() * sizeof(MetaBlock), kAlign);
+      bool ok = false;
+      if (ctx->meta_arena.alloc(up_bucket, &ge.meta.off)) {
+        if (ctx->pinned_arena.alloc(pin_need, &ge.pinned.off)) {
+          ge.meta.bytes = up_bucket;
+          ge.meta.live = true;
+          ge.pinned.bytes = pin_need;
+          ge.pinned.live = true;
+          ok = true;
+        } else {
+          ctx->meta_arena.release(ge.meta.off, up_bucket);
+        }
+      }
+      if (!ok) gi = -1;
+    }
+    if (gi >= 0 && !ctx->graphs[static_cast<size_t>(gi)].meta.live) gi = -1;
+    if (gi >= 0) {
+      GraphEntry& ge = ctx->graphs[static_cast<size_t>(gi)];
+      ge.seen++;
+      need_capture = ge.exec == nullptr;
+      up_copy = up_bucket;
+      off_meta_dl = up_bucket;
+    }
+  }
+
   Batch b;
   b.id = ctx->next_batch++;
   auto unwind = [&]() {
@@ -336,29 +416,38 @@ int launch_queued(align_ctx* ctx) {
       ctx->queued.push_front(r->id);
     }
   };
-  if (!ctx->meta_arena.alloc(up_bytes, &b.meta.off)) {
-    unwind();
-    return ALIGN_OK;  // retried after other batches release metadata
+  char* h = nullptr;
+  char* d = nullptr;
+  if (gi >= 0) {
+    GraphEntry& ge = ctx->graphs[static_cast<size_t>(gi)];
+    ge.busy = true;
+    b.graph = gi;
+    h = ctx->h_pinned + ge.pinned.off;
+    d = ctx->d_meta + ge.meta.off;
+  } else {
+    if (!ctx->meta_arena.alloc(up_bytes, &b.meta.off)) {
+      unwind();
+      return ALIGN_OK;  // retried after other batches release metadata
+    }
+    b.meta.bytes = up_bytes;
+    b.meta.live = true;
+    if (!ctx->pinned_arena.alloc(pin_bytes, &b.pinned.off)) {
+      ctx->meta_arena.release(b.meta.off, b.meta.bytes);
+      unwind();
+      return ALIGN_OK;
+    }
+    b.pinned.bytes = pin_bytes;
+    b.pinned.live = true;
+    h = ctx->h_pinned + b.pinned.off;
+    d = ctx->d_meta + b.meta.off;
   }
-  b.meta.bytes = up_bytes;
-  b.meta.live = true;
-  if (!ctx->pinned_arena.alloc(pin_bytes, &b.pinned.off)) {
-    ctx->meta_arena.release(b.meta.off, b.meta.bytes);
-    unwind();
-    return ALIGN_OK;
-  }
-  b.pinned.bytes = pin_bytes;
-  b.pinned.live = true;
-
-  char* h = ctx->h_pinned + b.pinned.off;
-  char* d = ctx->d_meta + b.meta.off;
   FwdJob* hjobs = reinterpret_cast<FwdJob*>(h + off_jobs);
   MetaBlock* hmeta = reinterpret_cast<MetaBlock*>(h + off_metas);
   int32_t* htgt = reinterpret_cast<int32_t*>(h + off_tgts);
   const FwdJob* djobs = reinterpret_cast<const FwdJob*>(d + off_jobs);
   MetaBlock* dmeta = reinterpret_cast<MetaBlock*>(d + off_metas);
   const int32_t* dtgt = reinterpret_cast<const int32_t*>(d + off_tgts);
-  b.h_meta = reinterpret_cast<MetaBlock*>(h + off_status);
+  b.h_meta = reinterpret_cast<MetaBlock*>(h + off_meta_dl);
 
   // Per-request metadata, targets and device views of inputs / outputs.
   std::vector<const int32_t*> req_tgt(take.size());
@@ -504,7 +593,11 @@ int launch_queued(align_ctx* ctx) {
   }
   cudaStream_t s0 = used[0];
   for (cudaStream_t s : used) CU(cudaStreamWaitEvent(s, fork, 0));
-  CU(cudaMemcpyAsync(d, h, up_bytes, cudaMemcpyHostToDevice, s0));
+  uint64_t nkernels = 0;
+  // Everything from the descriptor upload to the status download; issued
+  // directly, or captured once into the batch graph.
+  auto body = [&]() -> int {
+  CU(cudaMemcpyAsync(d, h, up_copy, cudaMemcpyHostToDevice, s0));
   for (size_t i = 0; i < take.size(); ++i) {
     Request& r = *take[i];
     if (r.host_io) {
@@ -526,7 +619,7 @@ int launch_queued(align_ctx* ctx) {
       set_error("launch_trellis", e);
       return ALIGN_E_CUDA;
     }
-    ctx->stats.kernel_launches++;
+    ++nkernels;
   }
   for (const CkLaunch& cl : cklaunch) {
     cudaStream_t s = used[lane_i++ % used.size()];
@@ -539,7 +632,7 @@ int launch_queued(align_ctx* ctx) {
         set_error("launch_trellis", e);
         return ALIGN_E_CUDA;
       }
-      ctx->stats.kernel_launches++;
+      ++nkernels;
     }
   }
   // Join, download statuses and host outputs, record completion.
@@ -559,6 +652,48 @@ int launch_queued(align_ctx* ctx) {
     CU(cudaMemcpyAsync(r.out.scores, req_out[i].scores, T * 4, cudaMemcpyDeviceToHost, s0));
     CU(cudaMemcpyAsync(r.out.total, req_out[i].total, 4, cudaMemcpyDeviceToHost, s0));
     if (r.out.states) CU(cudaMemcpyAsync(r.out.states, req_out[i].states, T * 4, cudaMemcpyDeviceToHost, s0));
+  }
+  return ALIGN_OK;
+  };
+
+  if (gi >= 0 && !need_capture) {
+    const uint64_t nk = glaunch.size() + [&] {
+      uint64_t c = 0;
+      for (const CkLaunch& cl : cklaunch) c += static_cast<uint64_t>(take[cl.req]->plan.nck) + 1;
+      return c;
+    }();
+    CU(cudaGraphLaunch(ctx->graphs[static_cast<size_t>(gi)].exec, s0));
+    ctx->stats.graph_launches++;
+    ctx->stats.kernel_launches += nk;
+  } else if (gi >= 0) {
+    GraphEntry& ge = ctx->graphs[static_cast<size_t>(gi)];
+    cudaGraph_t graph = nullptr;
+    int rc = ALIGN_E_CUDA;
+    if (cudaStreamBeginCapture(s0, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+      rc = body();
+      const cudaError_t ce = cudaStreamEndCapture(s0, &graph);
+      if (ce != cudaSuccess) rc = ALIGN_E_CUDA;
+    }
+    if (rc == ALIGN_OK && graph && cudaGraphInstantiate(&ge.exec, graph, 0) == cudaSuccess) {
+      cudaGraphDestroy(graph);
+      CU(cudaGraphLaunch(ge.exec, s0));
+      ctx->stats.graph_launches++;
+      ctx->stats.kernel_launches += nkernels;
+    } else {
+      // Capture not possible here: forget the entry's key and launch directly.
+      if (graph) cudaGraphDestroy(graph);
+      (void)cudaGetLastError();
+      ge.exec = nullptr;
+      ge.key.clear();
+      nkernels = 0;
+      rc = body();
+      if (rc != ALIGN_OK) return rc;
+      ctx->stats.kernel_launches += nkernels;
+    }
+  } else {
+    const int rc = body();
+    if (rc != ALIGN_OK) return rc;
+    ctx->stats.kernel_launches += nkernels;
   }
   b.done = take_event(ctx);
   b.events.push_back(b.done);
@@ -686,6 +821,8 @@ int align_destroy(align_ctx* ctx) {
   for (auto& kv : ctx->batches)
     for (cudaEvent_t e : kv.second.events) cudaEventDestroy(e);
   for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
+  for (GraphEntry& ge : ctx->graphs)
+    if (ge.exec) cudaGraphExecDestroy(ge.exec);
   for (cudaStream_t s : ctx->workers) {
     cudaStreamSynchronize(s);
     cudaStreamDestroy(s);

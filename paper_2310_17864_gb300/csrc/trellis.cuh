@@ -94,6 +94,7 @@ constexpr int32_t kStOk = 0;
 constexpr int32_t kStPending = 1;
 constexpr int32_t kStNoPath = -6;
 constexpr int32_t kStTimeout = -7;
+constexpr int32_t kStBadLaunch = -8;  // launch parameters do not fit the job (reported as ALIGN_E_CUDA)
 
 // Host-side launch entry points (defined in trellis_kernels.cu).
 struct LaunchShape {

@@ -286,6 +286,14 @@ __global__ void __launch_bounds__(512)
   const int ck_every = J.ck_every;
   const int ck_stride = J.ck_stride;
 
+  // Launch parameters must fit the job: a stage holds F rows of C floats and
+  // the team holds every state. The check is uniform over the cluster (same
+  // job, same parameters), so every CTA leaves before any cluster barrier.
+  if (F * C * 4 > P.stage_bytes || static_cast<int64_t>(ncta) * W * 32 * K < S) {
+    if (threadIdx.x == 0 && crank == 0) atomicExch(J.status, kStBadLaunch);
+    return;
+  }
+
   // ---- shared state: rings zeroed, barriers initialised ----
   for (int i = threadIdx.x; i < W * P.rb; i += blockDim.x) ring[i] = 0ull;
   if (threadIdx.x == 0) {

@@ -265,3 +265,33 @@ def test_watchdog_timeout_keeps_context_usable():
         compare(r, u.lp.numpy(), u.targets, 0, "after timeout")
     finally:
         ok.close()
+
+
+def test_graph_replay_equals_direct_launch():
+    """A batch with the same launch structure is captured once and replayed;
+    results equal direct launches bit for bit."""
+    build.build()
+    specs = synth.specs(2)[:20]
+    b = synth.make_batch(specs, device="cuda")
+    outs = lambda: [(torch.empty(s.T, dtype=torch.int32, device="cuda"), torch.empty(s.T, device="cuda"),
+                     torch.empty(1, device="cuda"), torch.empty(s.T, dtype=torch.int32, device="cuda")) for s in specs]
+    g = align.Aligner(device=0, batched=True)
+    d = align.Aligner(device=0, batched=True, graphs=False)
+    try:
+        ref = d.submit_batch([(b.utt(i), b.targets[i], 0, o) for i, o in enumerate(outs())])
+        d.flush()
+        for r in ref:
+            d.poll(r)
+        for _ in range(3):
+            rs = g.submit_batch([(b.utt(i), b.targets[i], 0, o) for i, o in enumerate(outs())])
+            g.flush()
+            for r, x in zip(rs, ref):
+                g.poll(r)
+                assert r.status == x.status == 0
+                assert torch.equal(r.path, x.path) and torch.equal(r.states, x.states)
+                assert r.scores.cpu().numpy().tobytes() == x.scores.cpu().numpy().tobytes()
+        assert g.stats()["graph_launches"] == 2  # captured on the second batch, replayed on the third
+        assert d.stats()["graph_launches"] == 0
+    finally:
+        g.close()
+        d.close()
