@@ -62,8 +62,10 @@ def serving_run(align, serve, synth, torch, dev: int, n: int) -> dict:
     """Workload 5: Poisson arrivals served by the continuous-batching loop with a
     16 GiB backpointer budget. Saturation = every request arriving at time 0;
     then offered loads of 0.5, 0.8 and 0.95 times the saturation request rate."""
+    from paper_2310_17864_gb300 import autotune
     b = synth.make_batch(synth.specs(5, n=n), device=f"cuda:{dev}")
     al = align.Aligner(device=dev, batched=True, bp_budget_bytes=16 << 30)
+    autotune.apply(al)
     try:
         warm = serve.poisson_requests(b, rate_per_s=1e9, seed=1)
         serve.serve(al, warm)
@@ -229,7 +231,9 @@ def main():
         outs.append((torch.empty(T, dtype=torch.int32, device=dev), torch.empty(T, dtype=torch.float32, device=dev),
                      torch.empty(1, dtype=torch.float32, device=dev), None))
     stream = torch.cuda.Stream(dev)
+    from paper_2310_17864_gb300 import autotune
     al = align.Aligner(device=dev, batched=True, stream=stream, bp_budget_bytes=4 << 30)
+    tuned = autotune.apply(al)  # per-range kernel shapes measured on GB300 (tuning_gb300.json)
     flush_buf = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
 
     items = [(utts[i], batch.targets[i], 0, outs[i]) for i in range(n)]
@@ -275,6 +279,7 @@ def main():
     plain = None
     if not args.no_plain:
         pl = align.Aligner(device=dev, stream=stream, bp_budget_bytes=4 << 30)
+        autotune.apply(pl)
         lat = []
         for k in range(2):
             flush_buf.fill_(1)
@@ -371,7 +376,8 @@ def main():
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "utterances": n, "cells_per_step": cells, "T_max": T_max,
-                   "l2": "flushed (256 MiB write) before every timed step", "parallelism": f"replicas{world}"},
+                   "l2": "flushed (256 MiB write) before every timed step", "parallelism": f"replicas{world}",
+                   "tuning": autotune.load() if tuned else "built-in default (K=4, 4 warps per CTA)"},
         "p50_ms": ms, "p99_ms": float(np.percentile(times, 99)),
         "plain": plain,
         "e2e": e2e,

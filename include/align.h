@@ -196,6 +196,13 @@ int align_set_tuning(align_ctx *ctx, int32_t states_per_lane, int32_t cta_warps,
 int align_probe_frame_latency(int32_t device, int32_t warps, int32_t ctas, int32_t frames,
                               double *ns_per_frame);
 
+/* Per-range tuning measured on this GPU: transcripts with S <= s_max states
+   use states_per_lane (2, 4, 8 or 16) and cta_warps (1..16); the smallest
+   matching s_max wins; ranges not covered use align_set_tuning's values.
+   s_max <= 0 clears the table. Up to 16 ranges (ALIGN_E_AGAIN beyond). The
+   autotuner of the Python package fills this table from timed trials. */
+int align_set_tuning_bucket(align_ctx *ctx, int32_t s_max, int32_t states_per_lane, int32_t cta_warps);
+
 /* ---- allocation-free entry point ---------------------------------------- */
 
 /* Align one utterance without allocating any memory, for callers that cannot

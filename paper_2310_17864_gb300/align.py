@@ -40,7 +40,7 @@ ALIGN_F_TEST_STALL = 0x80000000
 # Every entry point declared in include/align.h.
 EXPORTS = ("align_create", "align_destroy", "align_submit", "align_submit_host", "align_submit_batch", "align_flush",
            "align_poll", "align_poll_done", "align_join", "align_get_stats", "align_status_string", "align_last_error",
-           "align_set_tuning", "align_validate", "align_plan", "align_probe_frame_latency",
+           "align_set_tuning", "align_set_tuning_bucket", "align_validate", "align_plan", "align_probe_frame_latency",
            "align_forced_noalloc", "align_noalloc_last_error")
 
 
@@ -115,6 +115,7 @@ def lib() -> ctypes.CDLL:
         L.align_last_error.argtypes = []
         L.align_last_error.restype = ctypes.c_char_p
         L.align_set_tuning.argtypes = [vp, i32, i32, i32]
+        L.align_set_tuning_bucket.argtypes = [vp, i32, i32, i32]
         L.align_probe_frame_latency.argtypes = [i32, i32, i32, i32, ctypes.POINTER(ctypes.c_double)]
         L.align_forced_noalloc.argtypes = [vp, i64, i64, vp, i64, i32, AlignOut, vp, ctypes.POINTER(i32)]
         L.align_noalloc_last_error.argtypes = []
@@ -243,6 +244,10 @@ def align_forced_noalloc(log_probs_ptr: int, T: int, C: int, targets, blank: int
 
 def align_noalloc_last_error() -> str:
     return lib().align_noalloc_last_error().decode()
+
+
+def align_set_tuning_bucket(ctx, s_max: int, states_per_lane: int = 0, cta_warps: int = 0) -> None:
+    _check(lib().align_set_tuning_bucket(ctx, s_max, states_per_lane, cta_warps), "align_set_tuning_bucket")
 
 
 def align_validate(targets, C: int, blank: int, T: int) -> tuple[int, int]:
@@ -405,3 +410,9 @@ class Aligner:
 
     def set_tuning(self, states_per_lane: int = 0, cta_warps: int = 0, max_cluster: int = 0) -> None:
         align_set_tuning(self.ctx, states_per_lane, cta_warps, max_cluster)
+
+    def set_tuning_table(self, table) -> None:
+        """table: iterable of (s_max, states_per_lane, cta_warps); replaces the current table."""
+        align_set_tuning_bucket(self.ctx, 0)
+        for s_max, k, cw in table:
+            align_set_tuning_bucket(self.ctx, int(s_max), int(k), int(cw))

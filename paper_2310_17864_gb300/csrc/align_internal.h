@@ -7,12 +7,22 @@
 namespace gb300_align {
 
 // Kernel-shape choices (replaced by measurements through align_set_tuning).
+struct TuneBucket {
+  int s_max;      // applies to transcripts with S <= s_max states
+  int K;          // states per lane
+  int cta_warps;  // warps per CTA before the team is split over a cluster
+};
+
 struct TuneTable {
-  int K = 4;             // states per lane
+  int K = 4;             // states per lane (when no bucket matches)
   int cta_warps = 4;     // warps per CTA before a team is split over a cluster
   int max_warps = 16;    // hard limit of warps per CTA (the kernel is built for 512 threads)
   int max_cluster = 16;  // CTAs per cluster for long transcripts
+  int nbuckets = 0;      // measured choices per range of S, sorted by s_max
+  TuneBucket buckets[16];
 };
+// The (K, cta_warps) that apply to a transcript of S states.
+TuneTable resolve_tuning(const TuneTable& t, int64_t S);
 TuneTable default_tune_table();
 
 struct Plan {

@@ -16,6 +16,18 @@ inline uint64_t round_up(uint64_t v, uint64_t a) { return ceil_div(v, a) * a; }
 
 TuneTable default_tune_table() { return TuneTable{}; }
 
+TuneTable resolve_tuning(const TuneTable& t, int64_t S) {
+  TuneTable r = t;
+  for (int i = 0; i < t.nbuckets; ++i) {
+    if (S <= t.buckets[i].s_max) {
+      r.K = t.buckets[i].K;
+      r.cta_warps = t.buckets[i].cta_warps;
+      break;
+    }
+  }
+  return r;
+}
+
 int validate_request(const int32_t* targets, int64_t L, int64_t C, int32_t blank, int64_t T, int64_t* repeats) {
   if (T < 1 || C < 2 || L < 0 || blank < 0 || blank >= C) return ALIGN_E_INVAL;
   if (L > 0 && targets == nullptr) return ALIGN_E_INVAL;
@@ -30,10 +42,11 @@ int validate_request(const int32_t* targets, int64_t L, int64_t C, int32_t blank
   return ALIGN_OK;
 }
 
-int make_plan(const TuneTable& tune, int64_t T, int64_t C, int64_t L, uint64_t budget, bool force_checkpoint,
+int make_plan(const TuneTable& tune_in, int64_t T, int64_t C, int64_t L, uint64_t budget, bool force_checkpoint,
               Plan* out) {
   Plan p{};
   const int64_t S = 2 * L + 1;
+  const TuneTable tune = resolve_tuning(tune_in, S);
   // Shape: one CTA of up to cta_warps warps, else a cluster of CTAs of at most
   // cta_warps warps (portable sizes first), else wider CTAs and larger K.
   const int K = tune.K;

@@ -1007,6 +1007,28 @@ const char* align_status_string(int32_t code) {
 
 const char* align_last_error(void) { return g_last_error; }
 
+int align_set_tuning_bucket(align_ctx* ctx, int32_t s_max, int32_t states_per_lane, int32_t cta_warps) {
+  if (!ctx) return ALIGN_E_INVAL;
+  if (s_max <= 0) {  // clear the table
+    ctx->tune.nbuckets = 0;
+    return ALIGN_OK;
+  }
+  if ((states_per_lane != 2 && states_per_lane != 4 && states_per_lane != 8 && states_per_lane != 16) ||
+      cta_warps < 1 || cta_warps > 16)
+    return ALIGN_E_INVAL;
+  TuneTable& t = ctx->tune;
+  for (int i = 0; i < t.nbuckets; ++i) {
+    if (t.buckets[i].s_max == s_max) {
+      t.buckets[i] = TuneBucket{s_max, states_per_lane, cta_warps};
+      return ALIGN_OK;
+    }
+  }
+  if (t.nbuckets >= 16) return ALIGN_E_AGAIN;
+  t.buckets[t.nbuckets++] = TuneBucket{s_max, states_per_lane, cta_warps};
+  std::sort(t.buckets, t.buckets + t.nbuckets, [](const TuneBucket& a, const TuneBucket& b) { return a.s_max < b.s_max; });
+  return ALIGN_OK;
+}
+
 int align_set_tuning(align_ctx* ctx, int32_t states_per_lane, int32_t cta_warps, int32_t max_cluster) {
   if (!ctx) return ALIGN_E_INVAL;
   if (states_per_lane && states_per_lane != 2 && states_per_lane != 4 && states_per_lane != 8 &&
