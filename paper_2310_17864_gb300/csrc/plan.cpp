@@ -72,9 +72,11 @@ int make_plan(const TuneTable& tune_in, int64_t T, int64_t C, int64_t L, uint64_
   }
   if (!found) return ALIGN_E_TOO_LARGE;
   // Emission staging: stages of 4 KB (32 frames of a 32-class row), up to 8 KB
-  // for wide rows.
+  // for wide rows; frames per stage a power of two dividing the anchor window.
   const int64_t stage_budget = p.shape.warps >= 2 ? 8192 : 4096;
-  p.frames_per_stage = static_cast<int>(std::clamp<int64_t>(stage_budget / (4 * C), 1, 32));
+  const int64_t fmax = std::clamp<int64_t>(stage_budget / (4 * C), 1, kAnchorD);
+  p.frames_per_stage = 1;
+  while (p.frames_per_stage * 2 <= fmax) p.frames_per_stage *= 2;
   const uint64_t warps = static_cast<uint64_t>(p.shape.warps) * p.shape.ncta;
   const uint64_t row_bytes = warps * bp_words(p.shape.K) * 4ull;
   // Anchor rows: one row of S bytes (rounded to 16) per kAnchorD frames.
@@ -82,7 +84,10 @@ int make_plan(const TuneTable& tune_in, int64_t T, int64_t C, int64_t L, uint64_
   const auto zrows = [](int64_t frames) { return static_cast<uint64_t>((frames + kAnchorD - 1) / kAnchorD); };
   p.z_off = round_up(row_bytes * static_cast<uint64_t>(std::max<int64_t>(T - 1, 0)), 256);
   p.bp_bytes = p.z_off + round_up(zrows(T - 1) * p.zstride, 256);
-  p.ck_every = std::max(1, static_cast<int>(std::ceil(std::sqrt(static_cast<double>(T)))));
+  // About sqrt(T) frames per checkpoint segment, rounded up to whole anchor
+  // windows so that checkpoint frames end windows.
+  p.ck_every = static_cast<int>(
+      round_up(static_cast<uint64_t>(std::max(1.0, std::ceil(std::sqrt(static_cast<double>(T))))), kAnchorD));
   p.nck = static_cast<int>((T - 1) / p.ck_every + 1);
   p.ck_stride = static_cast<int>(round_up(static_cast<uint64_t>(S), 4));
   p.ckpt_bytes = round_up(static_cast<uint64_t>(p.nck) * p.ck_stride * 4ull, 256);

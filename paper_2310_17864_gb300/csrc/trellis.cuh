@@ -39,7 +39,7 @@
 
 namespace gb300_align {
 
-constexpr int kStages = 10;           // emission ring stages per CTA
+constexpr int kMaxStages = 10;        // emission ring stages per CTA, at most (planned per shape)
 constexpr int kLead = 4;              // stages in flight ahead of the consumer
 constexpr int kBtWindow = 32;         // frames per backtrack window
 constexpr int kAnchorD = 32;          // frames between anchor rows (== kBtWindow)
@@ -86,6 +86,7 @@ struct FwdParams {
   int32_t off_ring;        // shared-memory offsets
   int32_t off_stage;
   int32_t off_bt;
+  int32_t stages;          // emission stages in the ring (kLead .. kMaxStages)
   uint64_t wait_limit_ns;  // limit of every spin wait
 };
 

@@ -103,12 +103,12 @@ __device__ __forceinline__ void cp_async_mbar_arrive(uint64_t* bar) {
 
 // ------------------------------------------------------- shared-memory head --
 struct SmemHead {
-  uint64_t full[kStages];   // emission stage filled
-  uint64_t empty[kStages];  // emission stage released by every warp
+  uint64_t full[kMaxStages];   // emission stage filled
+  uint64_t empty[kMaxStages];  // emission stage released by every warp
   int32_t abort;            // set by any thread of this CTA whose wait hit the limit
   uint32_t unused;
   uint64_t sink;            // scratch slot written by the last warp of the team
-  int32_t pad[(256 - 16 * kStages - 16) / 4];
+  int32_t pad[(256 - 16 * kMaxStages - 16) / 4];
 };
 static_assert(sizeof(SmemHead) == 256, "head size");
 
@@ -276,7 +276,7 @@ __global__ void __launch_bounds__(512)
   const int s0 = (g * 32 + lane) * K;               // first state of this lane
   const int F = P.frames_per_stage;
   const int rb_mask = P.rb - 1;
-  const int nchunks = (t_end - t_begin + F - 1) / F;
+  const int nchunks = (t_end - 1 - t_begin + F - 1) / F;  // chunks of frames t_begin+1 .. t_end-1
   const bool bulk = (J.flags & kJobBulkRows) != 0;
   const uint64_t limit = P.wait_limit_ns;
   const float* __restrict__ lp = J.lp;
@@ -289,7 +289,13 @@ __global__ void __launch_bounds__(512)
   // Launch parameters must fit the job: a stage holds F rows of C floats and
   // the team holds every state. The check is uniform over the cluster (same
   // job, same parameters), so every CTA leaves before any cluster barrier.
-  if (F * C * 4 > P.stage_bytes || static_cast<int64_t>(ncta) * W * 32 * K < S) {
+  // F and the receive block are powers of two dividing kAnchorD, and checkpoint
+  // frames fall on window ends.
+  const bool pow2_ok = F >= 1 && F <= kAnchorD && (F & (F - 1)) == 0 && P.block >= 1 && P.block <= kAnchorD &&
+                       (P.block & (P.block - 1)) == 0;
+  const bool ck_ok = ckpt == nullptr || (ck_every > 0 && ck_every % kAnchorD == 0 && t_begin % ck_every == 0);
+  if (F * C * 4 > P.stage_bytes || static_cast<int64_t>(ncta) * W * 32 * K < S || P.stages < kLead ||
+      P.stages > kMaxStages || !pow2_ok || !ck_ok) {
     if (threadIdx.x == 0 && crank == 0) atomicExch(J.status, kStBadLaunch);
     return;
   }
@@ -297,7 +303,7 @@ __global__ void __launch_bounds__(512)
   // ---- shared state: rings zeroed, barriers initialised ----
   for (int i = threadIdx.x; i < W * P.rb; i += blockDim.x) ring[i] = 0ull;
   if (threadIdx.x == 0) {
-    for (int st = 0; st < kStages; ++st) {
+    for (int st = 0; st < P.stages; ++st) {
       mbar_init(&head->full[st], bulk ? 1u : 32u);
       mbar_init(&head->empty[st], static_cast<uint32_t>(W));
     }
@@ -324,57 +330,61 @@ __global__ void __launch_bounds__(512)
   }
 
   // ---- emission staging (warp 0 of each CTA is the producer) ----
-  int issued = 0;
-  auto issue_chunk = [&](int c) {
-    const int st = c % kStages;
-    const int f0 = t_begin + c * F;
+  // Chunk c holds the rows of frames t_begin+1+c*F .. t_begin+(c+1)*F and goes
+  // to stage c mod stages (round c / stages). F is a power of two dividing
+  // kAnchorD, so chunks tile the anchor windows. The row of frame t_begin is
+  // read directly by the lanes that need it.
+  int issued = 0;         // chunks issued (producer)
+  int p_stage = 0;        // stage of chunk `issued`
+  uint32_t p_round = 0;   // round of chunk `issued`
+  auto issue_next = [&]() {
+    const int f0 = t_begin + 1 + issued * F;
     const int nf = min(F, t_end - f0);
     const float* src = lp + static_cast<size_t>(f0) * C;
-    float* dst = reinterpret_cast<float*>(stages + st * P.stage_bytes);
+    float* dst = reinterpret_cast<float*>(stages + p_stage * P.stage_bytes);
     if (bulk) {
       if (lane == 0) {
         const uint32_t bytes = static_cast<uint32_t>(nf * C * 4);
-        mbar_arrive_expect_tx(&head->full[st], bytes);
-        bulk_g2s(dst, src, bytes, &head->full[st]);
+        mbar_arrive_expect_tx(&head->full[p_stage], bytes);
+        bulk_g2s(dst, src, bytes, &head->full[p_stage]);
       }
     } else {
       const int n = nf * C;
       for (int i = lane; i < n; i += 32) cp_async4(dst + i, src + i);
-      cp_async_mbar_arrive(&head->full[st]);
+      cp_async_mbar_arrive(&head->full[p_stage]);
+    }
+    ++issued;
+    if (++p_stage == P.stages) {
+      p_stage = 0;
+      ++p_round;
     }
   };
   if (warp == 0) {
-    for (int c = 0; c < min(kLead, nchunks); ++c) issue_chunk(c);
-    issued = min(kLead, nchunks);
+    const int first = min(kLead, nchunks);
+    for (int c = 0; c < first; ++c) issue_next();
   }
 
   // ---- frame t_begin: initialisation ----
   float a[K];
   int A[K];  // anchors: state at the last anchor frame on the best path to each state
-  int chunk = 0;
-  bool ok = warp_wait_phase(&head->full[0], 0, abort, limit, lane);
-  if (ok) {
-    const float* row = reinterpret_cast<const float*>(stages);
-    if (J.alpha_in == nullptr) {
-      const float eb = row[blank];
+  if (J.alpha_in == nullptr) {
+    // alpha_0: paths start in the blank (state 0) or the first label (state 1).
+    const float* row = lp + static_cast<size_t>(t_begin) * C;
 #pragma unroll
-      for (int j = 0; j < K; ++j) {
-        const int s = s0 + j;
-        a[j] = (s == 0) ? eb : ((s == 1 && S > 1) ? row[col[0]] : -INFINITY);
-      }
-    } else {
-#pragma unroll
-      for (int j = 0; j < K; ++j) {
-        const int s = s0 + j;
-        a[j] = (s < S) ? __ldg(J.alpha_in + s) : -INFINITY;
-      }
+    for (int j = 0; j < K; ++j) {
+      const int s = s0 + j;
+      a[j] = (s == 0) ? __ldg(row + blank) : ((s == 1 && S > 1) ? __ldg(row + col[0]) : -INFINITY);
     }
   } else {
 #pragma unroll
-    for (int j = 0; j < K; ++j) a[j] = -INFINITY;
+    for (int j = 0; j < K; ++j) {
+      const int s = s0 + j;
+      a[j] = (s < S) ? __ldg(J.alpha_in + s) : -INFINITY;
+    }
   }
 #pragma unroll
   for (int j = 0; j < K; ++j) A[j] = s0 + j;
+  const bool ok = true;
 
   // Ring endpoints. Each warp receives alpha(first state - 1) of frame t-1
   // from its own ring (written by the previous warp of the team, in this CTA
@@ -449,72 +459,97 @@ __global__ void __launch_bounds__(512)
   }
 
   // ---- frames t_begin+1 .. t_end-1 ----
-  // Frame of the next checkpoint row; without checkpoints a value beyond any
-  // frame count that still leaves next_ck + 1 - t positive.
+  // Frames run in anchor windows of kAnchorD (an anchor row after each),
+  // windows in receive blocks of B = P.block frames (one ring wait each) and
+  // in emission chunks of F frames. B and F are powers of two dividing
+  // kAnchorD, so a sub-run of min(B, F) frames crosses none of these
+  // boundaries and the bookkeeping is incremental (no division in the loop).
+  // Checkpoint frames are multiples of ck_every, itself a multiple of
+  // kAnchorD, so they fall on window ends.
   int next_ck = (ckpt != nullptr) ? (t_begin / ck_every + 1) * ck_every : (1 << 30);
-  int next_anchor = t_begin + kAnchorD;
+  const int B = P.block;
+  const int R = min(B, F);
   uint32_t* bpw = bp + static_cast<size_t>(g) * bp_rows * NW;  // row 0 of this warp (unused if bp == nullptr)
   const bool write_bp = (bp != nullptr) && is_l0;
   const float* stage_f = reinterpret_cast<const float*>(stages);
   const int stage_floats = P.stage_bytes / 4;
+  int c_stage = 0;        // stage of the current chunk
+  uint32_t c_round = 0;   // its round
+  int ridx = 0;           // row of frame t in the stage ring (floats)
+  float rv = -INFINITY;   // block receive: lane i holds the word of frame (block start - 1 + i)
+  int roff = 0;
+  int bi = 0;             // frame index within the current block
   int t = t_begin + 1;
-  while (ok && t < t_end) {
-    const int ft = t - t_begin;
-    const int c = ft / F;
-    if (c != chunk) {  // entering the next stage of emission rows
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&head->empty[chunk % kStages]);
-      chunk = c;
-      if (__any_sync(kFull, *abort != 0)) break;
-      if (warp == 0 && chunk + kLead - 1 < nchunks) {
-        // Load chunk + kLead - 1 into the stage that held chunk + kLead - 1 - kStages,
-        // once every warp has released it.
-        const int old = chunk + kLead - 1 - kStages;
-        if (old >= 0 && !warp_wait_phase(&head->empty[old % kStages], (old / kStages) & 1, abort, limit, lane))
-          break;
-        issue_chunk(chunk + kLead - 1);
-        issued = chunk + kLead;
+  while (t < t_end) {
+    const int ft = t - t_begin - 1;  // frames computed so far
+    if ((ft & (F - 1)) == 0) {       // first frame of a chunk
+      if (ft != 0) {
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&head->empty[c_stage]);
+        if (++c_stage == P.stages) {
+          c_stage = 0;
+          ++c_round;
+        }
+        if (warp == 0 && issued < nchunks) {
+          // Refill kLead - 1 chunks ahead, into the stage of chunk
+          // issued - stages once every warp has released it.
+          if (p_round > 0 && !warp_wait_phase(&head->empty[p_stage], (p_round - 1) & 1u, abort, limit, lane)) break;
+          issue_next();
+        }
       }
-      if (!warp_wait_phase(&head->full[chunk % kStages], (chunk / kStages) & 1, abort, limit, lane)) break;
+      if (__any_sync(kFull, *abort != 0)) break;
+      if (!warp_wait_phase(&head->full[c_stage], c_round & 1u, abort, limit, lane)) break;
+      ridx = c_stage * stage_floats;
     }
-    const int in_chunk = ft - c * F;
-    int ridx = (c % kStages) * stage_floats + in_chunk * C;  // row of frame t in the stage ring
-    const int n = min(min(min(F - in_chunk, t_end - t), min(next_ck, next_anchor) + 1 - t), P.block);
-
-    // Block receive: lane i takes the word of frame t-1+i (i < n).
-    float rv = -INFINITY;
-    int roff = 0;
-    if (recv_left) {
-      const int f = t - 1 + (lane < n ? lane : 0);
-      const uint64_t v = *reinterpret_cast<const volatile uint64_t*>(my_ring + (f & rb_mask));
-      const bool mine = static_cast<uint32_t>(v >> 40) == ((static_cast<uint32_t>(f) + 1u) & kTagMask);
-      uint64_t vv = v;
-      if (!__all_sync(kFull, mine)) vv = ring_block_spin(my_ring, t - 1, n, rb_mask, lane, abort, limit);
-      rv = __uint_as_float(static_cast<uint32_t>(vv));
-      roff = static_cast<int>((vv >> 32) & 0xffu);
-      // Frames < t + n - 1 are read after this block: tell the producer.
-      if (is_l0) st_remote_u32(prog_dst, static_cast<uint32_t>(t + n - 1));
+    if ((ft & (B - 1)) == 0) {  // first frame of a receive block
+      const int nb = min(B, t_end - t);
+      // Block receive: lane i takes the word of frame t-1+i (i < nb).
+      if (recv_left) {
+        const int f = t - 1 + (lane < nb ? lane : 0);
+        const uint64_t v = *reinterpret_cast<const volatile uint64_t*>(my_ring + (f & rb_mask));
+        const bool mine = static_cast<uint32_t>(v >> 40) == ((static_cast<uint32_t>(f) + 1u) & kTagMask);
+        uint64_t vv = v;
+        if (!__all_sync(kFull, mine)) vv = ring_block_spin(my_ring, t - 1, nb, rb_mask, lane, abort, limit);
+        rv = __uint_as_float(static_cast<uint32_t>(vv));
+        roff = static_cast<int>((vv >> 32) & 0xffu);
+        // Frames < t + nb - 1 are read after this block: tell the producer.
+        if (is_l0) st_remote_u32(prog_dst, static_cast<uint32_t>(t + nb - 1));
+      }
+      // Frame t-1 ends a window when this block starts one: its sender reset
+      // its anchors after sending it.
+      if (is_l0 && (ft & (kAnchorD - 1)) == 0) roff = 0;
+      // Block send: slots t .. t+nb-1 reuse those of frames t-rb .. t+nb-1-rb.
+      if (has_next && t + nb - 1 - P.rb >= prog_seen) {
+        prog_seen = static_cast<int>(prog_spin(my_prog, t + nb - 1 - P.rb, abort, limit));
+      }
+      bi = 0;
     }
-    // Frame t-1 may be an anchor frame: the sender's anchors were reset after it sent.
-    if (is_l0 && ((t - 1 - t_begin) % kAnchorD) == 0) roff = 0;
-    // Block send: slots t .. t+n-1 reuse those of frames t-rb .. t+n-1-rb.
-    if (has_next && t + n - 1 - P.rb >= prog_seen) {
-      prog_seen = static_cast<int>(prog_spin(my_prog, t + n - 1 - P.rb, abort, limit));
-    }
+    const int n = min(R, t_end - t);
 
     // Emissions of this lane's states (blank column shared by the even states),
-    // loaded one frame ahead of their use.
+    // loaded one frame ahead of their use. The ring has one spare row after
+    // its last stage, so the look-ahead past a chunk's end stays in bounds.
     float eb_n = stage_f[ridx + blank];
     float el_n[K / 2];
 #pragma unroll
     for (int q = 0; q < K / 2; ++q) el_n[q] = stage_f[ridx + col[q]];
-#pragma unroll 2
+    // Backpointer words of the previous frame: stored one frame late, after
+    // this frame's loads and shuffles are issued, so the ballot latency is
+    // not on the per-frame path.
+    uint32_t padv[K];
+    uint32_t pskp[K / 2];
+#pragma unroll
+    for (int j = 0; j < K; ++j) padv[j] = 0u;
+#pragma unroll
+    for (int j = 0; j < K / 2; ++j) pskp[j] = 0u;
+    bool pend = false;
+#pragma unroll(K == 2 ? 2 : 1)
     for (int i = 0; i < n; ++i, ++t) {
       const float eb = eb_n;
       float el[K / 2];
 #pragma unroll
       for (int q = 0; q < K / 2; ++q) el[q] = el_n[q];
-      ridx += (i + 1 < n) ? C : 0;
+      ridx += C;
       eb_n = stage_f[ridx + blank];
 #pragma unroll
       for (int q = 0; q < K / 2; ++q) el_n[q] = stage_f[ridx + col[q]];
@@ -522,10 +557,11 @@ __global__ void __launch_bounds__(512)
       // alpha_{t-1}(s0 - 1) and its anchor: lane below by shuffle, lane 0 from the block.
       const float shf = __shfl_up_sync(kFull, a[K - 1], 1);
       const int shA = __shfl_up_sync(kFull, A[K - 1], 1);
-      const float blk = __shfl_sync(kFull, rv, i);
-      const int blko = __shfl_sync(kFull, roff, i);
+      const float blk = __shfl_sync(kFull, rv, bi + i);
+      const int blko = __shfl_sync(kFull, roff, bi + i);
       const float left = is_l0 ? blk : shf;
       const int Aleft = is_l0 ? (s0 - 1 - blko) : shA;
+      store_bp_words_if<K>(bpw - NW, padv, pskp, write_bp && pend);
 
       uint32_t adv[K];
       uint32_t skp[K / 2];
@@ -553,19 +589,25 @@ __global__ void __launch_bounds__(512)
           a[j] = m + el[j >> 1];
         }
       }
-      store_bp_words_if<K>(bpw, adv, skp, write_bp);
+#pragma unroll
+      for (int j = 0; j < K; ++j) padv[j] = adv[j];
+#pragma unroll
+      for (int j = 0; j < K / 2; ++j) pskp[j] = skp[j];
+      pend = true;
       bpw += NW;
       send_one(t, a[K - 1], A[K - 1]);
     }
-    if (t - 1 == next_ck) {
-      store_ckpt(next_ck);
-      next_ck += ck_every;
-    }
-    if (t - 1 == next_anchor) {
-      store_anchor_row((next_anchor - t_begin) / kAnchorD - 1);
+    store_bp_words_if<K>(bpw - NW, padv, pskp, write_bp && pend);
+    bi += n;
+    const int done = t - 1 - t_begin;  // frames computed after this sub-run
+    if ((done & (kAnchorD - 1)) == 0) {  // window end: frame t-1 is an anchor frame
+      if (t - 1 == next_ck) {
+        store_ckpt(next_ck);
+        next_ck += ck_every;
+      }
+      store_anchor_row(done / kAnchorD - 1);
 #pragma unroll
       for (int j = 0; j < K; ++j) A[j] = s0 + j;
-      next_anchor += kAnchorD;
     }
   }
   // Last, partial window.
@@ -587,8 +629,8 @@ __global__ void __launch_bounds__(512)
   // Each stage has at most one chunk in flight; waiting for the latest chunk
   // issued on every stage covers all of them (a completed phase returns at once).
   if (warp == 0 && lane == 0) {
-    for (int c = max(0, issued - kStages); c < issued; ++c)
-      (void)wait_phase(&head->full[c % kStages], (c / kStages) & 1, abort, limit, false);
+    for (int c = max(0, issued - P.stages); c < issued; ++c)
+      (void)wait_phase(&head->full[c % P.stages], (c / P.stages) & 1, abort, limit, false);
   }
   __threadfence();
   __syncthreads();
@@ -759,11 +801,20 @@ cudaError_t launch_k(const LaunchShape& shape, const FwdParams& p, const FwdJob*
 FwdParams plan_params(const LaunchShape& shape, int C, int frames_per_stage, uint64_t wait_limit_ns) {
   FwdParams p{};
   const int F = frames_per_stage < 1 ? 1 : frames_per_stage;
-  // Block of frames per ring wait: the warps of a CTA lag each other by about
-  // one block per hop, and the emission ring tolerates (kStages - kLead) * F
-  // frames of lag between its first and last warp.
-  const int lag_room = (kStages - kLead) * F;
-  p.block = std::max(1, std::min(32, lag_room / std::max(1, shape.warps - 1)));
+  // Block of frames per ring wait: the warps of a CTA lag each other by up to
+  // one block per hop, and the emission ring tolerates (stages - kLead) * F
+  // frames of lag between its first and last warp before the producer (warp 0)
+  // waits for a stage to be released. Stages beyond that only cost shared
+  // memory, i.e. resident CTAs per SM, so the ring is sized to the lag: kLead
+  // stages for a one-warp CTA (warp 0 releases a stage itself just before it
+  // refills it), up to kMaxStages for wide CTAs.
+  // The block is a power of two dividing kAnchorD (as F is).
+  const int lag_room = (kMaxStages - kLead) * F;
+  const int hops = std::max(0, shape.warps - 1);
+  const int room = std::max(1, std::min(kAnchorD, lag_room / std::max(1, hops)));
+  p.block = 1;
+  while (p.block * 2 <= room) p.block *= 2;
+  p.stages = kLead + (hops * p.block + F - 1) / F;
   int rb = 8;
   while (rb < 2 * p.block + 2) rb <<= 1;
   p.rb = rb;
@@ -771,7 +822,9 @@ FwdParams plan_params(const LaunchShape& shape, int C, int frames_per_stage, uin
   p.stage_bytes = ((F * C * 4) + 15) & ~15;
   p.off_ring = static_cast<int>(sizeof(SmemHead)) + 32 * 4;
   p.off_stage = (p.off_ring + shape.warps * rb * 8 + 127) & ~127;
-  p.off_bt = (p.off_stage + kStages * p.stage_bytes + 127) & ~127;  // end of the forward region
+  // One spare row after the last stage: the emission look-ahead of a chunk's
+  // last frame reads (and discards) the row after it.
+  p.off_bt = (p.off_stage + p.stages * p.stage_bytes + C * 4 + 127) & ~127;  // end of the forward region
   p.wait_limit_ns = wait_limit_ns;
   return p;
 }

@@ -76,7 +76,8 @@ def test_plan_shapes_and_footprints():
     # Small budget: checkpointed, footprint ~ sqrt(T) rows.
     q = align.align_plan(180000, 32, 45000, budget=1 << 30)
     assert q["checkpointed"] == 1
-    assert q["checkpoint_every"] == int(np.ceil(np.sqrt(180000)))
+    # about sqrt(T) frames per segment, rounded up to whole 32-frame anchor windows
+    assert q["checkpoint_every"] == -(-int(np.ceil(np.sqrt(180000))) // 32) * 32
     assert q["checkpoints"] == (180000 - 1) // q["checkpoint_every"] + 1
     assert q["checkpoint_bytes"] < (1 << 30) < q["backpointer_bytes"]
     # Forced checkpointing.
@@ -90,6 +91,9 @@ def test_plan_shapes_and_footprints():
     assert align.align_plan(3000, 32, 750)["frames_per_stage"] == 32     # 12 warps
     assert align.align_plan(3000, 500, 750)["frames_per_stage"] == 4     # 8 KB cap
     assert align.align_plan(100, 500, 10)["frames_per_stage"] == 2       # 4 KB stages of 2 KB rows
+    # Rows per stage are a power of two dividing the 32-frame anchor window.
+    assert align.align_plan(3000, 96, 750)["frames_per_stage"] == 16     # 8 KB / 384 B = 21 -> 16
+    assert align.align_plan(100, 96, 10)["frames_per_stage"] == 8        # 4 KB / 384 B = 10 -> 8
 
 
 @pytest.mark.parametrize("K", [2, 4, 8, 16])

@@ -116,6 +116,23 @@ def test_validation_errors(al):
         assert e.value.code == code
 
 
+@pytest.mark.parametrize("K,cw", [(2, 1), (2, 2), (2, 8), (2, 16), (4, 1), (4, 16), (8, 4), (16, 2)])
+def test_launch_shapes_bit_identical(K, cw):
+    """Every (states per lane, warps per CTA) shape, including one-warp CTAs in
+    clusters and 8- / 16-warp CTAs (receive blocks of 16 / 8 frames), gives the
+    oracle's alignment; wide rows (C = 500) stage 4 frames per chunk."""
+    build.build()
+    a = align.Aligner(device=0, bp_budget_bytes=8 << 30)
+    try:
+        a.set_tuning(K, cw, 16)
+        for (T, C, L, seed) in [(700, 32, 300, 11), (333, 500, 120, 12), (95, 29, 40, 13), (33, 32, 5, 14),
+                                (1200, 32, 500, 15), (700, 500, 300, 16)]:
+            u = synth.make_utterance(seed * 1000 + K * 10 + cw, T, C, L, repeat_frac=0.1)
+            run(a, u.lp.numpy(), u.targets, 0, f"K{K}cw{cw}T{T}C{C}")
+    finally:
+        a.close()
+
+
 def test_checkpointed_equals_full():
     build.build()
     ck = align.Aligner(device=0, force_checkpoint=True)
