@@ -286,21 +286,31 @@ def main():
     flush_buf = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
     items = [(utts[i], batch.targets[i], 0, outs[i]) for i in range(n)]
 
+    # The stream is held by a device-side sleep while the host enqueues the
+    # batch, so the events time device work only. The hold must outlast the
+    # host enqueue (submit + flush of every utterance): it is calibrated on the
+    # warm-up steps to twice the slowest enqueue seen, at least 20 ms.
+    hold = {"cycles": 40_000_000, "enqueue_s": 0.0}
+
     def step_batched():
         flush_buf.fill_(1)
         with torch.cuda.stream(stream):
-            torch.cuda._sleep(40_000_000)  # hold the stream while the host enqueues the batch
+            torch.cuda._sleep(hold["cycles"])
             ev0 = torch.cuda.Event(enable_timing=True)
             ev1 = torch.cuda.Event(enable_timing=True)
             ev0.record(stream)
+            h0 = time.perf_counter()
             rs = al.submit_batch(items)
             al.flush()
             al.join(stream)
             ev1.record(stream)
+            h1 = time.perf_counter()
         for r in rs:
             al.poll(r)
             assert r.status == 0, r.status
         ev1.synchronize()
+        hold["enqueue_s"] = max(hold["enqueue_s"], h1 - h0)
+        hold["cycles"] = max(40_000_000, int(2 * hold["enqueue_s"] * 2.0e9))
         return ev0.elapsed_time(ev1)
 
     if args.profile:
@@ -321,11 +331,13 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     l0 = al.stats()["kernel_launches"]
+    tp0 = al.stats()["throughput_batches"]
     times = []
     with Clocks(dev) as clk:
         for _ in range(args.steps):
             times.append(step_batched())
     launches = (al.stats()["kernel_launches"] - l0) // max(args.steps, 1)
+    tp_batches = (al.stats()["throughput_batches"] - tp0) / max(args.steps, 1)
     torch.cuda.synchronize()
     ms = statistics.mean(times)
     if dist:
@@ -451,7 +463,10 @@ def main():
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": wl["name"], "utterances": n, "cells_per_step": cells, "T_max": T_max,
                    "l2": "flushed (256 MiB write) before every timed step", "parallelism": f"replicas{world}",
-                   "tuning": autotune.load() if tuned else "built-in default (K=4, 4 warps per CTA)"},
+                   "tuning": ({"latency": autotune.load(mode="latency"), "throughput": autotune.load(mode="throughput"),
+                              "throughput_batches_per_step": tp_batches}
+                             if tuned else "built-in default (K=4, 4 warps per CTA)"),
+                   "host_enqueue_ms": round(hold["enqueue_s"] * 1e3, 3)},
         "p50_ms": float(np.percentile(times, 50)), "p99_ms": float(np.percentile(times, 99)),
         "plain": plain,
         "e2e": e2e,

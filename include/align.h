@@ -171,6 +171,7 @@ typedef struct {
     uint64_t cells;             /* sum of T * S over finished requests */
     uint64_t checkpointed;      /* requests that ran with checkpointed recompute */
     uint64_t bp_bytes_peak;     /* peak arena use */
+    uint64_t throughput_batches; /* batches planned with the throughput tuning table */
 } align_stats;
 
 int align_get_stats(align_ctx *ctx, align_stats *out, int32_t reset);
@@ -202,6 +203,20 @@ int align_probe_frame_latency(int32_t device, int32_t warps, int32_t ctas, int32
    s_max <= 0 clears the table. Up to 16 ranges (ALIGN_E_AGAIN beyond). The
    autotuner of the Python package fills this table from timed trials. */
 int align_set_tuning_bucket(align_ctx *ctx, int32_t s_max, int32_t states_per_lane, int32_t cta_warps);
+
+/* Tuning tables: ALIGN_TUNE_LATENCY holds the shapes that finish one
+   utterance soonest (short chains of few-state lanes); ALIGN_TUNE_THROUGHPUT
+   the shapes that finish many utterances soonest when the GPU is
+   oversubscribed (more states per lane and warps per CTA). When a throughput
+   table is set, each batch is planned with it if its work exceeds what the GPU
+   runs concurrently: sum over requests of T * ceil(S / 64) above
+   T_max * 8 * (number of SMs); otherwise with the latency table. Same
+   arguments as align_set_tuning_bucket (which sets the latency table);
+   s_max <= 0 clears the given table. ALIGN_E_INVAL for an unknown table. */
+#define ALIGN_TUNE_LATENCY 0
+#define ALIGN_TUNE_THROUGHPUT 1
+int align_set_tuning_bucket_for(align_ctx *ctx, int32_t table, int32_t s_max, int32_t states_per_lane,
+                                int32_t cta_warps);
 
 /* ---- allocation-free entry point ---------------------------------------- */
 

@@ -40,7 +40,7 @@ ALIGN_F_TEST_STALL = 0x80000000
 # Every entry point declared in include/align.h.
 EXPORTS = ("align_create", "align_destroy", "align_submit", "align_submit_host", "align_submit_batch", "align_flush",
            "align_poll", "align_poll_done", "align_join", "align_get_stats", "align_status_string", "align_last_error",
-           "align_set_tuning", "align_set_tuning_bucket", "align_validate", "align_plan", "align_probe_frame_latency",
+           "align_set_tuning", "align_set_tuning_bucket", "align_set_tuning_bucket_for", "align_validate", "align_plan", "align_probe_frame_latency",
            "align_forced_noalloc", "align_noalloc_last_error")
 
 
@@ -68,7 +68,8 @@ class AlignRequest(ctypes.Structure):
 class AlignStats(ctypes.Structure):
     _fields_ = [("kernel_launches", ctypes.c_uint64), ("graph_launches", ctypes.c_uint64),
                 ("requests_done", ctypes.c_uint64), ("cells", ctypes.c_uint64),
-                ("checkpointed", ctypes.c_uint64), ("bp_bytes_peak", ctypes.c_uint64)]
+                ("checkpointed", ctypes.c_uint64), ("bp_bytes_peak", ctypes.c_uint64),
+                ("throughput_batches", ctypes.c_uint64)]
 
 
 class AlignPlanInfo(ctypes.Structure):
@@ -116,6 +117,7 @@ def lib() -> ctypes.CDLL:
         L.align_last_error.restype = ctypes.c_char_p
         L.align_set_tuning.argtypes = [vp, i32, i32, i32]
         L.align_set_tuning_bucket.argtypes = [vp, i32, i32, i32]
+        L.align_set_tuning_bucket_for.argtypes = [vp, i32, i32, i32, i32]
         L.align_probe_frame_latency.argtypes = [i32, i32, i32, i32, ctypes.POINTER(ctypes.c_double)]
         L.align_forced_noalloc.argtypes = [vp, i64, i64, vp, i64, i32, AlignOut, vp, ctypes.POINTER(i32)]
         L.align_noalloc_last_error.argtypes = []
@@ -248,6 +250,15 @@ def align_noalloc_last_error() -> str:
 
 def align_set_tuning_bucket(ctx, s_max: int, states_per_lane: int = 0, cta_warps: int = 0) -> None:
     _check(lib().align_set_tuning_bucket(ctx, s_max, states_per_lane, cta_warps), "align_set_tuning_bucket")
+
+
+ALIGN_TUNE_LATENCY = 0
+ALIGN_TUNE_THROUGHPUT = 1
+
+
+def align_set_tuning_bucket_for(ctx, table: int, s_max: int, states_per_lane: int = 0, cta_warps: int = 0) -> None:
+    _check(lib().align_set_tuning_bucket_for(ctx, table, s_max, states_per_lane, cta_warps),
+           "align_set_tuning_bucket_for")
 
 
 def align_validate(targets, C: int, blank: int, T: int) -> tuple[int, int]:
@@ -411,8 +422,10 @@ class Aligner:
     def set_tuning(self, states_per_lane: int = 0, cta_warps: int = 0, max_cluster: int = 0) -> None:
         align_set_tuning(self.ctx, states_per_lane, cta_warps, max_cluster)
 
-    def set_tuning_table(self, table) -> None:
-        """table: iterable of (s_max, states_per_lane, cta_warps); replaces the current table."""
-        align_set_tuning_bucket(self.ctx, 0)
+    def set_tuning_table(self, table, mode: str = "latency") -> None:
+        """table: iterable of (s_max, states_per_lane, cta_warps); replaces the
+        latency (default) or throughput table."""
+        which = {"latency": ALIGN_TUNE_LATENCY, "throughput": ALIGN_TUNE_THROUGHPUT}[mode]
+        align_set_tuning_bucket_for(self.ctx, which, 0)
         for s_max, k, cw in table:
-            align_set_tuning_bucket(self.ctx, int(s_max), int(k), int(cw))
+            align_set_tuning_bucket_for(self.ctx, which, int(s_max), int(k), int(cw))

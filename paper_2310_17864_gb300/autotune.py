@@ -9,10 +9,12 @@ the fastest. Two criteria:
   * ``latency``: one utterance alone (the per-frame chain of a single team);
   * ``throughput``: a batch of utterances of that size filling the GPU.
 
-The table is installed with ``align_set_tuning_bucket`` and can be saved as
-JSON (keyed by GPU name) and loaded by later runs. Usage:
+The two tables are installed with ``align_set_tuning_bucket_for`` (the
+library plans a batch with the throughput table when it oversubscribes the
+GPU, else with the latency table) and saved as JSON with the GPU name, one
+key per mode, for later runs. Usage:
 
-    python -m paper_2310_17864_gb300.autotune --mode latency --out tuning.json
+    python -m paper_2310_17864_gb300.autotune --mode both --out tuning.json
 """
 from __future__ import annotations
 
@@ -96,39 +98,52 @@ def tune(device: int = 0, mode: str = "latency", buckets=BUCKETS, C: int = 32, r
 
 
 def save(result: dict, path: str, device: int = 0) -> None:
+    """Store the table of ``result["mode"]`` (and its trials) in ``path``,
+    keeping the other mode's table if the file has one."""
     import torch
-    data = dict(result)
+    data = {}
+    if os.path.exists(path):
+        with open(path) as f:
+            data = json.load(f)
     data["gpu"] = torch.cuda.get_device_name(device)
+    data[result["mode"]] = result["table"]
+    data.setdefault("trials", {})[result["mode"]] = result["trials"]
     with open(path, "w") as f:
         json.dump(data, f, indent=1)
 
 
-def load(path: str = DEFAULT_TABLE) -> list | None:
-    """The table saved by ``save``, or None when absent."""
+def load(path: str = DEFAULT_TABLE, mode: str = "latency") -> list | None:
+    """The table of ``mode`` saved by ``save``, or None when absent."""
     if not os.path.exists(path):
         return None
     with open(path) as f:
-        return [tuple(x) for x in json.load(f)["table"]]
+        data = json.load(f)
+    table = data.get(mode)
+    return [tuple(x) for x in table] if table else None
 
 
 def apply(aligner: align.Aligner, path: str = DEFAULT_TABLE) -> bool:
-    table = load(path)
-    if not table:
-        return False
-    aligner.set_tuning_table(table)
-    return True
+    """Install every table found in ``path``; True if there was one."""
+    found = False
+    for mode in ("latency", "throughput"):
+        table = load(path, mode)
+        if table:
+            aligner.set_tuning_table(table, mode)
+            found = True
+    return found
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--device", type=int, default=0)
-    ap.add_argument("--mode", choices=["latency", "throughput"], default="latency")
+    ap.add_argument("--mode", choices=["latency", "throughput", "both"], default="both")
     ap.add_argument("--out", default=DEFAULT_TABLE)
     ap.add_argument("--reps", type=int, default=3)
     args = ap.parse_args()
-    res = tune(args.device, args.mode, reps=args.reps, verbose=True)
-    save(res, args.out, args.device)
-    print(json.dumps(res["table"]))
+    for mode in (("latency", "throughput") if args.mode == "both" else (args.mode,)):
+        res = tune(args.device, mode, reps=args.reps, verbose=True)
+        save(res, args.out, args.device)
+        print(mode, json.dumps(res["table"]))
 
 
 if __name__ == "__main__":

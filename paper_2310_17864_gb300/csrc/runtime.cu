@@ -137,6 +137,7 @@ struct Request {
   int32_t blank = 0;
   std::vector<int32_t> targets;
   Plan plan{};
+  int plan_table = ALIGN_TUNE_LATENCY;  // tuning table the plan was made with
   Alloc bp;                   // backpointers or checkpoints + segment buffer
   Alloc stage;                // host-I/O device staging
   int batch = -1;
@@ -198,7 +199,8 @@ struct align_ctx {
   uint64_t next_id = 1;
   int next_batch = 1;
 
-  TuneTable tune;
+  TuneTable tune;     // latency shapes (also the defaults)
+  TuneTable tune_tp;  // throughput shapes (nbuckets == 0: not set)
   int num_sms = 0;
   int smem_optin = 0;
   align_stats stats{};
@@ -264,8 +266,38 @@ uint64_t request_bp_bytes(const Plan& p) { return p.checkpointed ? p.ckpt_bytes 
 
 // Launch as many queued requests as fit, as one batch. Returns ALIGN_OK even
 // if nothing could be launched (they stay queued).
+// Plans the queued requests with the throughput table when their work
+// exceeds what the GPU runs at once (T * ceil(S/64) warp-frames, summed, above
+// T_max * 8 warps * SMs), else with the latency table. Plans are only
+// remade for requests whose table changes; a request keeps its plan if the
+// other table cannot place it.
+bool choose_tables(align_ctx* ctx) {
+  if (ctx->tune_tp.nbuckets == 0) return false;
+  uint64_t work = 0;
+  int64_t tmax = 0;
+  for (uint64_t id : ctx->queued) {
+    const Request& r = ctx->reqs.at(id);
+    work += static_cast<uint64_t>(r.T) * static_cast<uint64_t>((2 * r.L + 1 + 63) / 64);
+    tmax = std::max(tmax, r.T);
+  }
+  const bool tp = work > static_cast<uint64_t>(tmax) * 8ull * static_cast<uint64_t>(std::max(1, ctx->num_sms));
+  const int want = tp ? ALIGN_TUNE_THROUGHPUT : ALIGN_TUNE_LATENCY;
+  for (uint64_t id : ctx->queued) {
+    Request& r = ctx->reqs.at(id);
+    if (r.plan_table == want) continue;
+    Plan p{};
+    if (make_plan(tp ? ctx->tune_tp : ctx->tune, r.T, r.C, r.L, ctx->bp_arena.cap(),
+                  (ctx->flags & ALIGN_F_FORCE_CHECKPOINT) != 0, &p) == ALIGN_OK) {
+      r.plan = p;
+      r.plan_table = want;
+    }
+  }
+  return tp;
+}
+
 int launch_queued(align_ctx* ctx) {
   if (ctx->queued.empty()) return ALIGN_OK;
+  const bool tp_batch = choose_tables(ctx);
   std::vector<Request*> take;
   std::deque<uint64_t> keep;
   uint64_t meta_est = 0;  // descriptor + metadata + targets bytes of the batch
@@ -407,6 +439,7 @@ int launch_queued(align_ctx* ctx) {
     }
   }
 
+  if (tp_batch) ctx->stats.throughput_batches++;
   Batch b;
   b.id = ctx->next_batch++;
   auto unwind = [&]() {
@@ -1008,15 +1041,20 @@ const char* align_status_string(int32_t code) {
 const char* align_last_error(void) { return g_last_error; }
 
 int align_set_tuning_bucket(align_ctx* ctx, int32_t s_max, int32_t states_per_lane, int32_t cta_warps) {
-  if (!ctx) return ALIGN_E_INVAL;
+  return align_set_tuning_bucket_for(ctx, ALIGN_TUNE_LATENCY, s_max, states_per_lane, cta_warps);
+}
+
+int align_set_tuning_bucket_for(align_ctx* ctx, int32_t table, int32_t s_max, int32_t states_per_lane,
+                                int32_t cta_warps) {
+  if (!ctx || (table != ALIGN_TUNE_LATENCY && table != ALIGN_TUNE_THROUGHPUT)) return ALIGN_E_INVAL;
+  TuneTable& t = (table == ALIGN_TUNE_LATENCY) ? ctx->tune : ctx->tune_tp;
   if (s_max <= 0) {  // clear the table
-    ctx->tune.nbuckets = 0;
+    t.nbuckets = 0;
     return ALIGN_OK;
   }
   if ((states_per_lane != 2 && states_per_lane != 4 && states_per_lane != 8 && states_per_lane != 16) ||
       cta_warps < 1 || cta_warps > 16)
     return ALIGN_E_INVAL;
-  TuneTable& t = ctx->tune;
   for (int i = 0; i < t.nbuckets; ++i) {
     if (t.buckets[i].s_max == s_max) {
       t.buckets[i] = TuneBucket{s_max, states_per_lane, cta_warps};
@@ -1035,9 +1073,11 @@ int align_set_tuning(align_ctx* ctx, int32_t states_per_lane, int32_t cta_warps,
       states_per_lane != 16)
     return ALIGN_E_INVAL;
   if (cta_warps < 0 || cta_warps > 32 || max_cluster < 0 || max_cluster > 16) return ALIGN_E_INVAL;
-  if (states_per_lane) ctx->tune.K = states_per_lane;
-  if (cta_warps) ctx->tune.cta_warps = cta_warps;
-  if (max_cluster) ctx->tune.max_cluster = max_cluster;
+  for (TuneTable* t : {&ctx->tune, &ctx->tune_tp}) {  // the defaults of both tables
+    if (states_per_lane) t->K = states_per_lane;
+    if (cta_warps) t->cta_warps = cta_warps;
+    if (max_cluster) t->max_cluster = max_cluster;
+  }
   return ALIGN_OK;
 }
 
