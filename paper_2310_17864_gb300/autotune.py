@@ -76,6 +76,10 @@ def tune(device: int = 0, mode: str = "latency", buckets=BUCKETS, C: int = 32, r
                 al = align.Aligner(device=device, batched=True, bp_budget_bytes=8 << 30, graphs=False, stream=st)
                 try:
                     al.set_tuning(K, cw, 0)
+                    if mode == "throughput":
+                        # Batches that oversubscribe the GPU run the throughput build of
+                        # the kernel; let the library choose as it does in service.
+                        al.set_tuning_table([(1 << 30, K, cw)], "throughput")
                     outs = [(torch.empty(s.T, dtype=torch.int32, device=f"cuda:{device}"),
                              torch.empty(s.T, device=f"cuda:{device}"),
                              torch.empty(1, device=f"cuda:{device}"), None) for s in specs]

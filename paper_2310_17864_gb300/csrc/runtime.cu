@@ -288,6 +288,7 @@ bool choose_tables(align_ctx* ctx) {
     Plan p{};
     if (make_plan(tp ? ctx->tune_tp : ctx->tune, r.T, r.C, r.L, ctx->bp_arena.cap(),
                   (ctx->flags & ALIGN_F_FORCE_CHECKPOINT) != 0, &p) == ALIGN_OK) {
+      p.shape.occ = tp ? 1 : 0;
       r.plan = p;
       r.plan_table = want;
     }
@@ -357,14 +358,14 @@ int launch_queued(align_ctx* ctx) {
   // get 1 + nck descriptors each.
   // (K, warps, ncta, F, C) -> request indices. C is part of the key: the launch
   // parameters (emission stage size) depend on it.
-  std::map<std::tuple<int, int, int, int, int>, std::vector<int>> groups;
+  std::map<std::tuple<int, int, int, int, int, int>, std::vector<int>> groups;
   size_t njobs = 0;
   for (size_t i = 0; i < take.size(); ++i) {
     const Plan& p = take[i]->plan;
     if (p.checkpointed) {
       njobs += 1 + static_cast<size_t>(p.nck);
     } else {
-      groups[{p.shape.K, p.shape.warps, p.shape.ncta, p.frames_per_stage, static_cast<int>(take[i]->C)}].push_back(
+      groups[{p.shape.K, p.shape.warps, p.shape.ncta, p.frames_per_stage, static_cast<int>(take[i]->C), p.shape.occ}].push_back(
           static_cast<int>(i));
       njobs += 1;
     }
@@ -392,12 +393,13 @@ int launch_queued(align_ctx* ctx) {
     std::vector<int64_t> key{static_cast<int64_t>(take.size()), static_cast<int64_t>(up_bucket)};
     for (auto& kv : groups) {
       key.insert(key.end(), {std::get<0>(kv.first), std::get<1>(kv.first), std::get<2>(kv.first),
-                             std::get<3>(kv.first), std::get<4>(kv.first), static_cast<int64_t>(kv.second.size())});
+                             std::get<3>(kv.first), std::get<4>(kv.first), std::get<5>(kv.first),
+                             static_cast<int64_t>(kv.second.size())});
     }
     for (auto* r : take) {
       if (!r->plan.checkpointed) continue;
       const Plan& p = r->plan;
-      key.insert(key.end(), {-1, p.shape.K, p.shape.warps, p.shape.ncta, p.frames_per_stage, p.nck, r->C});
+      key.insert(key.end(), {-1, p.shape.K, p.shape.warps, p.shape.ncta, p.shape.occ, p.frames_per_stage, p.nck, r->C});
     }
     for (size_t k = 0; k < ctx->graphs.size(); ++k)
       if (ctx->graphs[k].key == key) gi = static_cast<int>(k);
@@ -541,6 +543,7 @@ int launch_queued(align_ctx* ctx) {
     LaunchShape shape;
     int F;
     size_t first, count;
+    int64_t t_max;  // longest job of the group (frames): its chain sets the launch's duration
   };
   std::vector<GroupLaunch> glaunch;
   struct CkLaunch {
@@ -550,12 +553,14 @@ int launch_queued(align_ctx* ctx) {
   size_t jn = 0;
   for (auto& kv : groups) {
     GroupLaunch gl{};
-    gl.shape = LaunchShape{std::get<0>(kv.first), std::get<1>(kv.first), std::get<2>(kv.first)};
+    gl.shape = LaunchShape{std::get<0>(kv.first), std::get<1>(kv.first), std::get<2>(kv.first), std::get<5>(kv.first)};
     gl.F = std::get<3>(kv.first);
     gl.first = jn;
     gl.count = kv.second.size();
+    gl.t_max = 0;
     for (int i : kv.second) {
       const Request& r = *take[static_cast<size_t>(i)];
+      gl.t_max = std::max(gl.t_max, r.T);
       FwdJob j = base_job(static_cast<size_t>(i));
       j.bp = reinterpret_cast<uint32_t*>(ctx->d_bp + r.bp.off);
       j.ztab = reinterpret_cast<uint8_t*>(ctx->d_bp + r.bp.off + r.plan.z_off);
@@ -568,6 +573,10 @@ int launch_queued(align_ctx* ctx) {
     }
     glaunch.push_back(gl);
   }
+  // Launch the groups with the longest chains first: when the batch fills the
+  // GPU, later launches wait for room, and the longest job must not wait.
+  std::stable_sort(glaunch.begin(), glaunch.end(),
+                   [](const GroupLaunch& x, const GroupLaunch& y) { return x.t_max > y.t_max; });
   for (size_t i = 0; i < take.size(); ++i) {
     const Request& r = *take[i];
     const Plan& p = r.plan;
@@ -642,18 +651,7 @@ int launch_queued(align_ctx* ctx) {
   b.events.push_back(ready);
   CU(cudaEventRecord(ready, s0));
   size_t lane_i = 0;
-  for (const GroupLaunch& gl : glaunch) {
-    cudaStream_t s = used[lane_i++ % used.size()];
-    if (s != s0) CU(cudaStreamWaitEvent(s, ready, 0));
-    const int C = hjobs[gl.first].C;
-    const FwdParams P = plan_params(gl.shape, C, gl.F, ctx->wait_limit_ns);
-    cudaError_t e = static_cast<cudaError_t>(launch_trellis(gl.shape, P, djobs + gl.first, static_cast<int>(gl.count), s));
-    if (e != cudaSuccess) {
-      set_error("launch_trellis", e);
-      return ALIGN_E_CUDA;
-    }
-    ++nkernels;
-  }
+  // Checkpointed sequences first (the longest utterances), then the groups.
   for (const CkLaunch& cl : cklaunch) {
     cudaStream_t s = used[lane_i++ % used.size()];
     if (s != s0) CU(cudaStreamWaitEvent(s, ready, 0));
@@ -667,6 +665,18 @@ int launch_queued(align_ctx* ctx) {
       }
       ++nkernels;
     }
+  }
+  for (const GroupLaunch& gl : glaunch) {
+    cudaStream_t s = used[lane_i++ % used.size()];
+    if (s != s0) CU(cudaStreamWaitEvent(s, ready, 0));
+    const int C = hjobs[gl.first].C;
+    const FwdParams P = plan_params(gl.shape, C, gl.F, ctx->wait_limit_ns);
+    cudaError_t e = static_cast<cudaError_t>(launch_trellis(gl.shape, P, djobs + gl.first, static_cast<int>(gl.count), s));
+    if (e != cudaSuccess) {
+      set_error("launch_trellis", e);
+      return ALIGN_E_CUDA;
+    }
+    ++nkernels;
   }
   // Join, download statuses and host outputs, record completion.
   for (cudaStream_t s : used) {

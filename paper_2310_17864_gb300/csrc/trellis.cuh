@@ -102,6 +102,8 @@ struct LaunchShape {
   int K;                   // states per lane
   int warps;               // warps per CTA
   int ncta;                // CTAs per cluster (1: no cluster)
+  int occ = 0;             // 1: build with fewer registers per thread (K <= 4) for more
+                           // resident warps, for batches that oversubscribe the GPU
 };
 
 // Number of 32-bit backpointer words per warp and frame.

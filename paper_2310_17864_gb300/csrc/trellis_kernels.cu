@@ -205,11 +205,11 @@ __device__ __forceinline__ void st_global_v4_if(uint32_t* p, uint32_t x, uint32_
       "r"(x), "r"(y), "r"(z), "r"(w), "r"(static_cast<uint32_t>(pred))
       : "memory");
 }
-__device__ __forceinline__ void st_cluster_u64_if(uint32_t addr, uint64_t v, bool pred) {
+__device__ __forceinline__ void st_cluster_v2_if(uint32_t addr, uint32_t lo, uint32_t hi, bool pred) {
   asm volatile(
-      "{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t@q st.relaxed.cluster.shared::cluster.u64 [%0], %1;\n\t}" ::"r"(
+      "{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %3, 0;\n\t@q st.relaxed.cluster.shared::cluster.v2.u32 [%0], {%1, %2};\n\t}" ::"r"(
           addr),
-      "l"(v), "r"(static_cast<uint32_t>(pred))
+      "r"(lo), "r"(hi), "r"(static_cast<uint32_t>(pred))
       : "memory");
 }
 // All backpointer words of one warp and frame, stored by lane 0 under a single
@@ -251,9 +251,25 @@ __device__ __forceinline__ void store_bp_words_if(uint32_t* dst, const uint32_t 
   }
 }
 
+// One backpointer row (NW = 3 or 6 words) stored by the lane that buffered it.
+template <int K, int NWB>
+__device__ __forceinline__ void store_bp_row(uint32_t* dst, const uint32_t (&w)[NWB]) {
+  if constexpr (NWB == 3) {  // 12-byte rows: 4-byte aligned
+    dst[0] = w[0];
+    dst[1] = w[1];
+    dst[2] = w[2];
+  } else if constexpr (NWB == 6) {  // 24-byte rows: 8-byte aligned
+    *reinterpret_cast<uint2*>(dst) = make_uint2(w[0], w[1]);
+    *reinterpret_cast<uint2*>(dst + 2) = make_uint2(w[2], w[3]);
+    *reinterpret_cast<uint2*>(dst + 4) = make_uint2(w[4], w[5]);
+  }
+}
+
 // ------------------------------------------------------------------ kernel --
-template <int K>
-__global__ void __launch_bounds__(512)
+// kOcc: the register budget of K <= 4 is capped at 64 per thread (two
+// 512-thread CTAs per SM), trading per-warp latency for resident warps.
+template <int K, bool kOcc>
+__global__ void __launch_bounds__(512, (kOcc && K <= 4) ? 2 : 1)
     trellis_kernel(const FwdJob* __restrict__ jobs, const FwdParams P) {
   static_assert(K % 2 == 0 && K >= 2 && K <= 16, "K must be even, 2..16");
   constexpr int NW = bp_words(K);
@@ -315,7 +331,12 @@ __global__ void __launch_bounds__(512)
 
   // ---- per-lane constants: label columns and skip caps of the label states ----
   int col[K / 2];
-  float cap[K / 2];
+  // Skip into label state i of this lane allowed: as a predicate (K <= 4), or
+  // as masks that turn alpha(s-2) into -inf when it is not (K >= 8, where
+  // predicate registers run out). Either way a forbidden skip never wins and
+  // an allowed one compares alpha(s-2) itself, as in the definition.
+  bool skok[K / 2];
+  uint32_t skeep[K / 2], sfill[K / 2];
 #pragma unroll
   for (int i = 0; i < K / 2; ++i) {
     const int s = s0 + 2 * i + 1;
@@ -326,7 +347,9 @@ __global__ void __launch_bounds__(512)
       skip = (s >= 3) && (lab != J.tgt[(s - 3) >> 1]);
     }
     col[i] = lab;
-    cap[i] = skip ? INFINITY : -INFINITY;  // min(alpha(s-2), cap) masks a forbidden skip to -inf
+    skok[i] = skip;
+    skeep[i] = skip ? 0xffffffffu : 0u;
+    sfill[i] = skip ? 0u : 0xff800000u;  // -inf
   }
 
   // ---- emission staging (warp 0 of each CTA is the producer) ----
@@ -426,10 +449,9 @@ __global__ void __launch_bounds__(512)
       if (s0 + j < S) dst[s0 + j] = a[j];
   };
   auto send_one = [&](int t, float v, int anc) {
-    const uint64_t word = (static_cast<uint64_t>((static_cast<uint32_t>(t) + 1u) & kTagMask) << 40) |
-                          (static_cast<uint64_t>(static_cast<uint32_t>(s_last - anc) & 0xffu) << 32) |
-                          __float_as_uint(v);
-    st_cluster_u64_if(send_base + (static_cast<uint32_t>(t) & send_mask) * 8u, word, is_l31);
+    // High word: tag (t+1 mod 2^24) << 8 | anchor offset; low word: alpha bits.
+    const uint32_t hi = ((static_cast<uint32_t>(t) + 1u) << 8) + (static_cast<uint32_t>(s_last - anc) & 0xffu);
+    st_cluster_v2_if(send_base + (static_cast<uint32_t>(t) & send_mask) * 8u, __float_as_uint(v), hi, is_l31);
   };
   // Anchor row of window m: s - anchor(s) of this lane's states, one store.
   uint8_t* const ztab = J.ztab;
@@ -473,6 +495,10 @@ __global__ void __launch_bounds__(512)
   const bool write_bp = (bp != nullptr) && is_l0;
   const float* stage_f = reinterpret_cast<const float*>(stages);
   const int stage_floats = P.stage_bytes / 4;
+  constexpr bool kBufBp = NW <= 6;  // K = 2, 4: a window's backpointer rows buffered in registers
+  uint32_t wb[kBufBp ? NW : 1];
+#pragma unroll
+  for (int j = 0; j < (kBufBp ? NW : 1); ++j) wb[j] = 0u;
   int c_stage = 0;        // stage of the current chunk
   uint32_t c_round = 0;   // its round
   int ridx = 0;           // row of frame t in the stage ring (floats)
@@ -533,9 +559,10 @@ __global__ void __launch_bounds__(512)
     float el_n[K / 2];
 #pragma unroll
     for (int q = 0; q < K / 2; ++q) el_n[q] = stage_f[ridx + col[q]];
-    // Backpointer words of the previous frame: stored one frame late, after
-    // this frame's loads and shuffles are issued, so the ballot latency is
-    // not on the per-frame path.
+    // Backpointer words. NW <= 6: lane i keeps the words of the window's
+    // frame i in registers and the warp stores a whole window at once (one
+    // row per lane). Wider rows: lane 0 stores the words of the previous
+    // frame one frame late, after this frame's loads and shuffles are issued.
     uint32_t padv[K];
     uint32_t pskp[K / 2];
 #pragma unroll
@@ -543,7 +570,8 @@ __global__ void __launch_bounds__(512)
 #pragma unroll
     for (int j = 0; j < K / 2; ++j) pskp[j] = 0u;
     bool pend = false;
-#pragma unroll(K == 2 ? 2 : 1)
+    const int fi0 = ft & (kAnchorD - 1);  // frame index of t within its window
+#pragma unroll(K == 2 ? 4 : 1)
     for (int i = 0; i < n; ++i, ++t) {
       const float eb = eb_n;
       float el[K / 2];
@@ -561,7 +589,7 @@ __global__ void __launch_bounds__(512)
       const int blko = __shfl_sync(kFull, roff, bi + i);
       const float left = is_l0 ? blk : shf;
       const int Aleft = is_l0 ? (s0 - 1 - blko) : shA;
-      store_bp_words_if<K>(bpw - NW, padv, pskp, write_bp && pend);
+      if constexpr (!kBufBp) store_bp_words_if<K>(bpw - NW, padv, pskp, write_bp && pend);
 
       uint32_t adv[K];
       uint32_t skp[K / 2];
@@ -576,12 +604,14 @@ __global__ void __launch_bounds__(512)
           adv[j] = __ballot_sync(kFull, b1);
           a[j] = m + eb;
         } else {  // label state: stay, advance, or skip when allowed
-          const float p2 = fminf((j == 1) ? left : a[j - 2], cap[j >> 1]);
+          const float p2raw = (j == 1) ? left : a[j - 2];
+          const float p2 = (K <= 4) ? p2raw
+                                    : __uint_as_float((__float_as_uint(p2raw) & skeep[j >> 1]) | sfill[j >> 1]);
           const int q2 = (j == 1) ? Aleft : A[j - 2];
           const bool b1 = p1 > a[j];
           float m = b1 ? p1 : a[j];
           int an = b1 ? q1 : A[j];
-          const bool b2 = p2 > m;
+          const bool b2 = ((K <= 4) ? skok[j >> 1] : true) && (p2 > m);
           m = b2 ? p2 : m;
           A[j] = b2 ? q2 : an;
           adv[j] = __ballot_sync(kFull, b1);
@@ -589,17 +619,32 @@ __global__ void __launch_bounds__(512)
           a[j] = m + el[j >> 1];
         }
       }
+      if constexpr (kBufBp) {
+        const bool mine = (lane == fi0 + i);
 #pragma unroll
-      for (int j = 0; j < K; ++j) padv[j] = adv[j];
+        for (int j = 0; j < K; ++j) wb[j] = mine ? adv[j] : wb[j];
 #pragma unroll
-      for (int j = 0; j < K / 2; ++j) pskp[j] = skp[j];
-      pend = true;
-      bpw += NW;
+        for (int j = 0; j < K / 2; ++j) wb[K + j] = mine ? skp[j] : wb[K + j];
+      } else {
+#pragma unroll
+        for (int j = 0; j < K; ++j) padv[j] = adv[j];
+#pragma unroll
+        for (int j = 0; j < K / 2; ++j) pskp[j] = skp[j];
+        pend = true;
+        bpw += NW;
+      }
       send_one(t, a[K - 1], A[K - 1]);
     }
-    store_bp_words_if<K>(bpw - NW, padv, pskp, write_bp && pend);
+    if constexpr (!kBufBp) store_bp_words_if<K>(bpw - NW, padv, pskp, write_bp && pend);
     bi += n;
     const int done = t - 1 - t_begin;  // frames computed after this sub-run
+    if constexpr (kBufBp) {
+      if (((done & (kAnchorD - 1)) == 0 || t == t_end) && bp != nullptr) {
+        // Rows row0 .. done-1 of this window: row r holds frame t_begin + 1 + r.
+        const int row0 = (done - 1) & ~(kAnchorD - 1);
+        if (lane < done - row0) store_bp_row<K>(bp + (static_cast<size_t>(g) * bp_rows + row0 + lane) * NW, wb);
+      }
+    }
     if ((done & (kAnchorD - 1)) == 0) {  // window end: frame t-1 is an anchor frame
       if (t - 1 == next_ck) {
         store_ckpt(next_ck);
@@ -768,11 +813,11 @@ __global__ void __launch_bounds__(1024) frame_probe_kernel(int frames, uint64_t 
   }
 }
 
-template <int K>
+template <int K, bool kOcc>
 cudaError_t launch_k(const LaunchShape& shape, const FwdParams& p, const FwdJob* d_jobs, int njobs,
                      cudaStream_t stream) {
   const int smem = smem_bytes(shape, p);
-  auto fn = trellis_kernel<K>;
+  auto fn = trellis_kernel<K, kOcc>;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
@@ -842,10 +887,10 @@ int launch_trellis(const LaunchShape& shape, const FwdParams& p, const FwdJob* d
   if (njobs <= 0) return cudaSuccess;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   switch (shape.K) {
-    case 2: return launch_k<2>(shape, p, d_jobs, njobs, s);
-    case 4: return launch_k<4>(shape, p, d_jobs, njobs, s);
-    case 8: return launch_k<8>(shape, p, d_jobs, njobs, s);
-    case 16: return launch_k<16>(shape, p, d_jobs, njobs, s);
+    case 2: return shape.occ ? launch_k<2, true>(shape, p, d_jobs, njobs, s) : launch_k<2, false>(shape, p, d_jobs, njobs, s);
+    case 4: return shape.occ ? launch_k<4, true>(shape, p, d_jobs, njobs, s) : launch_k<4, false>(shape, p, d_jobs, njobs, s);
+    case 8: return launch_k<8, false>(shape, p, d_jobs, njobs, s);
+    case 16: return launch_k<16, false>(shape, p, d_jobs, njobs, s);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -39,7 +39,8 @@ def _batch_outputs(al, b, n):
     return outs
 
 
-def test_throughput_table_for_oversubscribed_batches():
+@pytest.mark.parametrize("K,cw", [(4, 4), (2, 1)])
+def test_throughput_table_for_oversubscribed_batches(K, cw):
     """A batch whose work exceeds what the GPU runs at once is planned with
     the throughput table, a small one with the latency table; both give the
     oracle's alignment."""
@@ -51,7 +52,7 @@ def test_throughput_table_for_oversubscribed_batches():
     try:
         for a in (both, lat):
             a.set_tuning_table([(1 << 20, 2, 1)], "latency")
-        both.set_tuning_table([(1 << 20, 4, 4)], "throughput")
+        both.set_tuning_table([(1 << 20, K, cw)], "throughput")
         small = _batch_outputs(both, b, 2)
         assert both.stats()["throughput_batches"] == 0
         big = _batch_outputs(both, b, 400)

@@ -133,6 +133,32 @@ def test_launch_shapes_bit_identical(K, cw):
         a.close()
 
 
+@pytest.mark.parametrize("K", [2, 4, 8, 16])
+def test_nan_emissions_follow_the_definition(K):
+    """NaN log-probs: every comparison with NaN is false, as in the oracle's
+    strict '>' tests, so paths and states match it exactly for every lane
+    width (the skip rule never turns a NaN into a winning value)."""
+    build.build()
+    a = align.Aligner(device=0, bp_budget_bytes=8 << 30)
+    try:
+        a.set_tuning(K, 4, 16)
+        u = synth.make_utterance(777 + K, 300, 32, 60, repeat_frac=0.1)
+        lp = u.lp.numpy().copy()
+        rng = np.random.default_rng(5 + K)
+        lp[rng.random(lp.shape) < 0.01] = np.nan
+        res = a.align(torch.as_tensor(lp).cuda(), u.targets, 0, want_states=True)
+        o = oracle.viterbi_f32(lp, np.asarray(u.targets, np.int32), 0)
+        assert res.status == o["status"]
+        if o["status"] != 0:  # -inf final score: no path to compare
+            return
+        assert np.array_equal(res.states.cpu().numpy(), o["states"])
+        assert np.array_equal(res.path.cpu().numpy(), o["path"])
+        t = float(res.total.cpu().numpy()[0])
+        assert (np.isnan(t) and np.isnan(o["total"])) or np.float32(t).tobytes() == np.float32(o["total"]).tobytes()
+    finally:
+        a.close()
+
+
 def test_checkpointed_equals_full():
     build.build()
     ck = align.Aligner(device=0, force_checkpoint=True)
