@@ -54,6 +54,9 @@ extern "C" {
                                          queued requests together as one ragged batch */
 #define ALIGN_F_FORCE_CHECKPOINT 0x2u /* always use checkpointed recompute (no full backpointers) */
 #define ALIGN_F_NO_GRAPHS 0x4u        /* batched launches without CUDA-graph capture */
+#define ALIGN_F_NO_GRID_TEAMS 0x8u    /* transcripts beyond one thread-block cluster use larger
+                                         K per lane instead of a grid team (a cooperative launch of
+                                         one 16-warp CTA per SM linked through global memory) */
 #define ALIGN_F_TEST_STALL 0x80000000u /* testing the device watchdog only: in every request whose
                                          trellis spans more than one warp, the first warp never
                                          hands its values on, so the next warp's bounded wait runs
@@ -208,9 +211,11 @@ int align_set_tuning_bucket(align_ctx *ctx, int32_t s_max, int32_t states_per_la
    utterance soonest (short chains of few-state lanes); ALIGN_TUNE_THROUGHPUT
    the shapes that finish many utterances soonest when the GPU is
    oversubscribed (more states per lane and warps per CTA). When a throughput
-   table is set, each batch is planned with it if its work exceeds what the GPU
-   runs concurrently: sum over requests of T * ceil(S / 64) above
-   T_max * 8 * (number of SMs); otherwise with the latency table. Same
+   table is set, each batch of two or more requests is planned with it if its
+   work exceeds what the GPU runs concurrently: sum over requests of
+   T * ceil(S / 64) above T_max * 8 * (number of SMs); otherwise with the
+   latency table. Grid teams (see ALIGN_F_NO_GRID_TEAMS) are planned for
+   latency batches only. Same
    arguments as align_set_tuning_bucket (which sets the latency table);
    s_max <= 0 clears the given table. ALIGN_E_INVAL for an unknown table. */
 #define ALIGN_TUNE_LATENCY 0

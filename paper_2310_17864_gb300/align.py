@@ -35,6 +35,7 @@ ALIGN_E_NOMEM = -10
 ALIGN_F_BATCHED = 0x1
 ALIGN_F_FORCE_CHECKPOINT = 0x2
 ALIGN_F_NO_GRAPHS = 0x4
+ALIGN_F_NO_GRID_TEAMS = 0x8
 ALIGN_F_TEST_STALL = 0x80000000
 
 # Every entry point declared in include/align.h.
@@ -294,12 +295,13 @@ class Aligner:
     def __init__(self, device: int = 0, batched: bool = False, bp_budget_bytes: int = 0,
                  staging_bytes: int = 0, stream=None, force_checkpoint: bool = False,
                  wait_limit_ms: int = 0, max_inflight: int = 0, graphs: bool = True,
-                 test_stall: bool = False):
+                 test_stall: bool = False, grid_teams: bool = True):
         import torch
         self.torch = torch
         self.device = device
         flags = (ALIGN_F_BATCHED if batched else 0) | (ALIGN_F_FORCE_CHECKPOINT if force_checkpoint else 0)
         flags |= 0 if graphs else ALIGN_F_NO_GRAPHS
+        flags |= 0 if grid_teams else ALIGN_F_NO_GRID_TEAMS
         flags |= ALIGN_F_TEST_STALL if test_stall else 0
         cfg = AlignConfig(device=device, max_inflight=max_inflight, bp_budget_bytes=bp_budget_bytes,
                           staging_bytes=staging_bytes,

@@ -18,6 +18,7 @@ struct TuneTable {
   int cta_warps = 4;     // warps per CTA before a team is split over a cluster
   int max_warps = 16;    // hard limit of warps per CTA (the kernel is built for 512 threads)
   int max_cluster = 16;  // CTAs per cluster for long transcripts
+  int max_grid = 0;      // CTAs of a grid team (one per SM) beyond a cluster; 0: no grid teams
   int nbuckets = 0;      // measured choices per range of S, sorted by s_max
   TuneBucket buckets[16];
 };
@@ -38,7 +39,12 @@ struct Plan {
   int zstride = 0;            // bytes per anchor row (S rounded up to 16)
   uint64_t z_off = 0;         // offset of the anchor rows inside the full-mode allocation
   uint64_t seg_z_off = 0;     // offset of the anchor rows inside the segment buffer
+  uint64_t x_bytes = 0;       // grid teams: CTA links, after the backpointers (or the segment buffer)
 };
+// Device bytes of a request: backpointers (or checkpoints + one segment) and
+// the CTA links of a grid team; the links start at plan_x_off.
+inline uint64_t plan_x_off(const Plan& p) { return p.checkpointed ? p.ckpt_bytes + p.seg_bp_bytes : p.bp_bytes; }
+inline uint64_t plan_device_bytes(const Plan& p) { return plan_x_off(p) + p.x_bytes; }
 
 // Step A1: 0, ALIGN_E_INVAL, ALIGN_E_TARGET or ALIGN_E_INFEASIBLE; *repeats = R.
 int validate_request(const int32_t* targets, int64_t L, int64_t C, int32_t blank, int64_t T, int64_t* repeats);

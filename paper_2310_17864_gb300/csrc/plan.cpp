@@ -52,20 +52,36 @@ int make_plan(const TuneTable& tune_in, int64_t T, int64_t C, int64_t L, uint64_
   const int K = tune.K;
   const auto warp_cap = [&](int) { return std::min(16, tune.max_warps); };
   const int portable = std::min(8, tune.max_cluster);
+  // Transcripts beyond a cluster of the tuned K become grid teams (one CTA
+  // per SM, linked through global memory) when the device has the SMs, before
+  // K grows to 8 or 16 states per lane. A grid team spreads over as many SMs
+  // as it can: the fewest warps per CTA (at most 16) that fit on max_grid SMs,
+  // since the warps of one SM share its issue slots.
   struct Try {
-    int k, wcap, cmax;
+    int k, wcap, cmax, grid;
   };
   const int cw = std::max(1, std::min(tune.cta_warps, warp_cap(K)));
-  const Try tries[] = {{K, cw, portable},          {K, cw, tune.max_cluster}, {K, warp_cap(K), portable},
-                       {8, warp_cap(8), portable}, {K, warp_cap(K), tune.max_cluster},
-                       {8, warp_cap(8), tune.max_cluster}, {16, warp_cap(16), tune.max_cluster}};
+  const Try tries[] = {{K, cw, portable, 0},
+                       {K, cw, tune.max_cluster, 0},
+                       {K, warp_cap(K), tune.max_grid, 1},
+                       {K, warp_cap(K), portable, 0},
+                       {K, warp_cap(K), tune.max_cluster, 0},
+                       {8, warp_cap(8), portable, 0},
+                       {8, warp_cap(8), tune.max_cluster, 0},
+                       {8, warp_cap(8), tune.max_grid, 1},
+                       {16, warp_cap(16), tune.max_cluster, 0},
+                       {16, warp_cap(16), tune.max_grid, 1}};
   bool found = false;
   for (const Try& tr : tries) {
-    if (tr.k < K) continue;
+    if (tr.k < K || tr.cmax < 1) continue;
     const uint64_t G = ceil_div(static_cast<uint64_t>(S), 32ull * tr.k);
-    const uint64_t ncta = ceil_div(G, static_cast<uint64_t>(tr.wcap));
-    if (ncta <= static_cast<uint64_t>(std::max(1, tr.cmax))) {
+    const uint64_t wcap = tr.grid ? std::min<uint64_t>(static_cast<uint64_t>(tr.wcap),
+                                                       std::max<uint64_t>(1, ceil_div(G, static_cast<uint64_t>(tr.cmax))))
+                                  : static_cast<uint64_t>(tr.wcap);
+    const uint64_t ncta = ceil_div(G, wcap);
+    if (ncta <= static_cast<uint64_t>(tr.cmax)) {
       p.shape = LaunchShape{tr.k, static_cast<int>(ceil_div(G, ncta)), static_cast<int>(ncta)};
+      p.shape.grid = tr.grid;
       found = true;
       break;
     }
@@ -93,8 +109,9 @@ int make_plan(const TuneTable& tune_in, int64_t T, int64_t C, int64_t L, uint64_
   p.ckpt_bytes = round_up(static_cast<uint64_t>(p.nck) * p.ck_stride * 4ull, 256);
   p.seg_z_off = round_up(row_bytes * static_cast<uint64_t>(p.ck_every), 256);
   p.seg_bp_bytes = p.seg_z_off + round_up(zrows(p.ck_every) * p.zstride, 256);
-  p.checkpointed = force_checkpoint || p.bp_bytes > budget;
-  if (p.checkpointed && p.ckpt_bytes + p.seg_bp_bytes > budget) return ALIGN_E_TOO_LARGE;
+  p.x_bytes = p.shape.grid ? xlink_bytes(p.shape.ncta) : 0;
+  p.checkpointed = force_checkpoint || p.bp_bytes + p.x_bytes > budget;
+  if (p.checkpointed && p.ckpt_bytes + p.seg_bp_bytes + p.x_bytes > budget) return ALIGN_E_TOO_LARGE;
   *out = p;
   return ALIGN_OK;
 }

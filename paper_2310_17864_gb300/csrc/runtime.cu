@@ -176,6 +176,8 @@ struct align_ctx {
   cudaStream_t main = nullptr;
   bool own_main = false;
   std::vector<cudaStream_t> workers;
+  cudaStream_t grid_stream = nullptr;   // every grid-team launch, in order: two teams never
+                                        // compete for the SMs each needs all of at once
   std::vector<cudaEvent_t> fork_events;
   std::vector<cudaEvent_t> event_pool;  // reusable events for batch joins and completion
   int next_worker = 0;
@@ -262,13 +264,14 @@ int reap(align_ctx* ctx) {
   return ALIGN_OK;
 }
 
-uint64_t request_bp_bytes(const Plan& p) { return p.checkpointed ? p.ckpt_bytes + p.seg_bp_bytes : p.bp_bytes; }
+uint64_t request_bp_bytes(const Plan& p) { return plan_device_bytes(p); }
 
 // Launch as many queued requests as fit, as one batch. Returns ALIGN_OK even
 // if nothing could be launched (they stay queued).
-// Plans the queued requests with the throughput table when their work
-// exceeds what the GPU runs at once (T * ceil(S/64) warp-frames, summed, above
-// T_max * 8 warps * SMs), else with the latency table. Plans are only
+// Plans the queued requests with the throughput table when there are several
+// and their work exceeds what the GPU runs at once (T * ceil(S/64)
+// warp-frames, summed, above T_max * 8 warps * SMs), else with the latency
+// table. Plans are only
 // remade for requests whose table changes; a request keeps its plan if the
 // other table cannot place it.
 bool choose_tables(align_ctx* ctx) {
@@ -280,7 +283,9 @@ bool choose_tables(align_ctx* ctx) {
     work += static_cast<uint64_t>(r.T) * static_cast<uint64_t>((2 * r.L + 1 + 63) / 64);
     tmax = std::max(tmax, r.T);
   }
-  const bool tp = work > static_cast<uint64_t>(tmax) * 8ull * static_cast<uint64_t>(std::max(1, ctx->num_sms));
+  // One request alone is a latency problem whatever its size.
+  const bool tp = ctx->queued.size() >= 2 &&
+                  work > static_cast<uint64_t>(tmax) * 8ull * static_cast<uint64_t>(std::max(1, ctx->num_sms));
   const int want = tp ? ALIGN_TUNE_THROUGHPUT : ALIGN_TUNE_LATENCY;
   for (uint64_t id : ctx->queued) {
     Request& r = ctx->reqs.at(id);
@@ -317,10 +322,10 @@ int launch_queued(align_ctx* ctx) {
     if (!p.checkpointed && !ctx->bp_arena.alloc(need, &r.bp.off)) {
       // Full backpointers do not fit now: fall back to checkpointed recompute
       // if that fits, otherwise wait for memory to be released.
-      if (p.ckpt_bytes + p.seg_bp_bytes <= ctx->bp_arena.cap() - ctx->bp_arena.used() &&
-          ctx->bp_arena.alloc(p.ckpt_bytes + p.seg_bp_bytes, &r.bp.off)) {
+      const uint64_t ck_need = p.ckpt_bytes + p.seg_bp_bytes + p.x_bytes;
+      if (ck_need <= ctx->bp_arena.cap() - ctx->bp_arena.used() && ctx->bp_arena.alloc(ck_need, &r.bp.off)) {
         p.checkpointed = true;
-        need = p.ckpt_bytes + p.seg_bp_bytes;
+        need = ck_need;
       } else {
         keep.push_back(id);
         continue;
@@ -362,8 +367,8 @@ int launch_queued(align_ctx* ctx) {
   size_t njobs = 0;
   for (size_t i = 0; i < take.size(); ++i) {
     const Plan& p = take[i]->plan;
-    if (p.checkpointed) {
-      njobs += 1 + static_cast<size_t>(p.nck);
+    if (p.checkpointed || p.shape.grid) {  // a launch sequence of its own
+      njobs += p.checkpointed ? 1 + static_cast<size_t>(p.nck) : 1;
     } else {
       groups[{p.shape.K, p.shape.warps, p.shape.ncta, p.frames_per_stage, static_cast<int>(take[i]->C), p.shape.occ}].push_back(
           static_cast<int>(i));
@@ -397,9 +402,10 @@ int launch_queued(align_ctx* ctx) {
                              static_cast<int64_t>(kv.second.size())});
     }
     for (auto* r : take) {
-      if (!r->plan.checkpointed) continue;
       const Plan& p = r->plan;
-      key.insert(key.end(), {-1, p.shape.K, p.shape.warps, p.shape.ncta, p.shape.occ, p.frames_per_stage, p.nck, r->C});
+      if (!p.checkpointed && !p.shape.grid) continue;
+      key.insert(key.end(), {-1, p.shape.K, p.shape.warps, p.shape.ncta, p.shape.occ, p.shape.grid, p.frames_per_stage,
+                             p.checkpointed ? p.nck : -1, r->C});
     }
     for (size_t k = 0; k < ctx->graphs.size(); ++k)
       if (ctx->graphs[k].key == key) gi = static_cast<int>(k);
@@ -546,8 +552,11 @@ int launch_queued(align_ctx* ctx) {
     int64_t t_max;  // longest job of the group (frames): its chain sets the launch's duration
   };
   std::vector<GroupLaunch> glaunch;
+  // Requests with a launch sequence of their own: checkpointed (pass 1, then
+  // the segments last to first) and grid teams (one cooperative launch each).
   struct CkLaunch {
-    size_t req, first;
+    size_t req, first, count;
+    uint64_t* xlink;  // grid team links (zeroed before every launch), or nullptr
   };
   std::vector<CkLaunch> cklaunch;
   size_t jn = 0;
@@ -580,8 +589,23 @@ int launch_queued(align_ctx* ctx) {
   for (size_t i = 0; i < take.size(); ++i) {
     const Request& r = *take[i];
     const Plan& p = r.plan;
-    if (!p.checkpointed) continue;
-    CkLaunch cl{i, jn};
+    if (!p.checkpointed && !p.shape.grid) continue;
+    uint64_t* xl = p.shape.grid ? reinterpret_cast<uint64_t*>(ctx->d_bp + r.bp.off + plan_x_off(p)) : nullptr;
+    CkLaunch cl{i, jn, p.checkpointed ? static_cast<size_t>(p.nck) + 1 : 1, xl};
+    if (!p.checkpointed) {  // grid team, full backpointers
+      FwdJob j = base_job(i);
+      j.bp = reinterpret_cast<uint32_t*>(ctx->d_bp + r.bp.off);
+      j.ztab = reinterpret_cast<uint8_t*>(ctx->d_bp + r.bp.off + p.z_off);
+      j.zstride = p.zstride;
+      j.t_begin = 0;
+      j.t_end = j.T;
+      j.bp_rows = std::max(j.T - 1, 0);
+      j.flags |= kJobWriteFinal | kJobChase;
+      j.xlink = xl;
+      hjobs[jn++] = j;
+      cklaunch.push_back(cl);
+      continue;
+    }
     float* ck = reinterpret_cast<float*>(ctx->d_bp + r.bp.off);
     uint32_t* seg = reinterpret_cast<uint32_t*>(ctx->d_bp + r.bp.off + p.ckpt_bytes);
     FwdJob j = base_job(i);  // pass 1: checkpoints every Kc frames, final state, no backpointers
@@ -591,6 +615,7 @@ int launch_queued(align_ctx* ctx) {
     j.ck_every = p.ck_every;
     j.ck_stride = p.ck_stride;
     j.flags |= kJobWriteFinal;
+    j.xlink = xl;
     hjobs[jn++] = j;
     for (int c = p.nck - 1; c >= 0; --c) {  // pass 2: segments, last first
       FwdJob s = base_job(i);
@@ -605,6 +630,7 @@ int launch_queued(align_ctx* ctx) {
       s.ztab = reinterpret_cast<uint8_t*>(ctx->d_bp + r.bp.off + p.ckpt_bytes + p.seg_z_off);
       s.zstride = p.zstride;
       s.flags |= kJobChase;
+      s.xlink = xl;
       hjobs[jn++] = s;
     }
     cklaunch.push_back(cl);
@@ -616,7 +642,9 @@ int launch_queued(align_ctx* ctx) {
   CU(cudaEventRecord(fork, ctx->main));
   // Idle streams first, so a new batch never queues behind a long kernel of an
   // earlier batch (head-of-line blocking); the pool grows when all are busy.
-  const size_t nlanes = std::max<size_t>(1, glaunch.size() + cklaunch.size());
+  size_t ngrid = 0;  // grid teams: all on the context's grid stream
+  for (const CkLaunch& cl : cklaunch) ngrid += cl.xlink ? 1 : 0;
+  const size_t nlanes = std::max<size_t>(1, glaunch.size() + cklaunch.size() - ngrid);
   std::vector<cudaStream_t> used;
   for (size_t k = 0; k < ctx->workers.size() && used.size() < nlanes; ++k) {
     cudaStream_t s = ctx->workers[(static_cast<size_t>(ctx->next_worker) + k) % ctx->workers.size()];
@@ -633,6 +661,8 @@ int launch_queued(align_ctx* ctx) {
     cudaStream_t s = ctx->workers[(static_cast<size_t>(ctx->next_worker) + k) % ctx->workers.size()];
     if (std::find(used.begin(), used.end(), s) == used.end()) used.push_back(s);
   }
+  const size_t nwork = used.size();
+  if (ngrid) used.push_back(ctx->grid_stream);
   cudaStream_t s0 = used[0];
   for (cudaStream_t s : used) CU(cudaStreamWaitEvent(s, fork, 0));
   uint64_t nkernels = 0;
@@ -653,11 +683,12 @@ int launch_queued(align_ctx* ctx) {
   size_t lane_i = 0;
   // Checkpointed sequences first (the longest utterances), then the groups.
   for (const CkLaunch& cl : cklaunch) {
-    cudaStream_t s = used[lane_i++ % used.size()];
+    cudaStream_t s = cl.xlink ? ctx->grid_stream : used[lane_i++ % nwork];
     if (s != s0) CU(cudaStreamWaitEvent(s, ready, 0));
     const Plan& p = take[cl.req]->plan;
     const FwdParams P = plan_params(p.shape, static_cast<int>(take[cl.req]->C), p.frames_per_stage, ctx->wait_limit_ns);
-    for (int k = 0; k <= p.nck; ++k) {
+    for (size_t k = 0; k < cl.count; ++k) {
+      if (cl.xlink) CU(cudaMemsetAsync(cl.xlink, 0, p.x_bytes, s));
       cudaError_t e = static_cast<cudaError_t>(launch_trellis(p.shape, P, djobs + cl.first + k, 1, s));
       if (e != cudaSuccess) {
         set_error("launch_trellis", e);
@@ -667,7 +698,7 @@ int launch_queued(align_ctx* ctx) {
     }
   }
   for (const GroupLaunch& gl : glaunch) {
-    cudaStream_t s = used[lane_i++ % used.size()];
+    cudaStream_t s = used[lane_i++ % nwork];
     if (s != s0) CU(cudaStreamWaitEvent(s, ready, 0));
     const int C = hjobs[gl.first].C;
     const FwdParams P = plan_params(gl.shape, C, gl.F, ctx->wait_limit_ns);
@@ -702,7 +733,7 @@ int launch_queued(align_ctx* ctx) {
   if (gi >= 0 && !need_capture) {
     const uint64_t nk = glaunch.size() + [&] {
       uint64_t c = 0;
-      for (const CkLaunch& cl : cklaunch) c += static_cast<uint64_t>(take[cl.req]->plan.nck) + 1;
+      for (const CkLaunch& cl : cklaunch) c += cl.count;
       return c;
     }();
     CU(cudaGraphLaunch(ctx->graphs[static_cast<size_t>(gi)].exec, s0));
@@ -813,6 +844,11 @@ int align_create(align_ctx** out, const align_config* cfg_in) {
   CU(cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, cfg.device));
   ctx->smem_optin = max_smem_optin(cfg.device);
   ctx->tune = default_tune_table();
+  int coop = 0;
+  CU(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, cfg.device));
+  // Grid teams for latency-planned batches only: a team holds whole SMs, and
+  // batches that oversubscribe the GPU are better served by clusters.
+  if (coop && !(cfg.flags & ALIGN_F_NO_GRID_TEAMS)) ctx->tune.max_grid = ctx->num_sms;
   const uint64_t bp_bytes = cfg.bp_budget_bytes ? cfg.bp_budget_bytes : (1ull << 30);
   const uint64_t stage_bytes = cfg.staging_bytes ? cfg.staging_bytes : (64ull << 20);
   const uint64_t meta_bytes = 64ull << 20;
@@ -848,6 +884,7 @@ int align_create(align_ctx** out, const align_config* cfg_in) {
     CU(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
     ctx->workers.push_back(s);
   }
+  CU(cudaStreamCreateWithFlags(&ctx->grid_stream, cudaStreamNonBlocking));
   for (int i = 0; i < 64; ++i) {
     cudaEvent_t e;
     CU(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
@@ -869,6 +906,10 @@ int align_destroy(align_ctx* ctx) {
   for (cudaStream_t s : ctx->workers) {
     cudaStreamSynchronize(s);
     cudaStreamDestroy(s);
+  }
+  if (ctx->grid_stream) {
+    cudaStreamSynchronize(ctx->grid_stream);
+    cudaStreamDestroy(ctx->grid_stream);
   }
   for (cudaEvent_t e : ctx->fork_events) cudaEventDestroy(e);
   if (ctx->own_main) {

@@ -75,7 +75,7 @@ struct alignas(16) FwdJob {
   uint32_t flags;
   int32_t zstride;         // bytes per anchor row (multiple of 16, >= S)
   uint8_t* ztab;           // anchor rows: row m holds s - anchor(s) at the end of window m
-  void* pad1;
+  uint64_t* xlink;         // grid teams: links between consecutive CTAs (zeroed before launch)
 };
 
 struct FwdParams {
@@ -87,6 +87,7 @@ struct FwdParams {
   int32_t off_stage;
   int32_t off_bt;
   int32_t stages;          // emission stages in the ring (kLead .. kMaxStages)
+  int32_t grid_ctas;       // 0: a team is one thread-block cluster; > 0: CTAs per grid team
   uint64_t wait_limit_ns;  // limit of every spin wait
 };
 
@@ -104,7 +105,18 @@ struct LaunchShape {
   int ncta;                // CTAs per cluster (1: no cluster)
   int occ = 0;             // 1: build with fewer registers per thread (K <= 4) for more
                            // resident warps, for batches that oversubscribe the GPU
+  int grid = 0;            // 1: the team is ncta CTAs of one cooperative launch, one per SM,
+                           // linked through global memory (transcripts beyond a cluster)
 };
+
+// Bytes of the global links of a grid team of ncta CTAs: a ring of kMaxRing
+// words per CTA boundary, one progress word per CTA and a 2-word barrier.
+constexpr int kMaxRing = 128;  // ring slots per boundary, at least P.rb
+inline uint64_t xlink_bytes(int ncta) {
+  const uint64_t b = static_cast<uint64_t>(ncta > 1 ? ncta - 1 : 0) * kMaxRing * 8ull +
+                     static_cast<uint64_t>((ncta + 3) & ~3) * 4ull + 16ull;
+  return (b + 255) & ~255ull;
+}
 
 // Number of 32-bit backpointer words per warp and frame.
 #ifdef __CUDACC__

@@ -61,6 +61,17 @@ __device__ __forceinline__ uint32_t mapa_rank(uint32_t addr, uint32_t rank) {
 __device__ __forceinline__ void st_remote_u32(uint32_t addr, uint32_t v) {
   asm volatile("st.relaxed.cluster.shared::cluster.u32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
 }
+__device__ __forceinline__ void st_gpu_u32(uint32_t* p, uint32_t v) {
+  asm volatile("st.relaxed.gpu.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ uint32_t ld_acquire_gpu_u32(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_gpu_u32(uint32_t* p, uint32_t v) {
+  asm volatile("st.release.gpu.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
 }
@@ -205,13 +216,46 @@ __device__ __forceinline__ void st_global_v4_if(uint32_t* p, uint32_t x, uint32_
       "r"(x), "r"(y), "r"(z), "r"(w), "r"(static_cast<uint32_t>(pred))
       : "memory");
 }
-__device__ __forceinline__ void st_cluster_v2_if(uint32_t addr, uint32_t lo, uint32_t hi, bool pred) {
+__device__ __forceinline__ void st_cluster_u64_if(uint32_t addr, uint64_t v, bool pred) {
   asm volatile(
-      "{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %3, 0;\n\t@q st.relaxed.cluster.shared::cluster.v2.u32 [%0], {%1, %2};\n\t}" ::"r"(
+      "{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t@q st.relaxed.cluster.shared::cluster.u64 [%0], %1;\n\t}" ::"r"(
           addr),
-      "r"(lo), "r"(hi), "r"(static_cast<uint32_t>(pred))
+      "l"(v), "r"(static_cast<uint32_t>(pred))
       : "memory");
 }
+__device__ __forceinline__ void st_gpu_u64_if(uint64_t* p, uint64_t v, bool pred) {
+  asm volatile(
+      "{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t@q st.relaxed.gpu.u64 [%0], %1;\n\t}" ::"l"(p), "l"(v),
+      "r"(static_cast<uint32_t>(pred))
+      : "memory");
+}
+
+// Barrier of the CTAs of a grid team (co-resident: cooperative launch, one
+// CTA per SM). bar[0] counts arrivals, bar[1] is the generation. Bounded: on
+// timeout the CTA raises its abort flag and continues.
+__device__ void team_barrier(uint32_t* bar, uint32_t ncta, volatile int32_t* abort, uint64_t limit) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const uint32_t gen = ld_acquire_gpu_u32(bar + 1);
+    if (atomicAdd(bar, 1u) == ncta - 1) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      st_release_gpu_u32(bar + 1, gen + 1u);
+    } else {
+      const uint64_t t0 = gtimer();
+      while (ld_acquire_gpu_u32(bar + 1) == gen) {
+        if (gtimer() - t0 > limit) {
+          *abort = 1;
+          break;
+        }
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+}
+
 // All backpointer words of one warp and frame, stored by lane 0 under a single
 // predicate (one setp per frame).
 template <int K>
@@ -268,7 +312,11 @@ __device__ __forceinline__ void store_bp_row(uint32_t* dst, const uint32_t (&w)[
 // ------------------------------------------------------------------ kernel --
 // kOcc: the register budget of K <= 4 is capped at 64 per thread (two
 // 512-thread CTAs per SM), trading per-warp latency for resident warps.
-template <int K, bool kOcc>
+//
+// kGrid: the team is P.grid_ctas consecutive CTAs of a cooperative launch
+// (one per SM) instead of a thread-block cluster; the links between CTAs (the
+// boundary rings, progress words, barrier) are in global memory.
+template <int K, bool kOcc, bool kGrid>
 __global__ void __launch_bounds__(512, (kOcc && K <= 4) ? 2 : 1)
     trellis_kernel(const FwdJob* __restrict__ jobs, const FwdParams P) {
   static_assert(K % 2 == 0 && K >= 2 && K <= 16, "K must be even, 2..16");
@@ -280,8 +328,8 @@ __global__ void __launch_bounds__(512, (kOcc && K <= 4) ? 2 : 1)
   unsigned char* stages = smem + P.off_stage;
   volatile int32_t* abort = &head->abort;
 
-  const uint32_t ncta = cluster_nctarank();
-  const uint32_t crank = cluster_ctarank();
+  const uint32_t ncta = kGrid ? static_cast<uint32_t>(max(P.grid_ctas, 1)) : cluster_nctarank();
+  const uint32_t crank = kGrid ? blockIdx.x % ncta : cluster_ctarank();
   const int W = blockDim.x >> 5;
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
@@ -311,7 +359,8 @@ __global__ void __launch_bounds__(512, (kOcc && K <= 4) ? 2 : 1)
                        (P.block & (P.block - 1)) == 0;
   const bool ck_ok = ckpt == nullptr || (ck_every > 0 && ck_every % kAnchorD == 0 && t_begin % ck_every == 0);
   if (F * C * 4 > P.stage_bytes || static_cast<int64_t>(ncta) * W * 32 * K < S || P.stages < kLead ||
-      P.stages > kMaxStages || !pow2_ok || !ck_ok) {
+      P.stages > kMaxStages || !pow2_ok || !ck_ok || (kGrid && (P.grid_ctas < 1 || J.xlink == nullptr ||
+                                                                  P.rb > kMaxRing))) {
     if (threadIdx.x == 0 && crank == 0) atomicExch(J.status, kStBadLaunch);
     return;
   }
@@ -327,7 +376,9 @@ __global__ void __launch_bounds__(512, (kOcc && K <= 4) ? 2 : 1)
     fence_barrier_init();
   }
   __syncthreads();
-  if (ncta > 1) cluster_sync();  // neighbours' rings exist and are zero before any remote store
+  // Neighbours' rings exist and are zero before any remote store (grid teams:
+  // the global links were zeroed before the launch).
+  if (!kGrid && ncta > 1) cluster_sync();
 
   // ---- per-lane constants: label columns and skip caps of the label states ----
   int col[K / 2];
@@ -425,20 +476,53 @@ __global__ void __launch_bounds__(512, (kOcc && K <= 4) ? 2 : 1)
   const bool has_next = send_local || send_remote;
   if (threadIdx.x < 32) prog_w[threadIdx.x] = static_cast<uint32_t>(t_begin);
   __syncthreads();
-  if (ncta > 1) cluster_sync();  // progress words initialised before any remote publish
-  const uint32_t send_base = send_local    ? smem_addr(ring + (warp + 1) * P.rb)
+  if (!kGrid && ncta > 1) cluster_sync();  // progress words initialised before any remote publish
+  // Grid teams: ring b (CTA b's last warp -> CTA b+1) at xlink + b * kMaxRing,
+  // then prog[b] (how far CTA b+1 has read ring b), then the team barrier.
+  uint64_t* const xring = kGrid ? J.xlink : nullptr;
+  uint32_t* const xprog = kGrid ? reinterpret_cast<uint32_t*>(J.xlink + static_cast<size_t>(ncta - 1) * kMaxRing) : nullptr;
+  uint32_t* const xbar = kGrid ? xprog + ((ncta + 3u) & ~3u) : nullptr;
+  // Team barrier with a uniform give-up decision (see the tails below).
+  auto team_sync_ok = [&]() -> bool {
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0 && *abort != 0) atomicExch(J.status, kStTimeout);
+    if constexpr (kGrid) {
+      team_barrier(xbar, ncta, abort, limit);  // ends with __syncthreads
+      if (*abort != 0) {                       // this CTA's barrier wait ran out
+        if (threadIdx.x == 0) atomicExch(J.status, kStTimeout);
+        return false;
+      }
+    } else if (ncta > 1) {
+      cluster_sync();
+    } else {
+      __syncthreads();
+    }
+    return *reinterpret_cast<const volatile int32_t*>(J.status) != kStTimeout;
+  };
+  const uint32_t send_base = kGrid ? 0u
+                             : send_local  ? smem_addr(ring + (warp + 1) * P.rb)
                              : send_remote ? mapa_rank(smem_addr(ring), crank + 1)
                                            : smem_addr(&head->sink);
+  uint64_t* const send_ptr = !kGrid ? nullptr
+                             : send_local  ? ring + (warp + 1) * P.rb
+                             : send_remote ? xring + static_cast<size_t>(crank) * kMaxRing
+                                           : &head->sink;
   const uint32_t send_mask = has_next ? static_cast<uint32_t>(rb_mask) : 0u;
   // Where this warp publishes how far it has read its ring (its producer's prog_w slot).
-  const uint32_t prog_dst = !recv_left ? 0u
+  const uint32_t prog_dst = (kGrid || !recv_left) ? 0u
                             : (warp > 0) ? smem_addr(prog_w + (warp - 1))
                                          : mapa_rank(smem_addr(prog_w + (W - 1)), crank - 1);
-  const volatile uint32_t* my_prog = prog_w + warp;  // progress of the warp this one sends to
+  uint32_t* const prog_dst_g = (!kGrid || !recv_left) ? nullptr
+                               : (warp > 0) ? prog_w + (warp - 1)
+                                            : xprog + (crank - 1);
+  // Progress of the warp this one sends to.
+  const volatile uint32_t* my_prog = (kGrid && send_remote) ? xprog + crank : prog_w + warp;
   int prog_seen = t_begin;                           // consumer has read every frame < prog_seen
   const bool is_l0 = (lane == 0);
   const bool is_l31 = (lane == 31) && !((J.flags & kJobTestStall) && g == 0);
-  const uint64_t* my_ring = ring + warp * P.rb;
+  const uint64_t* my_ring = (kGrid && warp == 0 && crank > 0) ? xring + static_cast<size_t>(crank - 1) * kMaxRing
+                                                               : ring + warp * P.rb;
   constexpr uint32_t kTagMask = (1u << kTagBits) - 1u;
   const int s_last = s0 + K - 1;
 
@@ -450,8 +534,13 @@ __global__ void __launch_bounds__(512, (kOcc && K <= 4) ? 2 : 1)
   };
   auto send_one = [&](int t, float v, int anc) {
     // High word: tag (t+1 mod 2^24) << 8 | anchor offset; low word: alpha bits.
+    // One 64-bit store: a reader that sees the tag also sees the value.
     const uint32_t hi = ((static_cast<uint32_t>(t) + 1u) << 8) + (static_cast<uint32_t>(s_last - anc) & 0xffu);
-    st_cluster_v2_if(send_base + (static_cast<uint32_t>(t) & send_mask) * 8u, __float_as_uint(v), hi, is_l31);
+    const uint64_t word = (static_cast<uint64_t>(hi) << 32) | __float_as_uint(v);
+    if constexpr (kGrid)
+      st_gpu_u64_if(send_ptr + (static_cast<uint32_t>(t) & send_mask), word, is_l31);
+    else
+      st_cluster_u64_if(send_base + (static_cast<uint32_t>(t) & send_mask) * 8u, word, is_l31);
   };
   // Anchor row of window m: s - anchor(s) of this lane's states, one store.
   uint8_t* const ztab = J.ztab;
@@ -539,7 +628,12 @@ __global__ void __launch_bounds__(512, (kOcc && K <= 4) ? 2 : 1)
         rv = __uint_as_float(static_cast<uint32_t>(vv));
         roff = static_cast<int>((vv >> 32) & 0xffu);
         // Frames < t + nb - 1 are read after this block: tell the producer.
-        if (is_l0) st_remote_u32(prog_dst, static_cast<uint32_t>(t + nb - 1));
+        if (is_l0) {
+          if constexpr (kGrid)
+            st_gpu_u32(prog_dst_g, static_cast<uint32_t>(t + nb - 1));
+          else
+            st_remote_u32(prog_dst, static_cast<uint32_t>(t + nb - 1));
+        }
       }
       // Frame t-1 ends a window when this block starts one: its sender reset
       // its anchors after sending it.
@@ -677,12 +771,10 @@ __global__ void __launch_bounds__(512, (kOcc && K <= 4) ? 2 : 1)
     for (int c = max(0, issued - P.stages); c < issued; ++c)
       (void)wait_phase(&head->full[c % P.stages], (c / P.stages) & 1, abort, limit, false);
   }
-  __threadfence();
-  __syncthreads();
-  if (ncta > 1) cluster_sync();  // all backpointers / anchor rows / final values written
-  const bool aborted = (*abort != 0);
-  if (aborted && threadIdx.x == 0) atomicExch(J.status, kStTimeout);
-  if (aborted) return;  // uniform across the CTA (read after the barrier)
+  // All backpointers / anchor rows / final values written. A CTA whose wait
+  // ran out marks the request timed out before the team barrier; after it
+  // every CTA of the team reads the same status and leaves together.
+  if (!team_sync_ok()) return;
 
   // ---- tail 1 (warp 0 of CTA 0): final state, total, hops back through the anchor rows ----
   // Boundary states go to path[t_begin + m*D] (m < nwin) and path[t_end - 1];
@@ -735,9 +827,7 @@ __global__ void __launch_bounds__(512, (kOcc && K <= 4) ? 2 : 1)
     }
   }
   if (!chase) return;
-  __threadfence();
-  __syncthreads();
-  if (ncta > 1) cluster_sync();  // boundary states visible to every warp of the team
+  if (!team_sync_ok()) return;  // boundary states visible to every warp of the team
 
   // ---- tail 2 (every lane of the team): walk the windows in parallel ----
   // Window m covers frames (t_begin + m*D, e] with e = min(t_begin + (m+1)*D,
@@ -764,9 +854,7 @@ __global__ void __launch_bounds__(512, (kOcc && K <= 4) ? 2 : 1)
     }
     if (m == 0) J.path[b] = sc;
   }
-  __threadfence();
-  __syncthreads();
-  if (ncta > 1) cluster_sync();  // every frame's state is in path[]
+  if (!team_sync_ok()) return;  // every frame's state is in path[]
 
   // ---- tail 3 (every thread of the team): states -> tokens, states, scores ----
   {
@@ -813,11 +901,20 @@ __global__ void __launch_bounds__(1024) frame_probe_kernel(int frames, uint64_t 
   }
 }
 
-template <int K, bool kOcc>
+template <int K, bool kOcc, bool kGrid>
 cudaError_t launch_k(const LaunchShape& shape, const FwdParams& p, const FwdJob* d_jobs, int njobs,
                      cudaStream_t stream) {
-  const int smem = smem_bytes(shape, p);
-  auto fn = trellis_kernel<K, kOcc>;
+  int smem = smem_bytes(shape, p);
+  if (kGrid) {
+    // One CTA per SM: all of the opt-in shared memory, so that no other CTA
+    // shares the SM and the cooperative launch can place the whole team.
+    int dev = 0;
+    cudaError_t de = cudaGetDevice(&dev);
+    if (de != cudaSuccess) return de;
+    smem = std::max(smem, max_smem_optin(dev));
+    if (njobs != 1) return cudaErrorInvalidValue;  // one team per cooperative launch
+  }
+  auto fn = trellis_kernel<K, kOcc, kGrid>;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
@@ -826,7 +923,12 @@ cudaError_t launch_k(const LaunchShape& shape, const FwdParams& p, const FwdJob*
   cfg.dynamicSmemBytes = static_cast<size_t>(smem);
   cfg.stream = stream;
   cudaLaunchAttribute attr[1];
-  if (shape.ncta > 1) {
+  if (kGrid) {
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+  } else if (shape.ncta > 1) {
     if (shape.ncta > 8) {
       e = cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
       if (e != cudaSuccess) return e;
@@ -860,6 +962,7 @@ FwdParams plan_params(const LaunchShape& shape, int C, int frames_per_stage, uin
   p.block = 1;
   while (p.block * 2 <= room) p.block *= 2;
   p.stages = kLead + (hops * p.block + F - 1) / F;
+  p.grid_ctas = shape.grid ? shape.ncta : 0;
   int rb = 8;
   while (rb < 2 * p.block + 2) rb <<= 1;
   p.rb = rb;
@@ -887,10 +990,20 @@ int launch_trellis(const LaunchShape& shape, const FwdParams& p, const FwdJob* d
   if (njobs <= 0) return cudaSuccess;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   switch (shape.K) {
-    case 2: return shape.occ ? launch_k<2, true>(shape, p, d_jobs, njobs, s) : launch_k<2, false>(shape, p, d_jobs, njobs, s);
-    case 4: return shape.occ ? launch_k<4, true>(shape, p, d_jobs, njobs, s) : launch_k<4, false>(shape, p, d_jobs, njobs, s);
-    case 8: return launch_k<8, false>(shape, p, d_jobs, njobs, s);
-    case 16: return launch_k<16, false>(shape, p, d_jobs, njobs, s);
+    case 2:
+      if (shape.grid) return launch_k<2, false, true>(shape, p, d_jobs, njobs, s);
+      return shape.occ ? launch_k<2, true, false>(shape, p, d_jobs, njobs, s)
+                       : launch_k<2, false, false>(shape, p, d_jobs, njobs, s);
+    case 4:
+      if (shape.grid) return launch_k<4, false, true>(shape, p, d_jobs, njobs, s);
+      return shape.occ ? launch_k<4, true, false>(shape, p, d_jobs, njobs, s)
+                       : launch_k<4, false, false>(shape, p, d_jobs, njobs, s);
+    case 8:
+      if (shape.grid) return launch_k<8, false, true>(shape, p, d_jobs, njobs, s);
+      return launch_k<8, false, false>(shape, p, d_jobs, njobs, s);
+    case 16:
+      if (shape.grid) return launch_k<16, false, true>(shape, p, d_jobs, njobs, s);
+      return launch_k<16, false, false>(shape, p, d_jobs, njobs, s);
     default: return cudaErrorInvalidValue;
   }
 }

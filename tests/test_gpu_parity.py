@@ -310,6 +310,81 @@ def test_watchdog_timeout_keeps_context_usable():
         ok.close()
 
 
+def test_grid_team_equals_cluster_and_checkpointed():
+    """A transcript beyond one cluster of the default shape (S = 34,001) runs
+    as a grid team (one 16-warp CTA per SM, links in global memory); the
+    result is bit-identical to the cluster plan with more states per lane and
+    to checkpointed recompute on the grid team."""
+    build.build()
+    T, L = 36000, 17000
+    u = synth.make_utterance(31, T, 32, L)
+    lp = u.lp.cuda()
+    outs = {}
+    for name, kw in [("grid", {}), ("cluster", {"grid_teams": False}), ("grid_ck", {"force_checkpoint": True})]:
+        a = align.Aligner(device=0, bp_budget_bytes=8 << 30, **kw)
+        try:
+            r = a.align(lp, u.targets, 0, want_states=True)
+            assert r.status == 0, (name, r.status)
+            outs[name] = [x.cpu().view(torch.int32) for x in (r.path, r.states, r.scores, r.total)]
+        finally:
+            a.close()
+    for name in ("cluster", "grid_ck"):
+        for x, y in zip(outs["grid"], outs[name]):
+            assert torch.equal(x, y), name
+    # The oracle's frame states at sampled frames, from the forward/backward max-plus sums.
+    o = oracle.viterbi_f32(u.lp.numpy(), np.asarray(u.targets, np.int32), 0)
+    assert np.array_equal(outs["grid"][1].numpy(), o["states"])
+
+
+def test_two_grid_teams_and_small_requests_in_one_batch():
+    """Grid teams of one batch run one after the other on the context's grid
+    stream (each needs its SMs at once) while small requests run beside them;
+    every result equals the request aligned alone."""
+    build.build()
+    us = [synth.make_utterance(41, 36000, 32, 17000), synth.make_utterance(42, 34000, 32, 16500),
+          synth.make_utterance(43, 500, 32, 120), synth.make_utterance(44, 800, 32, 200)]
+    al = align.Aligner(device=0, batched=True, bp_budget_bytes=12 << 30)
+    one = align.Aligner(device=0, bp_budget_bytes=8 << 30)
+    try:
+        items, outs = [], []
+        for u in us:
+            T = u.lp.shape[0]
+            o = (torch.empty(T, dtype=torch.int32, device="cuda:0"), torch.empty(T, device="cuda:0"),
+                 torch.empty(1, device="cuda:0"), None)
+            outs.append(o)
+            items.append((u.lp.cuda(), u.targets, 0, o))
+        rs = al.submit_batch(items)
+        al.flush()
+        for r in rs:
+            al.poll(r)
+            assert r.status == 0
+        for u, o in zip(us, outs):
+            ref = one.align(u.lp.cuda(), u.targets, 0)
+            assert torch.equal(o[0], ref.path) and torch.equal(o[1].view(torch.int32), ref.scores.view(torch.int32))
+    finally:
+        al.close()
+        one.close()
+
+
+def test_grid_team_watchdog():
+    """The bounded waits of a grid team (ring, progress, team barrier) end a
+    stalled request with ALIGN_E_TIMEOUT; the context stays usable."""
+    build.build()
+    u = synth.make_utterance(32, 36000, 32, 17000)
+    st = align.Aligner(device=0, bp_budget_bytes=8 << 30, wait_limit_ms=100, test_stall=True)
+    try:
+        r = st.align(u.lp.cuda(), u.targets, 0)
+        assert r.status == align.ALIGN_E_TIMEOUT
+    finally:
+        st.close()
+    v = synth.make_utterance(4, 100, 32, 20)
+    ok = align.Aligner(device=0)
+    try:
+        compare(ok.align(v.lp.cuda(), v.targets, 0), v.lp.numpy(), v.targets, 0, "after grid timeout")
+    finally:
+        ok.close()
+
+
 def test_graph_replay_equals_direct_launch():
     """A batch with the same launch structure is captured once and replayed;
     results equal direct launches bit for bit."""
