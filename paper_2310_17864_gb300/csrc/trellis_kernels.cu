@@ -831,16 +831,18 @@ __global__ void __launch_bounds__(512, (kOcc && K <= 4) ? 2 : 1)
 
   // ---- tail 2 (every lane of the team): walk the windows in parallel ----
   // Window m covers frames (t_begin + m*D, e] with e = min(t_begin + (m+1)*D,
-  // t_end - 1); its top state is path[e]. One lane walks one window, reading
-  // the two backpointer words of each step straight from L2 (the rows were
-  // written moments ago), and stores the state of every frame into path[]
-  // (window 0 also frame t_begin). Lanes of a warp walk 32 windows at once.
+  // t_end - 1); its top state is path[e]. One lane walks one window and stores
+  // the state of every frame into path[] (window 0 also frame t_begin); lanes
+  // of a warp walk 32 windows at once. The backpointer words are read with
+  // plain (L1-cached) loads: they were written before the team barrier, whose
+  // acquire makes them visible, and consecutive frames of a warp group share
+  // cache lines.
   const int G = static_cast<int>(ncta) * W;
   const int nwalk = max(nwin, 1);
   for (int m = g * 32 + lane; m < nwalk; m += G * 32) {
     const int b = t_begin + m * kAnchorD;
     const int e = (nwin == 0) ? t_begin : min(b + kAnchorD, t_end - 1);
-    int sc = __ldcg(J.path + e);
+    int sc = J.path[e];
     for (int f = e; f > b; --f) {
       J.path[f] = sc;
       const int gs = sc / GS;
@@ -848,8 +850,8 @@ __global__ void __launch_bounds__(512, (kOcc && K <= 4) ? 2 : 1)
       const int ln = r / K;
       const int j = r % K;
       const uint32_t* wd = bp + (static_cast<size_t>(gs) * bp_rows + (f - t_begin - 1)) * NW;
-      const uint32_t av = (__ldcg(wd + j) >> ln) & 1u;
-      const uint32_t sk = (__ldcg(wd + K + (j >> 1)) >> ln) & static_cast<uint32_t>(j) & 1u;
+      const uint32_t av = (wd[j] >> ln) & 1u;
+      const uint32_t sk = (wd[K + (j >> 1)] >> ln) & static_cast<uint32_t>(j) & 1u;
       sc -= sk ? 2 : static_cast<int>(av);
     }
     if (m == 0) J.path[b] = sc;
@@ -857,16 +859,38 @@ __global__ void __launch_bounds__(512, (kOcc && K <= 4) ? 2 : 1)
   if (!team_sync_ok()) return;  // every frame's state is in path[]
 
   // ---- tail 3 (every thread of the team): states -> tokens, states, scores ----
+  // Each thread takes kT3 frames per round, loading all their states, then
+  // all their tokens, then all their emission values: three memory round
+  // trips per round instead of three per frame.
   {
+    constexpr int kT3 = 8;
     const int tid = g * 32 + lane;
     const int nthr = G * 32;
-#pragma unroll 4
-    for (int f = t_begin + tid; f < t_end; f += nthr) {
-      const int st = __ldcg(J.path + f);
-      const int tok = (st & 1) ? __ldg(J.tgt + (st >> 1)) : blank;
-      J.path[f] = tok;
-      if (J.states) J.states[f] = st;
-      J.scores[f] = __ldg(lp + static_cast<size_t>(f) * C + tok);
+    int32_t* const states_out = J.states;
+    for (int f0 = t_begin + tid; f0 < t_end; f0 += kT3 * nthr) {
+      int st[kT3], tok[kT3];
+      float sv[kT3];
+#pragma unroll
+      for (int k = 0; k < kT3; ++k) {
+        const int f = f0 + k * nthr;
+        st[k] = (f < t_end) ? J.path[f] : 0;
+      }
+#pragma unroll
+      for (int k = 0; k < kT3; ++k) tok[k] = (st[k] & 1) ? __ldg(J.tgt + (st[k] >> 1)) : blank;
+#pragma unroll
+      for (int k = 0; k < kT3; ++k) {
+        const int f = f0 + k * nthr;
+        sv[k] = (f < t_end) ? __ldg(lp + static_cast<size_t>(f) * C + tok[k]) : 0.0f;
+      }
+#pragma unroll
+      for (int k = 0; k < kT3; ++k) {
+        const int f = f0 + k * nthr;
+        if (f < t_end) {
+          J.path[f] = tok[k];
+          if (states_out) states_out[f] = st[k];
+          J.scores[f] = sv[k];
+        }
+      }
     }
   }
 }
@@ -904,19 +928,24 @@ __global__ void __launch_bounds__(1024) frame_probe_kernel(int frames, uint64_t 
 template <int K, bool kOcc, bool kGrid>
 cudaError_t launch_k(const LaunchShape& shape, const FwdParams& p, const FwdJob* d_jobs, int njobs,
                      cudaStream_t stream) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const int smem_max = max_smem_optin(dev);
   int smem = smem_bytes(shape, p);
   if (kGrid) {
     // One CTA per SM: all of the opt-in shared memory, so that no other CTA
     // shares the SM and the cooperative launch can place the whole team.
-    int dev = 0;
-    cudaError_t de = cudaGetDevice(&dev);
-    if (de != cudaSuccess) return de;
-    smem = std::max(smem, max_smem_optin(dev));
+    smem = std::max(smem, smem_max);
     if (njobs != 1) return cudaErrorInvalidValue;  // one team per cooperative launch
   }
   auto fn = trellis_kernel<K, kOcc, kGrid>;
-  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  // The allowed maximum is always the device's opt-in limit, never the size
+  // of the launch at hand: launches of one kernel captured into a graph ask
+  // for different sizes, and none may see a limit lowered by another.
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max);
   if (e != cudaSuccess) return e;
+  if (smem > smem_max) return cudaErrorInvalidValue;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(static_cast<unsigned>(njobs * shape.ncta), 1, 1);
   cfg.blockDim = dim3(static_cast<unsigned>(shape.warps * 32), 1, 1);
