@@ -108,6 +108,10 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
 __device__ __forceinline__ void cp_async4(void* dst, const void* src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
 }
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_mbar_arrive(uint64_t* bar) {
   asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
@@ -349,6 +353,13 @@ __global__ void __launch_bounds__(512, (kOcc && K <= 4) ? 2 : 1)
   float* __restrict__ ckpt = J.ckpt;
   const int ck_every = J.ck_every;
   const int ck_stride = J.ck_stride;
+  // Output pointers in registers: stores through them could alias the
+  // descriptor, and re-reading it from global memory after every store put a
+  // memory round trip on each step of the backtrack.
+  int32_t* const path = J.path;
+  float* const scores_out = J.scores;
+  int32_t* const states_out = J.states;
+  const int32_t* const tgt = J.tgt;
 
   // Launch parameters must fit the job: a stage holds F rows of C floats and
   // the team holds every state. The check is uniform over the cluster (same
@@ -394,8 +405,8 @@ __global__ void __launch_bounds__(512, (kOcc && K <= 4) ? 2 : 1)
     int lab = 0;
     bool skip = false;
     if (s < S) {
-      lab = J.tgt[(s - 1) >> 1];
-      skip = (s >= 3) && (lab != J.tgt[(s - 3) >> 1]);
+      lab = tgt[(s - 1) >> 1];
+      skip = (s >= 3) && (lab != tgt[(s - 3) >> 1]);
     }
     col[i] = lab;
     skok[i] = skip;
@@ -797,27 +808,31 @@ __global__ void __launch_bounds__(512, (kOcc && K <= 4) ? 2 : 1)
       s_cur = __ldcg(J.state_io);
     }
     if (chase) {
-      if (lane == 0) J.path[t_end - 1] = s_cur;
-      // Batches of kHopBatch rows: the states of the next kHopBatch window
-      // starts lie in [s - 2*kHopBatch*D, s]; lanes copy that byte range of
-      // each row into shared memory, then lane 0 hops.
-      uint8_t* zb = tail;  // [kHopBatch][span]
-      constexpr int kSpan = ((2 * kHopBatch * kAnchorD + 16) + 15) / 16 * 16 + 16;
+      if (lane == 0) path[t_end - 1] = s_cur;
+      // Batches of kHopBatch rows: lane q copies bytes [lo + 16q, lo + 16q + 16)
+      // of every row into shared memory (asynchronous copies, one wait), the
+      // range [s - kHopSpan, s] around the current state; then lane 0 hops.
+      // A path moves at most 64 states per window but far fewer in practice;
+      // a hop below the staged range reads its byte from global memory.
+      uint8_t* zb = tail;  // [kHopBatch][kHopRowBytes]
       for (int m = nwin - 1; m >= 0; m -= kHopBatch) {
         const int nb = min(kHopBatch, m + 1);
-        const int lo = max(0, s_cur - 2 * kHopBatch * kAnchorD) & ~15;
+        const int lo = max(0, s_cur - kHopSpan) & ~15;
         const int hi = min(zstride, (s_cur + 16) & ~15);  // exclusive, 16-aligned
-        const int nchunk = (hi - lo) / 16;
-        for (int k = lane; k < nb * nchunk; k += 32) {
-          const int r = k / nchunk, q = k % nchunk;
-          const uint4 v = __ldcg(reinterpret_cast<const uint4*>(ztab + static_cast<size_t>(m - r) * zstride + lo) + q);
-          *reinterpret_cast<uint4*>(zb + r * kSpan + q * 16) = v;
+        const int nchunk = (hi - lo) / 16;                // <= kHopRowBytes / 16
+        if (lane < nchunk) {
+          for (int r = 0; r < nb; ++r)
+            cp_async16(zb + r * kHopRowBytes + lane * 16, ztab + static_cast<size_t>(m - r) * zstride + lo + lane * 16);
         }
+        cp_async_wait_all();
         __syncwarp();
         if (lane == 0) {
           for (int r = 0; r < nb; ++r) {
-            s_cur -= zb[r * kSpan + (s_cur - lo)];
-            J.path[t_begin + (m - r) * kAnchorD] = s_cur;
+            const int off = s_cur - lo;
+            const int d = (off >= 0) ? static_cast<int>(zb[r * kHopRowBytes + off])
+                                     : static_cast<int>(__ldcg(ztab + static_cast<size_t>(m - r) * zstride + s_cur));
+            s_cur -= d;
+            path[t_begin + (m - r) * kAnchorD] = s_cur;
           }
         }
         s_cur = __shfl_sync(kFull, s_cur, 0);
@@ -842,9 +857,9 @@ __global__ void __launch_bounds__(512, (kOcc && K <= 4) ? 2 : 1)
   for (int m = g * 32 + lane; m < nwalk; m += G * 32) {
     const int b = t_begin + m * kAnchorD;
     const int e = (nwin == 0) ? t_begin : min(b + kAnchorD, t_end - 1);
-    int sc = J.path[e];
+    int sc = path[e];
     for (int f = e; f > b; --f) {
-      J.path[f] = sc;
+      path[f] = sc;
       const int gs = sc / GS;
       const int r = sc % GS;
       const int ln = r / K;
@@ -854,7 +869,7 @@ __global__ void __launch_bounds__(512, (kOcc && K <= 4) ? 2 : 1)
       const uint32_t sk = (wd[K + (j >> 1)] >> ln) & static_cast<uint32_t>(j) & 1u;
       sc -= sk ? 2 : static_cast<int>(av);
     }
-    if (m == 0) J.path[b] = sc;
+    if (m == 0) path[b] = sc;
   }
   if (!team_sync_ok()) return;  // every frame's state is in path[]
 
@@ -866,17 +881,16 @@ __global__ void __launch_bounds__(512, (kOcc && K <= 4) ? 2 : 1)
     constexpr int kT3 = 8;
     const int tid = g * 32 + lane;
     const int nthr = G * 32;
-    int32_t* const states_out = J.states;
     for (int f0 = t_begin + tid; f0 < t_end; f0 += kT3 * nthr) {
       int st[kT3], tok[kT3];
       float sv[kT3];
 #pragma unroll
       for (int k = 0; k < kT3; ++k) {
         const int f = f0 + k * nthr;
-        st[k] = (f < t_end) ? J.path[f] : 0;
+        st[k] = (f < t_end) ? path[f] : 0;
       }
 #pragma unroll
-      for (int k = 0; k < kT3; ++k) tok[k] = (st[k] & 1) ? __ldg(J.tgt + (st[k] >> 1)) : blank;
+      for (int k = 0; k < kT3; ++k) tok[k] = (st[k] & 1) ? __ldg(tgt + (st[k] >> 1)) : blank;
 #pragma unroll
       for (int k = 0; k < kT3; ++k) {
         const int f = f0 + k * nthr;
@@ -886,9 +900,9 @@ __global__ void __launch_bounds__(512, (kOcc && K <= 4) ? 2 : 1)
       for (int k = 0; k < kT3; ++k) {
         const int f = f0 + k * nthr;
         if (f < t_end) {
-          J.path[f] = tok[k];
+          path[f] = tok[k];
           if (states_out) states_out[f] = st[k];
-          J.scores[f] = sv[k];
+          scores_out[f] = sv[k];
         }
       }
     }
@@ -1010,8 +1024,7 @@ int smem_bytes(const LaunchShape& shape, const FwdParams& p) {
   // The backtrack reuses the ring / stage region for the hop buffer of
   // kHopBatch anchor-row slices.
   (void)shape;
-  const int span = ((2 * kHopBatch * kAnchorD + 16) + 15) / 16 * 16 + 16;
-  return std::max(p.off_bt, p.off_ring + kHopBatch * span);
+  return std::max(p.off_bt, p.off_ring + kHopBatch * kHopRowBytes);
 }
 
 int launch_trellis(const LaunchShape& shape, const FwdParams& p, const FwdJob* d_jobs, int njobs,
