@@ -376,24 +376,28 @@ def main():
     # End to end through the host-buffer path of align_submit_batch.
     e2e = None
     if not args.no_e2e:
-        host_lp = [u.cpu().pin_memory() for u in utts]
-        host_out = [(torch.empty(T, dtype=torch.int32).pin_memory(), torch.empty(T, dtype=torch.float32).pin_memory(),
-                     torch.empty(1, dtype=torch.float32).pin_memory(), None) for T in T_of]
-        h2d = sum(x.numel() * 4 for x in host_lp) + sum(t.size * 4 for t in batch.targets)
-        d2h = sum(T * 8 + 4 for T in T_of)
+        # The batch as a user holds it: one packed pinned host tensor of emissions
+        # (utterance i = rows offsets[i]:offsets[i+1]), packed targets, packed outputs.
+        host_lp = batch.lp.cpu().pin_memory()
+        tg_packed = np.concatenate([np.asarray(t, dtype=np.int32) for t in batch.targets])
+        tg_off = np.concatenate([[0], np.cumsum([len(t) for t in batch.targets])]).astype(np.int64)
+        total_T = int(batch.offsets[-1])
+        host_out = (torch.empty(total_T, dtype=torch.int32).pin_memory(),
+                    torch.empty(total_T, dtype=torch.float32).pin_memory(),
+                    torch.empty(n, dtype=torch.float32).pin_memory(), None)
+        h2d = host_lp.numel() * 4 + tg_packed.size * 4
+        d2h = total_T * 8 + n * 4
         ha = align.Aligner(device=dev, batched=True, bp_budget_bytes=budget, max_inflight=max(8192, 2 * n),
                            staging_bytes=min(int(1.3 * (h2d + d2h)) + (64 << 20), 16 << 30))
         autotune.apply(ha)
-        host_items = [(host_lp[i], batch.targets[i], 0, host_out[i]) for i in range(n)]
         e_times = []
         for k in range(2 + max(3, args.steps // 4)):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            rs = ha.submit_batch(host_items, host=True)
+            pr = ha.submit_packed(host_lp, batch.offsets, tg_packed, tg_off, host_out, host=True)
             ha.flush()
-            for r in rs:
-                ha.poll(r)
-                assert r.status == 0, r.status
+            ha.wait_packed(pr)
+            assert (pr.status == 0).all(), pr.status[pr.status != 0][:4]
             if k >= 2:
                 e_times.append(time.perf_counter() - t0)
         ha.close()

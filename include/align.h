@@ -112,10 +112,12 @@ int align_submit(align_ctx *ctx, const float *log_probs, int64_t T, int64_t C,
                  const int32_t *targets, int64_t L, int32_t blank, align_out out,
                  uint64_t *request_id);
 
-/* Same as align_submit, but log_probs and out.* are HOST pointers. The library
-   copies the emissions host->device and the results device->host itself
-   (asynchronously when the host memory is page-locked). The host buffers must
-   stay valid until align_poll reports the request done. */
+/* Same as align_submit, but log_probs and out.* are HOST pointers. When the
+   device can address all of them (page-locked mapped memory, or any host
+   memory on a device that reads the host page tables), one batched copy
+   kernel per batch moves the emissions in and one the results out; otherwise
+   the library copies host->device and device->host with one copy per buffer. The host buffers must stay valid
+   and unmodified until align_poll reports the request done. */
 int align_submit_host(align_ctx *ctx, const float *log_probs, int64_t T, int64_t C,
                       const int32_t *targets, int64_t L, int32_t blank, align_out out,
                       uint64_t *request_id);

@@ -148,7 +148,16 @@ def _check(rc: int, what: str) -> int:
 
 
 def _i32(targets) -> np.ndarray:
+    if isinstance(targets, np.ndarray) and targets.dtype == np.int32 and targets.ndim == 1 and \
+            targets.flags.c_contiguous:
+        return targets
     return np.ascontiguousarray(np.asarray(targets, dtype=np.int32).reshape(-1))
+
+
+# Row layout of AlignRequest (with its AlignOut) for building whole batches at once.
+_REQ_DTYPE = np.dtype([("lp", np.uint64), ("T", np.int64), ("C", np.int64), ("tg", np.uint64), ("L", np.int64),
+                       ("blank", np.int32), ("flags", np.uint32), ("path", np.uint64), ("scores", np.uint64),
+                       ("total", np.uint64), ("states", np.uint64)])
 
 
 # --------------------------------------------------------- same-named calls --
@@ -180,15 +189,21 @@ def align_submit_host(ctx, log_probs_ptr: int, T: int, C: int, targets, blank: i
 
 
 def align_submit_batch(ctx, reqs) -> tuple[list[int], list[int]]:
-    """reqs: sequence of AlignRequest. Returns (request ids, per-request status)."""
+    """reqs: sequence of AlignRequest, or a numpy array of _REQ_DTYPE rows.
+    Returns (request ids, per-request status)."""
     n = len(reqs)
-    arr = (AlignRequest * n)(*reqs)
-    ids = (ctypes.c_uint64 * n)()
-    st = (ctypes.c_int32 * n)()
-    rc = lib().align_submit_batch(ctx, n, arr, ids, st)
-    if rc < 0 and all(x != 0 for x in st):  # a context-level failure
+    if isinstance(reqs, np.ndarray):
+        assert reqs.dtype == _REQ_DTYPE and reqs.flags.c_contiguous
+        arr = reqs.ctypes.data_as(ctypes.POINTER(AlignRequest))
+    else:
+        arr = (AlignRequest * n)(*reqs)
+    ids = np.zeros(n, dtype=np.uint64)
+    st = np.zeros(n, dtype=np.int32)
+    rc = lib().align_submit_batch(ctx, n, arr, ids.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
+                                  st.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
+    if rc < 0 and n and bool(np.all(st != 0)):  # a context-level failure
         raise AlignError(rc, "align_submit_batch")
-    return list(ids), list(st)
+    return ids.tolist(), st.tolist()
 
 
 def align_flush(ctx) -> None:
@@ -289,6 +304,14 @@ class Result:
     status: int = ALIGN_PENDING
 
 
+@dataclass
+class PackedResult:
+    """Requests of one packed batch (utterance i = rows offsets[i]:offsets[i+1])."""
+    request_ids: np.ndarray   # uint64 [n]
+    status: np.ndarray        # int32 [n], ALIGN_PENDING until waited for
+    keep: tuple               # the packed buffers, kept alive until done
+
+
 class Aligner:
     """Owns one context. Device submits take CUDA tensors and return CUDA tensors."""
 
@@ -366,17 +389,29 @@ class Aligner:
     def submit_batch(self, items, host: bool = False) -> list[Result]:
         """items: sequence of (log_probs, targets, blank, out) with out = (path, scores, total, states)
         tensors (device tensors, or host tensors when host=True). One C call for the whole batch."""
-        reqs, keep, results = [], [], []
-        for lp, tg, blank, out in items:
+        n = len(items)
+        reqs = np.zeros(n, dtype=_REQ_DTYPE)
+        cols = {k: [0] * n for k in ("lp", "T", "C", "tg", "L", "blank", "path", "scores", "total", "states")}
+        keep, results = [], []
+        for i, (lp, tg, blank, out) in enumerate(items):
             tg = _i32(tg)
             path, scores, total, states = out
             T, C = lp.shape
-            o = AlignOut(path.data_ptr(), scores.data_ptr(), total.data_ptr(),
-                         states.data_ptr() if states is not None else None)
-            reqs.append(AlignRequest(lp.data_ptr(), T, C, tg.ctypes.data, tg.size, blank,
-                                     ALIGN_REQ_HOST if host else 0, o))
+            cols["lp"][i] = lp.data_ptr()
+            cols["T"][i] = T
+            cols["C"][i] = C
+            cols["tg"][i] = tg.ctypes.data
+            cols["L"][i] = tg.size
+            cols["blank"][i] = blank
+            cols["path"][i] = path.data_ptr()
+            cols["scores"][i] = scores.data_ptr()
+            cols["total"][i] = total.data_ptr()
+            cols["states"][i] = states.data_ptr() if states is not None else 0
             keep.append((lp, tg))
             results.append(Result(0, path, scores, total, states))
+        for k, v in cols.items():
+            reqs[k] = v
+        reqs["flags"] = ALIGN_REQ_HOST if host else 0
         ids, st = align_submit_batch(self.ctx, reqs)
         for r, rid, code, k in zip(results, ids, st, keep):
             if code < 0:
@@ -392,7 +427,7 @@ class Aligner:
         rc, st = align_poll(self.ctx, res.request_id, timeout_ms)
         if rc == ALIGN_OK:
             res.status = st
-            self._live.pop(res.request_id, None)
+            self._finish(res.request_id, st)
             return True
         return False
 
@@ -400,12 +435,111 @@ class Aligner:
         """Results that finished since the last call (status filled in), without waiting."""
         out = []
         for rid, st in align_poll_done(self.ctx, max_n):
-            entry = self._live.pop(rid, None)
-            if entry is not None:
-                res = entry[1]
-                res.status = st
+            res = self._finish(rid, st)
+            if res is not None:
                 out.append(res)
         return out
+
+    def submit_packed(self, log_probs, offsets, targets, target_offsets, out, blank: int = 0,
+                      host: bool = False) -> PackedResult:
+        """A ragged batch in packed form, marshalled without a per-utterance
+        Python loop. log_probs: float32 [sum T, C] (utterance i = rows
+        offsets[i]:offsets[i+1]); targets: int32 [sum L] (utterance i =
+        targets[target_offsets[i]:target_offsets[i+1]]), host memory;
+        out = (path int32 [sum T], scores float32 [sum T], total float32 [n],
+        states int32 [sum T] or None) in the same packing. Device tensors, or
+        host tensors when host=True. One C call for the whole batch."""
+        offsets = np.asarray(offsets, dtype=np.int64)
+        target_offsets = np.asarray(target_offsets, dtype=np.int64)
+        tg = _i32(targets)
+        n = offsets.size - 1
+        path, scores, total, states = out
+        T, C = log_probs.shape
+        if log_probs.dtype != self.torch.float32 or not log_probs.is_contiguous():
+            raise ValueError("log_probs must be a contiguous float32 [sum T, C] tensor")
+        if offsets[-1] != T or target_offsets.size != n + 1 or target_offsets[-1] != tg.size or total.numel() < n:
+            raise ValueError("offsets / target_offsets do not match the packed tensors")
+        f0 = offsets[:-1].astype(np.uint64)
+        reqs = np.zeros(n, dtype=_REQ_DTYPE)
+        reqs["lp"] = np.uint64(log_probs.data_ptr()) + f0 * np.uint64(4 * C)
+        reqs["T"] = np.diff(offsets)
+        reqs["C"] = C
+        reqs["tg"] = np.uint64(tg.ctypes.data) + target_offsets[:-1].astype(np.uint64) * np.uint64(4)
+        reqs["L"] = np.diff(target_offsets)
+        reqs["blank"] = blank
+        reqs["flags"] = ALIGN_REQ_HOST if host else 0
+        reqs["path"] = np.uint64(path.data_ptr()) + f0 * np.uint64(4)
+        reqs["scores"] = np.uint64(scores.data_ptr()) + f0 * np.uint64(4)
+        reqs["total"] = np.uint64(total.data_ptr()) + np.arange(n, dtype=np.uint64) * np.uint64(4)
+        if states is not None:
+            reqs["states"] = np.uint64(states.data_ptr()) + f0 * np.uint64(4)
+        ids, st = align_submit_batch(self.ctx, reqs)
+        ids = np.asarray(ids, dtype=np.uint64)
+        st = np.asarray(st, dtype=np.int32)
+        bad = st < 0
+        if bad.any():
+            raise AlignError(int(st[bad][0]), "align_submit_batch")
+        res = PackedResult(ids, np.full(n, ALIGN_PENDING, dtype=np.int32), (log_probs, tg, out))
+        for i, rid in enumerate(ids.tolist()):
+            self._live[rid] = (None, (res, i))
+        return res
+
+    def _waiter(self):
+        """A stream of this context's device used only to wait for batches."""
+        if getattr(self, "_wait_stream", None) is None:
+            self._wait_stream = self.torch.cuda.Stream(self.device)
+        return self._wait_stream
+
+    def _finish(self, rid: int, code: int):
+        """Record a finished request; returns its Result (None for a packed one)."""
+        entry = self._live.pop(rid, None)
+        if entry is None:
+            return None
+        target = entry[1]
+        if isinstance(target, tuple):
+            target[0].status[target[1]] = code
+            return None
+        target.status = code
+        return target
+
+    def wait_packed(self, res: PackedResult) -> None:
+        """Block until every request of a packed batch is done; fills res.status."""
+        if res.request_ids.size <= 16:  # few requests: a blocking poll each
+            for i, rid in enumerate(res.request_ids.tolist()):
+                if res.status[i] == ALIGN_PENDING:
+                    rc, code = align_poll(self.ctx, rid, -1)
+                    if rc == ALIGN_OK:
+                        self._finish(rid, code)
+            if not (res.status == ALIGN_PENDING).any():
+                return
+        st = self._waiter()
+        self.join(st)
+        st.synchronize()
+        while (res.status == ALIGN_PENDING).any():
+            got = align_poll_done(self.ctx, max(4096, 2 * int((res.status == ALIGN_PENDING).sum())))
+            for rid, code in got:
+                self._finish(rid, code)
+            if not got:
+                self.join(st)
+                st.synchronize()
+
+    def wait(self, results) -> None:
+        """Block until every result in `results` is done: one device-side join
+        and synchronisation, then one status sweep (align_poll_done) instead of
+        one align_poll per request."""
+        pending = {r.request_id: r for r in results if r.request_id in self._live}
+        if not pending:
+            return
+        st = self._waiter()
+        self.join(st)
+        st.synchronize()
+        while pending:
+            for r in self.poll_done(max_n=max(4096, 2 * len(pending))):
+                pending.pop(r.request_id, None)
+            if pending:  # finished on the GPU but not yet reaped: poll the rest
+                for rid in list(pending):
+                    if self.poll(pending[rid], 0):
+                        pending.pop(rid)
 
     def align(self, log_probs, targets, blank: int = 0, want_states: bool = False) -> Result:
         res = self.submit(log_probs, targets, blank, want_states)

@@ -132,6 +132,12 @@ struct Request {
   ReqState state = ReqState::Queued;
   const float* lp = nullptr;  // device emissions (or host, when host_io)
   bool host_io = false;
+  // host_io: device-addressable aliases of the host buffers (mapped pinned
+  // memory, or system memory the device reaches through the host page
+  // tables); then one batched copy kernel moves them instead of one
+  // cudaMemcpyAsync per buffer. Null when any buffer is not addressable.
+  const void* lp_alias = nullptr;
+  align_out out_alias{};
   align_out out{};            // caller outputs (device or host)
   int64_t T = 0, C = 0, L = 0;
   int32_t blank = 0;
@@ -201,6 +207,7 @@ struct align_ctx {
   uint64_t next_id = 1;
   int next_batch = 1;
 
+  bool host_ats = false;  // the device reads pageable host memory through the host page tables
   TuneTable tune;     // latency shapes (also the defaults)
   TuneTable tune_tp;  // throughput shapes (nbuckets == 0: not set)
   int num_sms = 0;
@@ -211,6 +218,21 @@ struct align_ctx {
 namespace {
 
 uint64_t inflight_count(const align_ctx* ctx) { return ctx->reqs.size(); }
+
+// A device-addressable alias of host memory, or nullptr.
+void* device_alias(const align_ctx* ctx, const void* p) {
+  if (!p) return nullptr;
+  // The device reads any host address through the host page tables: no query.
+  if (ctx->host_ats) return const_cast<void*>(p);
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return nullptr;
+  }
+  if (a.type == cudaMemoryTypeHost && a.devicePointer) return a.devicePointer;
+  if (a.type == cudaMemoryTypeManaged) return const_cast<void*>(p);
+  return nullptr;
+}
 
 
 cudaEvent_t take_event(align_ctx* ctx) {
@@ -312,8 +334,12 @@ int launch_queued(align_ctx* ctx) {
   while (!ctx->queued.empty()) {
     const uint64_t id = ctx->queued.front();
     Request& r = ctx->reqs.at(id);
-    const uint64_t m = (1 + static_cast<uint64_t>(r.plan.nck)) * sizeof(FwdJob) + 64 +
-                       static_cast<uint64_t>(r.L) * 4 + 16;
+    uint64_t m = (1 + static_cast<uint64_t>(r.plan.nck)) * sizeof(FwdJob) + 64 +
+                 static_cast<uint64_t>(r.L) * 4 + 16;
+    if (r.host_io && r.lp_alias) {  // batched-copy chunks of this request
+      const uint64_t T = static_cast<uint64_t>(r.T);
+      m += (T * static_cast<uint64_t>(r.C) * 4 / kCopyChunk + 3 * (T * 4 / kCopyChunk) + 5) * sizeof(CopyChunk);
+    }
     if (meta_est + m + 4 * kAlign > meta_room) break;  // the rest waits for the next batch
     ctx->queued.pop_front();
     // Admission: backpointer / checkpoint footprint, plus staging for host I/O.
@@ -377,10 +403,21 @@ int launch_queued(align_ctx* ctx) {
   }
   uint64_t tgt_words = 0;
   for (auto* r : take) tgt_words += round_up(static_cast<uint64_t>(std::max<int64_t>(r->L, 1)), 4);
+  // Batched host copies: chunks of the emissions in, of the outputs out.
+  const auto nch = [](uint64_t bytes) { return bytes ? (bytes + kCopyChunk - 1) / kCopyChunk : 0; };
+  uint64_t n_h2d = 0, n_d2h = 0;
+  for (auto* r : take) {
+    if (!r->host_io || !r->lp_alias) continue;
+    const uint64_t T = static_cast<uint64_t>(r->T);
+    n_h2d += nch(T * static_cast<uint64_t>(r->C) * 4);
+    n_d2h += 2 * nch(T * 4) + 1 + (r->out.states ? nch(T * 4) : 0);
+  }
   const uint64_t off_jobs = 0;
   const uint64_t off_metas = round_up(njobs * sizeof(FwdJob), kAlign);
   const uint64_t off_tgts = round_up(off_metas + take.size() * sizeof(MetaBlock), kAlign);
-  const uint64_t up_bytes = round_up(off_tgts + tgt_words * 4, kAlign);
+  const uint64_t off_h2d = round_up(off_tgts + tgt_words * 4, kAlign);
+  const uint64_t off_d2h = round_up(off_h2d + n_h2d * sizeof(CopyChunk), kAlign);
+  const uint64_t up_bytes = round_up(off_d2h + n_d2h * sizeof(CopyChunk), kAlign);
   const uint64_t off_status = up_bytes;  // pinned only: metadata download (status of every request)
   const uint64_t pin_bytes = up_bytes + round_up(take.size() * sizeof(MetaBlock), kAlign);
 
@@ -494,6 +531,17 @@ int launch_queued(align_ctx* ctx) {
   std::vector<const int32_t*> req_tgt(take.size());
   std::vector<const float*> req_lp(take.size());
   std::vector<align_out> req_out(take.size());
+  CopyChunk* hh2d = reinterpret_cast<CopyChunk*>(h + off_h2d);
+  CopyChunk* hd2h = reinterpret_cast<CopyChunk*>(h + off_d2h);
+  const CopyChunk* dh2d = reinterpret_cast<const CopyChunk*>(d + off_h2d);
+  const CopyChunk* dd2h = reinterpret_cast<const CopyChunk*>(d + off_d2h);
+  size_t ih2d = 0, id2h = 0;
+  const auto add_chunks = [](CopyChunk* list, size_t& n, const void* src, void* dst, uint64_t bytes) {
+    for (uint64_t o = 0; o < bytes; o += kCopyChunk) {
+      list[n++] = CopyChunk{static_cast<const char*>(src) + o, static_cast<char*>(dst) + o,
+                            std::min(kCopyChunk, bytes - o), 0};
+    }
+  };
   uint64_t tw = 0;
   for (size_t i = 0; i < take.size(); ++i) {
     Request& r = *take[i];
@@ -516,6 +564,14 @@ int launch_queued(align_ctx* ctx) {
       req_out[i].scores = reinterpret_cast<float*>(sbase + hs.scores);
       req_out[i].total = reinterpret_cast<float*>(sbase + hs.total);
       req_out[i].states = r.out.states ? reinterpret_cast<int32_t*>(sbase + hs.states) : nullptr;
+      if (r.lp_alias) {
+        const uint64_t T = static_cast<uint64_t>(r.T);
+        add_chunks(hh2d, ih2d, r.lp_alias, const_cast<float*>(req_lp[i]), T * static_cast<uint64_t>(r.C) * 4);
+        add_chunks(hd2h, id2h, req_out[i].path, r.out_alias.path, T * 4);
+        add_chunks(hd2h, id2h, req_out[i].scores, r.out_alias.scores, T * 4);
+        add_chunks(hd2h, id2h, req_out[i].total, r.out_alias.total, 4);
+        if (r.out.states) add_chunks(hd2h, id2h, req_out[i].states, r.out_alias.states, T * 4);
+      }
     } else {
       req_lp[i] = r.lp;
       req_out[i] = r.out;
@@ -672,10 +728,19 @@ int launch_queued(align_ctx* ctx) {
   CU(cudaMemcpyAsync(d, h, up_copy, cudaMemcpyHostToDevice, s0));
   for (size_t i = 0; i < take.size(); ++i) {
     Request& r = *take[i];
-    if (r.host_io) {
+    if (r.host_io && !r.lp_alias) {
       CU(cudaMemcpyAsync(const_cast<float*>(req_lp[i]), r.lp, static_cast<size_t>(r.T * r.C) * 4,
                          cudaMemcpyHostToDevice, s0));
     }
+  }
+
+  if (ih2d) {
+    const cudaError_t e = static_cast<cudaError_t>(launch_copy_chunks(dh2d, static_cast<int>(ih2d), ctx->num_sms, s0));
+    if (e != cudaSuccess) {
+      set_error("copy_chunks", e);
+      return ALIGN_E_CUDA;
+    }
+    ++nkernels;
   }
   cudaEvent_t ready = take_event(ctx);
   b.events.push_back(ready);
@@ -718,9 +783,17 @@ int launch_queued(align_ctx* ctx) {
     CU(cudaStreamWaitEvent(s0, j, 0));
   }
   CU(cudaMemcpyAsync(b.h_meta, dmeta, take.size() * sizeof(MetaBlock), cudaMemcpyDeviceToHost, s0));
+  if (id2h) {
+    const cudaError_t e = static_cast<cudaError_t>(launch_copy_chunks(dd2h, static_cast<int>(id2h), ctx->num_sms, s0));
+    if (e != cudaSuccess) {
+      set_error("copy_chunks", e);
+      return ALIGN_E_CUDA;
+    }
+    ++nkernels;
+  }
   for (size_t i = 0; i < take.size(); ++i) {
     Request& r = *take[i];
-    if (!r.host_io) continue;
+    if (!r.host_io || r.lp_alias) continue;
     const size_t T = static_cast<size_t>(r.T);
     CU(cudaMemcpyAsync(r.out.path, req_out[i].path, T * 4, cudaMemcpyDeviceToHost, s0));
     CU(cudaMemcpyAsync(r.out.scores, req_out[i].scores, T * 4, cudaMemcpyDeviceToHost, s0));
@@ -803,8 +876,20 @@ int submit_common(align_ctx* ctx, const float* lp, int64_t T, int64_t C, const i
   Plan p{};
   rc = make_plan(ctx->tune, T, C, L, ctx->bp_arena.cap(), (ctx->flags & ALIGN_F_FORCE_CHECKPOINT) != 0, &p);
   if (rc != ALIGN_OK) return rc;
-  if (host_io && host_stage_bytes(T, C) > ctx->stage_arena.cap()) return ALIGN_E_TOO_LARGE;
   Request r;
+  if (host_io) {
+    align_out al{};
+    const void* la = device_alias(ctx, lp);
+    al.path = static_cast<int32_t*>(device_alias(ctx, out.path));
+    al.scores = static_cast<float*>(device_alias(ctx, out.scores));
+    al.total = static_cast<float*>(device_alias(ctx, out.total));
+    al.states = out.states ? static_cast<int32_t*>(device_alias(ctx, out.states)) : nullptr;
+    if (la && al.path && al.scores && al.total && (!out.states || al.states)) {
+      r.lp_alias = la;
+      r.out_alias = al;
+    }
+    if (host_stage_bytes(T, C) > ctx->stage_arena.cap()) return ALIGN_E_TOO_LARGE;
+  }
   r.id = ctx->next_id++;
   r.lp = lp;
   r.host_io = host_io;
@@ -846,6 +931,9 @@ int align_create(align_ctx** out, const align_config* cfg_in) {
   ctx->tune = default_tune_table();
   int coop = 0;
   CU(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, cfg.device));
+  int ats = 0;
+  CU(cudaDeviceGetAttribute(&ats, cudaDevAttrPageableMemoryAccessUsesHostPageTables, cfg.device));
+  ctx->host_ats = ats != 0;
   // Grid teams for latency-planned batches only: a team holds whole SMs, and
   // batches that oversubscribe the GPU are better served by clusters.
   if (coop && !(cfg.flags & ALIGN_F_NO_GRID_TEAMS)) ctx->tune.max_grid = ctx->num_sms;

@@ -142,4 +142,15 @@ int launch_frame_probe(int warps, int ncta, int frames, uint64_t limit_ns, uint6
 // Largest dynamic shared memory the kernel for this shape may use.
 int max_smem_optin(int device);
 
+// One piece of a batched host <-> device copy (copy_kernels.cu): both
+// addresses must be addressable by the device.
+struct alignas(16) CopyChunk {
+  const void* src;
+  void* dst;
+  uint64_t bytes;
+  uint64_t pad;
+};
+constexpr uint64_t kCopyChunk = 256ull << 10;  // bytes per chunk at most
+int launch_copy_chunks(const CopyChunk* d_chunks, int n, int sm_count, void* stream);
+
 }  // namespace gb300_align

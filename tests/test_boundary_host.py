@@ -119,3 +119,17 @@ def test_product_has_no_cpu_fallback(monkeypatch):
     monkeypatch.setattr(align, "LIB_PATH", "/nonexistent/libalign.so")
     with pytest.raises(ImportError):
         align.lib()
+
+
+def test_request_row_layout_matches_abi():
+    """The numpy row layout used to build whole batches equals align_request."""
+    import ctypes
+    assert align._REQ_DTYPE.itemsize == ctypes.sizeof(align.AlignRequest)
+    out_off = align.AlignRequest.out.offset
+    want = {"lp": align.AlignRequest.log_probs.offset, "T": align.AlignRequest.T.offset,
+            "C": align.AlignRequest.C.offset, "tg": align.AlignRequest.targets.offset,
+            "L": align.AlignRequest.L.offset, "blank": align.AlignRequest.blank.offset,
+            "flags": align.AlignRequest.flags.offset, "path": out_off + align.AlignOut.path.offset,
+            "scores": out_off + align.AlignOut.scores.offset, "total": out_off + align.AlignOut.total.offset,
+            "states": out_off + align.AlignOut.states.offset}
+    assert {k: align._REQ_DTYPE.fields[k][1] for k in want} == want

@@ -202,6 +202,39 @@ def test_host_io(al):
     compare(res, u.lp.numpy(), u.targets, 0, "host")
 
 
+@pytest.mark.parametrize("pinned", [True, False])
+def test_host_batch_copies(pinned):
+    """Host-buffer requests of a batch (pinned, or pageable where the device
+    reads host page tables; otherwise per-buffer copies) move in and out with
+    batched copy kernels, including buffers larger than one copy chunk and
+    unaligned row sizes; results equal the oracle."""
+    build.build()
+    shapes = [(300, 32, 70, 1), (9000, 32, 2000, 2), (257, 29, 60, 3), (40, 5, 9, 4), (2100, 500, 500, 5)]
+    us = [synth.make_utterance(s, T, C, L, repeat_frac=0.1) for (T, C, L, s) in shapes]
+    al = align.Aligner(device=0, batched=True, bp_budget_bytes=4 << 30)
+    try:
+        items, outs = [], []
+        for u in us:
+            T = u.lp.shape[0]
+            lp = u.lp.pin_memory() if pinned else u.lp.clone()
+            o = tuple(torch.empty(n, dtype=dt, pin_memory=pinned) for n, dt in
+                      ((T, torch.int32), (T, torch.float32), (1, torch.float32), (T, torch.int32)))
+            outs.append(o)
+            items.append((lp, u.targets, 0, o))
+        rs = al.submit_batch(items, host=True)
+        al.flush()
+        for r in rs:
+            al.poll(r)
+        for u, o, r in zip(us, outs, rs):
+            ref = oracle.viterbi_f32(u.lp.numpy(), np.asarray(u.targets, np.int32), 0)
+            assert r.status == ref["status"] == 0
+            assert np.array_equal(o[0].numpy(), ref["path"]) and np.array_equal(o[3].numpy(), ref["states"])
+            assert o[1].numpy().tobytes() == ref["scores"].tobytes()
+            assert np.float32(o[2].numpy()[0]).tobytes() == np.float32(ref["total"]).tobytes()
+    finally:
+        al.close()
+
+
 def test_config2_batched_equals_plain_and_oracle():
     build.build()
     b = synth.make_batch(synth.specs(2), device="cuda")
@@ -361,6 +394,40 @@ def test_two_grid_teams_and_small_requests_in_one_batch():
         for u, o in zip(us, outs):
             ref = one.align(u.lp.cuda(), u.targets, 0)
             assert torch.equal(o[0], ref.path) and torch.equal(o[1].view(torch.int32), ref.scores.view(torch.int32))
+    finally:
+        al.close()
+        one.close()
+
+
+@pytest.mark.parametrize("host", [False, True])
+def test_submit_packed_equals_single_requests(host):
+    """A packed ragged batch (one emission tensor, packed targets and outputs)
+    gives the same results as submitting its utterances one by one."""
+    build.build()
+    specs = synth.specs(4, C=32, n=40)
+    b = synth.make_batch(specs, device="cpu" if host else "cuda")
+    n = len(b)
+    tg = np.concatenate([np.asarray(t, np.int32) for t in b.targets])
+    tg_off = np.concatenate([[0], np.cumsum([len(t) for t in b.targets])])
+    TT = int(b.offsets[-1])
+    kw = {"pin_memory": True} if host else {"device": "cuda"}
+    out = (torch.empty(TT, dtype=torch.int32, **kw), torch.empty(TT, dtype=torch.float32, **kw),
+           torch.empty(n, dtype=torch.float32, **kw), torch.empty(TT, dtype=torch.int32, **kw))
+    lp = b.lp.pin_memory() if host else b.lp
+    al = align.Aligner(device=0, batched=True, bp_budget_bytes=4 << 30)
+    one = align.Aligner(device=0, bp_budget_bytes=4 << 30)
+    try:
+        pr = al.submit_packed(lp, b.offsets, tg, tg_off, out, host=host)
+        al.flush()
+        al.wait_packed(pr)
+        assert (pr.status == 0).all()
+        for i in range(n):
+            f0, f1 = int(b.offsets[i]), int(b.offsets[i + 1])
+            r = one.align(b.utt(i).cuda(), b.targets[i], 0, want_states=True)
+            assert torch.equal(out[0][f0:f1].cpu(), r.path.cpu())
+            assert torch.equal(out[3][f0:f1].cpu(), r.states.cpu())
+            assert torch.equal(out[1][f0:f1].cpu().view(torch.int32), r.scores.cpu().view(torch.int32))
+            assert out[2][i].cpu().view(torch.int32).item() == r.total.cpu().view(torch.int32).item()
     finally:
         al.close()
         one.close()
