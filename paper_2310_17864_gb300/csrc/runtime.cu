@@ -564,14 +564,6 @@ int launch_queued(align_ctx* ctx) {
       req_out[i].scores = reinterpret_cast<float*>(sbase + hs.scores);
       req_out[i].total = reinterpret_cast<float*>(sbase + hs.total);
       req_out[i].states = r.out.states ? reinterpret_cast<int32_t*>(sbase + hs.states) : nullptr;
-      if (r.lp_alias) {
-        const uint64_t T = static_cast<uint64_t>(r.T);
-        add_chunks(hh2d, ih2d, r.lp_alias, const_cast<float*>(req_lp[i]), T * static_cast<uint64_t>(r.C) * 4);
-        add_chunks(hd2h, id2h, req_out[i].path, r.out_alias.path, T * 4);
-        add_chunks(hd2h, id2h, req_out[i].scores, r.out_alias.scores, T * 4);
-        add_chunks(hd2h, id2h, req_out[i].total, r.out_alias.total, 4);
-        if (r.out.states) add_chunks(hd2h, id2h, req_out[i].states, r.out_alias.states, T * 4);
-      }
     } else {
       req_lp[i] = r.lp;
       req_out[i] = r.out;
@@ -601,10 +593,29 @@ int launch_queued(align_ctx* ctx) {
 
   // Fill descriptors: shape groups first (contiguous ranges), then the
   // checkpointed sequences.
+  // Copy chunks of a launch's host-buffer requests: [first, first + count) of
+  // the emission (in) and output (out) lists, moved on the launch's own stream
+  // so that copies of one group overlap the kernels of others.
+  struct CopyRange {
+    size_t in_first = 0, in_count = 0, out_first = 0, out_count = 0;
+  };
+  const auto add_request_chunks = [&](size_t i, CopyRange& cr) {
+    const Request& r = *take[i];
+    if (!r.host_io || !r.lp_alias) return;
+    const uint64_t T = static_cast<uint64_t>(r.T);
+    add_chunks(hh2d, ih2d, r.lp_alias, const_cast<float*>(req_lp[i]), T * static_cast<uint64_t>(r.C) * 4);
+    add_chunks(hd2h, id2h, req_out[i].path, r.out_alias.path, T * 4);
+    add_chunks(hd2h, id2h, req_out[i].scores, r.out_alias.scores, T * 4);
+    add_chunks(hd2h, id2h, req_out[i].total, r.out_alias.total, 4);
+    if (r.out.states) add_chunks(hd2h, id2h, req_out[i].states, r.out_alias.states, T * 4);
+    cr.in_count = ih2d - cr.in_first;
+    cr.out_count = id2h - cr.out_first;
+  };
   struct GroupLaunch {
     LaunchShape shape;
     int F;
     size_t first, count;
+    CopyRange cr;
     int64_t t_max;  // longest job of the group (frames): its chain sets the launch's duration
   };
   std::vector<GroupLaunch> glaunch;
@@ -613,6 +624,7 @@ int launch_queued(align_ctx* ctx) {
   struct CkLaunch {
     size_t req, first, count;
     uint64_t* xlink;  // grid team links (zeroed before every launch), or nullptr
+    CopyRange cr;
   };
   std::vector<CkLaunch> cklaunch;
   size_t jn = 0;
@@ -623,7 +635,10 @@ int launch_queued(align_ctx* ctx) {
     gl.first = jn;
     gl.count = kv.second.size();
     gl.t_max = 0;
+    gl.cr.in_first = ih2d;
+    gl.cr.out_first = id2h;
     for (int i : kv.second) {
+      add_request_chunks(static_cast<size_t>(i), gl.cr);
       const Request& r = *take[static_cast<size_t>(i)];
       gl.t_max = std::max(gl.t_max, r.T);
       FwdJob j = base_job(static_cast<size_t>(i));
@@ -647,7 +662,10 @@ int launch_queued(align_ctx* ctx) {
     const Plan& p = r.plan;
     if (!p.checkpointed && !p.shape.grid) continue;
     uint64_t* xl = p.shape.grid ? reinterpret_cast<uint64_t*>(ctx->d_bp + r.bp.off + plan_x_off(p)) : nullptr;
-    CkLaunch cl{i, jn, p.checkpointed ? static_cast<size_t>(p.nck) + 1 : 1, xl};
+    CkLaunch cl{i, jn, p.checkpointed ? static_cast<size_t>(p.nck) + 1 : 1, xl, CopyRange{}};
+    cl.cr.in_first = ih2d;
+    cl.cr.out_first = id2h;
+    add_request_chunks(i, cl.cr);
     if (!p.checkpointed) {  // grid team, full backpointers
       FwdJob j = base_job(i);
       j.bp = reinterpret_cast<uint32_t*>(ctx->d_bp + r.bp.off);
@@ -734,14 +752,24 @@ int launch_queued(align_ctx* ctx) {
     }
   }
 
-  if (ih2d) {
-    const cudaError_t e = static_cast<cudaError_t>(launch_copy_chunks(dh2d, static_cast<int>(ih2d), ctx->num_sms, s0));
+  // Copy kernels of one launch's host-buffer requests, in or out, on its stream.
+  const auto copy_range = [&](const CopyChunk* list, size_t first, size_t count, cudaStream_t s) -> int {
+    if (!count) return ALIGN_OK;
+    const cudaError_t e =
+        static_cast<cudaError_t>(launch_copy_chunks(list + first, static_cast<int>(count), ctx->num_sms, s));
     if (e != cudaSuccess) {
       set_error("copy_chunks", e);
       return ALIGN_E_CUDA;
     }
     ++nkernels;
-  }
+    return ALIGN_OK;
+  };
+  // Large host batches move each launch's buffers on its own stream (copies
+  // overlap other launches' kernels); small ones in one copy kernel each way.
+  uint64_t in_bytes = 0;
+  for (size_t k = 0; k < ih2d; ++k) in_bytes += hh2d[k].bytes;
+  const bool split_copies = in_bytes > (64ull << 20);
+  if (!split_copies && copy_range(dh2d, 0, ih2d, s0) != ALIGN_OK) return ALIGN_E_CUDA;
   cudaEvent_t ready = take_event(ctx);
   b.events.push_back(ready);
   CU(cudaEventRecord(ready, s0));
@@ -752,6 +780,7 @@ int launch_queued(align_ctx* ctx) {
     if (s != s0) CU(cudaStreamWaitEvent(s, ready, 0));
     const Plan& p = take[cl.req]->plan;
     const FwdParams P = plan_params(p.shape, static_cast<int>(take[cl.req]->C), p.frames_per_stage, ctx->wait_limit_ns);
+    if (split_copies && copy_range(dh2d, cl.cr.in_first, cl.cr.in_count, s) != ALIGN_OK) return ALIGN_E_CUDA;
     for (size_t k = 0; k < cl.count; ++k) {
       if (cl.xlink) CU(cudaMemsetAsync(cl.xlink, 0, p.x_bytes, s));
       cudaError_t e = static_cast<cudaError_t>(launch_trellis(p.shape, P, djobs + cl.first + k, 1, s));
@@ -761,18 +790,21 @@ int launch_queued(align_ctx* ctx) {
       }
       ++nkernels;
     }
+    if (split_copies && copy_range(dd2h, cl.cr.out_first, cl.cr.out_count, s) != ALIGN_OK) return ALIGN_E_CUDA;
   }
   for (const GroupLaunch& gl : glaunch) {
     cudaStream_t s = used[lane_i++ % nwork];
     if (s != s0) CU(cudaStreamWaitEvent(s, ready, 0));
     const int C = hjobs[gl.first].C;
     const FwdParams P = plan_params(gl.shape, C, gl.F, ctx->wait_limit_ns);
+    if (split_copies && copy_range(dh2d, gl.cr.in_first, gl.cr.in_count, s) != ALIGN_OK) return ALIGN_E_CUDA;
     cudaError_t e = static_cast<cudaError_t>(launch_trellis(gl.shape, P, djobs + gl.first, static_cast<int>(gl.count), s));
     if (e != cudaSuccess) {
       set_error("launch_trellis", e);
       return ALIGN_E_CUDA;
     }
     ++nkernels;
+    if (split_copies && copy_range(dd2h, gl.cr.out_first, gl.cr.out_count, s) != ALIGN_OK) return ALIGN_E_CUDA;
   }
   // Join, download statuses and host outputs, record completion.
   for (cudaStream_t s : used) {
@@ -782,15 +814,9 @@ int launch_queued(align_ctx* ctx) {
     CU(cudaEventRecord(j, s));
     CU(cudaStreamWaitEvent(s0, j, 0));
   }
+  if (!split_copies && copy_range(dd2h, 0, id2h, s0) != ALIGN_OK) return ALIGN_E_CUDA;
   CU(cudaMemcpyAsync(b.h_meta, dmeta, take.size() * sizeof(MetaBlock), cudaMemcpyDeviceToHost, s0));
-  if (id2h) {
-    const cudaError_t e = static_cast<cudaError_t>(launch_copy_chunks(dd2h, static_cast<int>(id2h), ctx->num_sms, s0));
-    if (e != cudaSuccess) {
-      set_error("copy_chunks", e);
-      return ALIGN_E_CUDA;
-    }
-    ++nkernels;
-  }
+
   for (size_t i = 0; i < take.size(); ++i) {
     Request& r = *take[i];
     if (!r.host_io || r.lp_alias) continue;

@@ -399,6 +399,36 @@ def test_two_grid_teams_and_small_requests_in_one_batch():
         one.close()
 
 
+def test_host_batch_large_moves_per_launch():
+    """A host batch above 64 MB moves each launch's buffers on its own stream
+    (copies overlapping other launches); results equal the device path."""
+    build.build()
+    specs = [synth.Spec(4000 + 37 * i, 300, 700 + 11 * i, 0.1, synth.sub_seed(777, i)) for i in range(16)]
+    b = synth.make_batch(specs, device="cpu")
+    assert b.lp.numel() * 4 > (64 << 20)
+    n = len(b)
+    tg = np.concatenate([np.asarray(t, np.int32) for t in b.targets])
+    tg_off = np.concatenate([[0], np.cumsum([len(t) for t in b.targets])])
+    TT = int(b.offsets[-1])
+    out = (torch.empty(TT, dtype=torch.int32).pin_memory(), torch.empty(TT, dtype=torch.float32).pin_memory(),
+           torch.empty(n, dtype=torch.float32).pin_memory(), None)
+    al = align.Aligner(device=0, batched=True, bp_budget_bytes=4 << 30, staging_bytes=512 << 20)
+    one = align.Aligner(device=0, bp_budget_bytes=4 << 30)
+    try:
+        pr = al.submit_packed(b.lp.pin_memory(), b.offsets, tg, tg_off, out, host=True)
+        al.flush()
+        al.wait_packed(pr)
+        assert (pr.status == 0).all()
+        for i in range(n):
+            f0, f1 = int(b.offsets[i]), int(b.offsets[i + 1])
+            r = one.align(b.utt(i).cuda(), b.targets[i], 0)
+            assert torch.equal(out[0][f0:f1], r.path.cpu())
+            assert torch.equal(out[1][f0:f1].view(torch.int32), r.scores.cpu().view(torch.int32))
+    finally:
+        al.close()
+        one.close()
+
+
 @pytest.mark.parametrize("host", [False, True])
 def test_submit_packed_equals_single_requests(host):
     """A packed ragged batch (one emission tensor, packed targets and outputs)
