@@ -61,6 +61,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="batch64", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-spans", action="store_true", help="skip the token-span leg")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the CPU oracle baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
@@ -347,6 +348,41 @@ def main():
         dist.barrier()
     value = world * cells / (ms / 1e3)
 
+    # Token spans (per transcript token: start, end, mean score) of this batch's
+    # alignments: one packed call, timed with events on its stream.
+    spans_line = None
+    if not args.no_spans:
+        sp_out = [(o[0], o[1], o[2], torch.empty(T, dtype=torch.int32, device=dev)) for o, T in zip(outs, T_of)]
+        rs = al.submit_batch([(utts[i], batch.targets[i], 0, sp_out[i]) for i in range(n)])
+        al.flush()
+        al.wait(rs)
+        assert all(r.status == 0 for r in rs)
+        st_all = torch.cat([o[3] for o in sp_out])
+        sc_all = torch.cat([o[1] for o in sp_out])
+        tg_off = np.concatenate([[0], np.cumsum(L_of)]).astype(np.int64)
+        fo_d = torch.as_tensor(np.asarray(batch.offsets, dtype=np.int64), device=dev)
+        to_d = torch.as_tensor(tg_off, device=dev)
+        totals = (int(batch.offsets[-1]), int(tg_off[-1]))
+        sp_times = []
+        with torch.cuda.stream(stream):
+            for k in range(3 + args.steps):
+                flush_buf.fill_(1)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                align.token_spans(st_all, sc_all, fo_d, to_d, stream=stream, totals=totals)
+                e1.record(stream)
+                e1.synchronize()
+                if k >= 3:
+                    sp_times.append(e0.elapsed_time(e1))
+        sp_ms = statistics.mean(sp_times)
+        n_tok = int(tg_off[-1])
+        sp_bytes = int(st_all.numel()) * 8 + n_tok * 12  # states + scores read, start/end/score written
+        spans_line = {"ms": sp_ms, "tokens": n_tok, "frames": int(st_all.numel()),
+                      "tokens_per_s": n_tok / (sp_ms / 1e3), "alg_bytes": sp_bytes,
+                      "gbs": sp_bytes / (sp_ms / 1e3) / 1e9, "launches": 2,
+                      "note": "two memsets and two kernels on device-resident offsets; L2 flushed before each"}
+
     # Plain: one synchronous submit + poll per utterance (at most 256 utterances).
     plain = None
     if not args.no_plain:
@@ -477,6 +513,7 @@ def main():
         "gpu_launches": int(launches),
         "roofline": rl,
         "serving": serving,
+        "token_spans": spans_line,
         "cpu_baseline": cpu,
         "clocks": clk.summary(),
     }

@@ -225,6 +225,30 @@ int align_set_tuning_bucket(align_ctx *ctx, int32_t s_max, int32_t states_per_la
 int align_set_tuning_bucket_for(align_ctx *ctx, int32_t table, int32_t s_max, int32_t states_per_lane,
                                 int32_t cta_warps);
 
+/* ---- token spans: the alignment per transcript token -------------------- */
+
+/* Token spans of one or more finished alignments, packed: utterance u owns
+   frames frame_offsets[u] .. frame_offsets[u+1]-1 of states / scores and
+   tokens token_offsets[u] .. token_offsets[u+1]-1 of the outputs (paper
+   Sec. 4: forced alignment gives the alignment between audio frames and
+   transcript tokens; this collapses it to one span per token). Transcript
+   token i occupies the frames whose trellis state is 2i + 1 (the states
+   output of align_submit); span_start[k] = first such frame, span_end[k] =
+   one past the last (frames relative to the utterance's first frame), and
+   span_score[k] = the FP32 sum of those frames' scores, added in frame order,
+   divided by the span length (IEEE division). A token with no frame (not a
+   valid alignment) gets -1, -1, 0.
+   All pointers are DEVICE pointers: states int32 [total_frames], scores
+   float32 [total_frames], frame_offsets / token_offsets int64 [n+1] with
+   frame_offsets[n] = total_frames and token_offsets[n] = total_tokens;
+   outputs int32 / int32 / float32 [total_tokens]. Runs asynchronously on
+   cuda_stream (NULL = legacy default stream): two memsets and two kernels.
+   ALIGN_E_INVAL for negative sizes or missing pointers, ALIGN_E_CUDA if a
+   launch fails. */
+int align_token_spans(const int32_t *states, const float *scores, const int64_t *frame_offsets,
+                      const int64_t *token_offsets, int32_t n, int64_t total_frames, int64_t total_tokens,
+                      int32_t *span_start, int32_t *span_end, float *span_score, void *cuda_stream);
+
 /* ---- allocation-free entry point ---------------------------------------- */
 
 /* Align one utterance without allocating any memory, for callers that cannot

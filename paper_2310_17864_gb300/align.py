@@ -42,7 +42,7 @@ ALIGN_F_TEST_STALL = 0x80000000
 EXPORTS = ("align_create", "align_destroy", "align_submit", "align_submit_host", "align_submit_batch", "align_flush",
            "align_poll", "align_poll_done", "align_join", "align_get_stats", "align_status_string", "align_last_error",
            "align_set_tuning", "align_set_tuning_bucket", "align_set_tuning_bucket_for", "align_validate", "align_plan", "align_probe_frame_latency",
-           "align_forced_noalloc", "align_noalloc_last_error")
+           "align_forced_noalloc", "align_noalloc_last_error", "align_token_spans")
 
 
 class AlignConfig(ctypes.Structure):
@@ -119,6 +119,7 @@ def lib() -> ctypes.CDLL:
         L.align_set_tuning.argtypes = [vp, i32, i32, i32]
         L.align_set_tuning_bucket.argtypes = [vp, i32, i32, i32]
         L.align_set_tuning_bucket_for.argtypes = [vp, i32, i32, i32, i32]
+        L.align_token_spans.argtypes = [vp, vp, vp, vp, i32, i64, i64, vp, vp, vp, vp]
         L.align_probe_frame_latency.argtypes = [i32, i32, i32, i32, ctypes.POINTER(ctypes.c_double)]
         L.align_forced_noalloc.argtypes = [vp, i64, i64, vp, i64, i32, AlignOut, vp, ctypes.POINTER(i32)]
         L.align_noalloc_last_error.argtypes = []
@@ -266,6 +267,49 @@ def align_noalloc_last_error() -> str:
 
 def align_set_tuning_bucket(ctx, s_max: int, states_per_lane: int = 0, cta_warps: int = 0) -> None:
     _check(lib().align_set_tuning_bucket(ctx, s_max, states_per_lane, cta_warps), "align_set_tuning_bucket")
+
+
+def align_token_spans(states, scores, frame_offsets, token_offsets, n: int, total_frames: int, total_tokens: int,
+                      span_start, span_end, span_score, stream_ptr: int | None = None) -> None:
+    """Same-named call: every pointer argument is a device address (int)."""
+    _check(lib().align_token_spans(states, scores, frame_offsets, token_offsets, n, total_frames, total_tokens,
+                                   span_start, span_end, span_score, stream_ptr), "align_token_spans")
+
+
+def token_spans(states, scores, frame_offsets, token_offsets, stream=None, totals=None):
+    """Token spans of packed alignments (CUDA tensors): states int32 [sum T],
+    scores float32 [sum T], frame_offsets / token_offsets int64 [n+1], host
+    arrays (copied to the device) or CUDA int64 tensors (then pass
+    totals=(sum T, sum L) to avoid reading them back). Returns (start int32,
+    end int32, score float32) CUDA tensors of [sum L]; frames relative to
+    each utterance."""
+    import torch
+    dev = states.device
+
+    def dev_offsets(x):
+        if isinstance(x, torch.Tensor) and x.is_cuda:
+            return x.to(torch.int64), None
+        h = np.asarray(x.cpu() if isinstance(x, torch.Tensor) else x, dtype=np.int64)
+        return torch.from_numpy(h).to(dev), h
+
+    fo, fo_h = dev_offsets(frame_offsets)
+    to, to_h = dev_offsets(token_offsets)
+    n = fo.numel() - 1
+    if totals is not None:
+        total_T, total_L = int(totals[0]), int(totals[1])
+    else:
+        total_T = int(fo_h[-1]) if fo_h is not None else int(fo[-1].item())
+        total_L = int(to_h[-1]) if to_h is not None else int(to[-1].item())
+    if states.dtype != torch.int32 or scores.dtype != torch.float32 or states.numel() < total_T or \
+            scores.numel() < total_T or not states.is_cuda or not scores.is_cuda:
+        raise ValueError("states int32 / scores float32 CUDA tensors of sum T elements expected")
+    start = torch.empty(total_L, dtype=torch.int32, device=dev)
+    end = torch.empty(total_L, dtype=torch.int32, device=dev)
+    score = torch.empty(total_L, dtype=torch.float32, device=dev)
+    st = stream if stream is not None else torch.cuda.current_stream(dev)
+    align_token_spans(states.data_ptr(), scores.data_ptr(), fo.data_ptr(), to.data_ptr(), n, total_T, total_L,
+                      start.data_ptr(), end.data_ptr(), score.data_ptr(), st.cuda_stream)
+    return start, end, score
 
 
 ALIGN_TUNE_LATENCY = 0
