@@ -80,16 +80,21 @@ def expand_tokens(targets, blank: int = BLANK) -> np.ndarray:
     return ext
 
 
-def emissions(seed: int, T: int, C: int, planted_tokens: np.ndarray, device="cpu",
-              out: torch.Tensor | None = None) -> torch.Tensor:
-    """log_softmax(3*N(0,1) + 4*onehot(planted)) as FP32 [T, C]."""
+def raw_logits(seed: int, T: int, C: int, planted_tokens: np.ndarray, device="cpu") -> torch.Tensor:
+    """3*N(0,1) + 4*onehot(planted) as FP32 [T, C] (the scores before log_softmax)."""
     g = torch.Generator(device=device)
     g.manual_seed(seed)
     logits = torch.randn((T, C), generator=g, device=device, dtype=torch.float32)
     logits.mul_(3.0)
     idx = torch.as_tensor(planted_tokens, device=device, dtype=torch.int64)
     logits[torch.arange(T, device=device), idx] += 4.0
-    lp = torch.log_softmax(logits, dim=-1)
+    return logits
+
+
+def emissions(seed: int, T: int, C: int, planted_tokens: np.ndarray, device="cpu",
+              out: torch.Tensor | None = None) -> torch.Tensor:
+    """log_softmax(3*N(0,1) + 4*onehot(planted)) as FP32 [T, C]."""
+    lp = torch.log_softmax(raw_logits(seed, T, C, planted_tokens, device), dim=-1)
     if out is not None:
         out.copy_(lp)
         return out
@@ -121,12 +126,17 @@ class Utterance:
 
 
 def make_utterance(seed: int, T: int, C: int, L: int, repeat_frac: float = 0.0,
-                   device="cpu", blank: int = BLANK) -> Utterance:
+                   device="cpu", blank: int = BLANK, logits: bool = False) -> Utterance:
+    """A seeded utterance; with logits=True, `lp` holds the raw scores before
+    log_softmax (same seed: log_softmax of them is the logits=False lp)."""
     rng = np.random.default_rng(seed)
     targets = make_targets(rng, L, C, repeat_frac, blank)
     planted = plant_state_path(rng, T, targets)
     tokens = expand_tokens(targets, blank)[planted]
-    lp = emissions(seed, T, C, tokens, device=device)
+    if logits:
+        lp = raw_logits(seed, T, C, tokens, device=device)
+    else:
+        lp = emissions(seed, T, C, tokens, device=device)
     return Utterance(lp=lp, targets=targets, planted=planted, seed=seed)
 
 
