@@ -62,6 +62,7 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="batch64", choices=sorted(WORKLOADS))
     ap.add_argument("--no-spans", action="store_true", help="skip the token-span leg")
+    ap.add_argument("--no-logits", action="store_true", help="skip the fused log_softmax leg")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the CPU oracle baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
@@ -383,6 +384,54 @@ def main():
                       "gbs": sp_bytes / (sp_ms / 1e3) / 1e9, "launches": 2,
                       "note": "two memsets and two kernels on device-resident offsets; L2 flushed before each"}
 
+    # Logits inputs: log_softmax fused into the kernel's staging (one request
+    # flag) against a separate log_softmax pass over the packed [sum T, C]
+    # logits followed by the log-probability path; same batch, device time.
+    logits_line = None
+    if not args.no_logits:
+        lb = synth.make_batch(synth.specs(wl["cfg"], C=wl["C"]), device=f"cuda:{dev}", logits=True)
+        l_utts = [lb.utt(i) for i in range(n)]
+        lp_buf = torch.empty_like(lb.lp)
+        lp_utts = [lp_buf[int(lb.offsets[i]):int(lb.offsets[i + 1])] for i in range(n)]
+
+        def timed(fn):
+            ts = []
+            for k in range(3 + args.steps):
+                flush_buf.fill_(1)
+                with torch.cuda.stream(stream):
+                    torch.cuda._sleep(hold["cycles"])
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    rs = fn()
+                    al.join(stream)
+                    e1.record(stream)
+                al.wait(rs)
+                assert all(r.status == 0 for r in rs)
+                e1.synchronize()
+                if k >= 3:
+                    ts.append(e0.elapsed_time(e1))
+            return statistics.mean(ts)
+
+        def fused():
+            rs = al.submit_batch([(l_utts[i], lb.targets[i], 0, outs[i]) for i in range(n)], logits=True)
+            al.flush()
+            return rs
+
+        def separate():
+            torch.log_softmax(lb.lp, dim=-1, out=lp_buf)
+            rs = al.submit_batch([(lp_utts[i], lb.targets[i], 0, outs[i]) for i in range(n)])
+            al.flush()
+            return rs
+
+        f_ms = timed(fused)
+        s_ms = timed(separate)
+        logits_line = {"fused_ms": f_ms, "separate_ms": s_ms, "fused_cells_per_s": cells / (f_ms / 1e3),
+                       "separate_cells_per_s": cells / (s_ms / 1e3),
+                       "separate": "torch.log_softmax over the packed logits, then the log-probability path",
+                       "logit_bytes": int(lb.lp.numel()) * 4}
+        del lb, lp_buf
+
     # Plain: one synchronous submit + poll per utterance (at most 256 utterances).
     plain = None
     if not args.no_plain:
@@ -514,6 +563,7 @@ def main():
         "roofline": rl,
         "serving": serving,
         "token_spans": spans_line,
+        "logits": logits_line,
         "cpu_baseline": cpu,
         "clocks": clk.summary(),
     }

@@ -124,6 +124,14 @@ int align_submit_host(align_ctx *ctx, const float *log_probs, int64_t T, int64_t
 
 /* One request of a batch submission. */
 #define ALIGN_REQ_HOST 0x1u  /* log_probs and out.* are HOST pointers (as align_submit_host) */
+#define ALIGN_REQ_LOGITS 0x2u /* log_probs holds raw per-frame scores (logits): the kernel
+                                 applies log_softmax over each row as it stages it (one extra
+                                 warp per CTA: lse = m + logf(sum expf(x - m)), m the row
+                                 maximum, then x - lse in FP32), so no separate log_softmax
+                                 pass over [T][C] is needed; scores are then log-probabilities.
+                                 Results equal an alignment of those FP32 log-probabilities;
+                                 they may differ from one of log-probabilities computed
+                                 elsewhere by the rounding of expf / logf. */
 typedef struct {
     const float *log_probs;   /* [T][C] FP32 row-major, device (or host with ALIGN_REQ_HOST) */
     int64_t T, C;

@@ -58,6 +58,7 @@ class AlignOut(ctypes.Structure):
 
 
 ALIGN_REQ_HOST = 0x1
+ALIGN_REQ_LOGITS = 0x2   # log_probs holds raw logits: log_softmax is applied inside the kernel
 
 
 class AlignRequest(ctypes.Structure):
@@ -388,7 +389,10 @@ class Aligner:
         except Exception:
             pass
 
-    def submit(self, log_probs, targets, blank: int = 0, want_states: bool = False, out=None) -> Result:
+    def submit(self, log_probs, targets, blank: int = 0, want_states: bool = False, out=None,
+               logits: bool = False) -> Result:
+        """Device tensors. logits=True: log_probs holds raw logits and the
+        kernel applies log_softmax per frame while staging (ALIGN_REQ_LOGITS)."""
         torch = self.torch
         if not (log_probs.is_cuda and log_probs.dtype == torch.float32 and log_probs.dim() == 2
                 and log_probs.is_contiguous()):
@@ -402,6 +406,9 @@ class Aligner:
             states = torch.empty(T, dtype=torch.int32, device=dev) if want_states else None
         else:
             path, scores, total, states = out
+        if logits:
+            (res,) = self.submit_batch([(log_probs, targets, blank, (path, scores, total, states))], logits=True)
+            return res
         o = AlignOut(path.data_ptr(), scores.data_ptr(), total.data_ptr(),
                      states.data_ptr() if states is not None else None)
         rid = align_submit(self.ctx, log_probs.data_ptr(), T, C, targets, blank, o)
@@ -430,7 +437,7 @@ class Aligner:
         self._live[rid] = (log_probs, res)
         return res
 
-    def submit_batch(self, items, host: bool = False) -> list[Result]:
+    def submit_batch(self, items, host: bool = False, logits: bool = False) -> list[Result]:
         """items: sequence of (log_probs, targets, blank, out) with out = (path, scores, total, states)
         tensors (device tensors, or host tensors when host=True). One C call for the whole batch."""
         n = len(items)
@@ -455,7 +462,7 @@ class Aligner:
             results.append(Result(0, path, scores, total, states))
         for k, v in cols.items():
             reqs[k] = v
-        reqs["flags"] = ALIGN_REQ_HOST if host else 0
+        reqs["flags"] = (ALIGN_REQ_HOST if host else 0) | (ALIGN_REQ_LOGITS if logits else 0)
         ids, st = align_submit_batch(self.ctx, reqs)
         for r, rid, code, k in zip(results, ids, st, keep):
             if code < 0:
@@ -485,7 +492,7 @@ class Aligner:
         return out
 
     def submit_packed(self, log_probs, offsets, targets, target_offsets, out, blank: int = 0,
-                      host: bool = False) -> PackedResult:
+                      host: bool = False, logits: bool = False) -> PackedResult:
         """A ragged batch in packed form, marshalled without a per-utterance
         Python loop. log_probs: float32 [sum T, C] (utterance i = rows
         offsets[i]:offsets[i+1]); targets: int32 [sum L] (utterance i =
@@ -511,7 +518,7 @@ class Aligner:
         reqs["tg"] = np.uint64(tg.ctypes.data) + target_offsets[:-1].astype(np.uint64) * np.uint64(4)
         reqs["L"] = np.diff(target_offsets)
         reqs["blank"] = blank
-        reqs["flags"] = ALIGN_REQ_HOST if host else 0
+        reqs["flags"] = (ALIGN_REQ_HOST if host else 0) | (ALIGN_REQ_LOGITS if logits else 0)
         reqs["path"] = np.uint64(path.data_ptr()) + f0 * np.uint64(4)
         reqs["scores"] = np.uint64(scores.data_ptr()) + f0 * np.uint64(4)
         reqs["total"] = np.uint64(total.data_ptr()) + np.arange(n, dtype=np.uint64) * np.uint64(4)
@@ -585,8 +592,8 @@ class Aligner:
                     if self.poll(pending[rid], 0):
                         pending.pop(rid)
 
-    def align(self, log_probs, targets, blank: int = 0, want_states: bool = False) -> Result:
-        res = self.submit(log_probs, targets, blank, want_states)
+    def align(self, log_probs, targets, blank: int = 0, want_states: bool = False, logits: bool = False) -> Result:
+        res = self.submit(log_probs, targets, blank, want_states, logits=logits)
         self.flush()
         self.poll(res)
         return res

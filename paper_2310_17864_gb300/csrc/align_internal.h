@@ -40,11 +40,14 @@ struct Plan {
   uint64_t z_off = 0;         // offset of the anchor rows inside the full-mode allocation
   uint64_t seg_z_off = 0;     // offset of the anchor rows inside the segment buffer
   uint64_t x_bytes = 0;       // grid teams: CTA links, after the backpointers (or the segment buffer)
+  uint64_t lse_bytes = 0;     // logits inputs: the per-frame log_softmax shift, after the links
 };
-// Device bytes of a request: backpointers (or checkpoints + one segment) and
-// the CTA links of a grid team; the links start at plan_x_off.
+// Device bytes of a request: backpointers (or checkpoints + one segment), the
+// CTA links of a grid team (from plan_x_off), the per-frame shift of a
+// logits request (from plan_lse_off).
 inline uint64_t plan_x_off(const Plan& p) { return p.checkpointed ? p.ckpt_bytes + p.seg_bp_bytes : p.bp_bytes; }
-inline uint64_t plan_device_bytes(const Plan& p) { return plan_x_off(p) + p.x_bytes; }
+inline uint64_t plan_lse_off(const Plan& p) { return plan_x_off(p) + p.x_bytes; }
+inline uint64_t plan_device_bytes(const Plan& p) { return plan_lse_off(p) + p.lse_bytes; }
 
 // Step A1: 0, ALIGN_E_INVAL, ALIGN_E_TARGET or ALIGN_E_INFEASIBLE; *repeats = R.
 int validate_request(const int32_t* targets, int64_t L, int64_t C, int32_t blank, int64_t T, int64_t* repeats);

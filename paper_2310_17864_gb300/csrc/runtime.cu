@@ -138,6 +138,7 @@ struct Request {
   // cudaMemcpyAsync per buffer. Null when any buffer is not addressable.
   const void* lp_alias = nullptr;
   align_out out_alias{};
+  bool logits = false;  // lp holds raw logits (ALIGN_REQ_LOGITS)
   align_out out{};            // caller outputs (device or host)
   int64_t T = 0, C = 0, L = 0;
   int32_t blank = 0;
@@ -218,6 +219,22 @@ struct align_ctx {
 namespace {
 
 uint64_t inflight_count(const align_ctx* ctx) { return ctx->reqs.size(); }
+
+// Plan of a request with one tuning table. Logits requests get a normaliser
+// warp per CTA (so at most 15 compute warps) and a per-frame shift buffer.
+int plan_request(const align_ctx* ctx, const TuneTable& table, int64_t T, int64_t C, int64_t L, bool logits,
+                 Plan* out) {
+  TuneTable t = table;
+  if (logits) t.max_warps = std::min(t.max_warps, 15);
+  const int rc = make_plan(t, T, C, L, ctx->bp_arena.cap(), (ctx->flags & ALIGN_F_FORCE_CHECKPOINT) != 0, out);
+  if (rc != ALIGN_OK) return rc;
+  if (logits) {
+    out->shape.norm = 1;
+    out->lse_bytes = (static_cast<uint64_t>(T) * 4 + 255) & ~255ull;
+    if (plan_device_bytes(*out) > ctx->bp_arena.cap()) return ALIGN_E_TOO_LARGE;
+  }
+  return ALIGN_OK;
+}
 
 // A device-addressable alias of host memory, or nullptr.
 void* device_alias(const align_ctx* ctx, const void* p) {
@@ -313,8 +330,7 @@ bool choose_tables(align_ctx* ctx) {
     Request& r = ctx->reqs.at(id);
     if (r.plan_table == want) continue;
     Plan p{};
-    if (make_plan(tp ? ctx->tune_tp : ctx->tune, r.T, r.C, r.L, ctx->bp_arena.cap(),
-                  (ctx->flags & ALIGN_F_FORCE_CHECKPOINT) != 0, &p) == ALIGN_OK) {
+    if (plan_request(ctx, tp ? ctx->tune_tp : ctx->tune, r.T, r.C, r.L, r.logits, &p) == ALIGN_OK) {
       p.shape.occ = tp ? 1 : 0;
       r.plan = p;
       r.plan_table = want;
@@ -389,14 +405,15 @@ int launch_queued(align_ctx* ctx) {
   // get 1 + nck descriptors each.
   // (K, warps, ncta, F, C) -> request indices. C is part of the key: the launch
   // parameters (emission stage size) depend on it.
-  std::map<std::tuple<int, int, int, int, int, int>, std::vector<int>> groups;
+  std::map<std::tuple<int, int, int, int, int, int, int>, std::vector<int>> groups;
   size_t njobs = 0;
   for (size_t i = 0; i < take.size(); ++i) {
     const Plan& p = take[i]->plan;
     if (p.checkpointed || p.shape.grid) {  // a launch sequence of its own
       njobs += p.checkpointed ? 1 + static_cast<size_t>(p.nck) : 1;
     } else {
-      groups[{p.shape.K, p.shape.warps, p.shape.ncta, p.frames_per_stage, static_cast<int>(take[i]->C), p.shape.occ}].push_back(
+      groups[{p.shape.K, p.shape.warps, p.shape.ncta, p.frames_per_stage, static_cast<int>(take[i]->C), p.shape.occ,
+              p.shape.norm}].push_back(
           static_cast<int>(i));
       njobs += 1;
     }
@@ -436,13 +453,13 @@ int launch_queued(align_ctx* ctx) {
     for (auto& kv : groups) {
       key.insert(key.end(), {std::get<0>(kv.first), std::get<1>(kv.first), std::get<2>(kv.first),
                              std::get<3>(kv.first), std::get<4>(kv.first), std::get<5>(kv.first),
-                             static_cast<int64_t>(kv.second.size())});
+                             std::get<6>(kv.first), static_cast<int64_t>(kv.second.size())});
     }
     for (auto* r : take) {
       const Plan& p = r->plan;
       if (!p.checkpointed && !p.shape.grid) continue;
-      key.insert(key.end(), {-1, p.shape.K, p.shape.warps, p.shape.ncta, p.shape.occ, p.shape.grid, p.frames_per_stage,
-                             p.checkpointed ? p.nck : -1, r->C});
+      key.insert(key.end(), {-1, p.shape.K, p.shape.warps, p.shape.ncta, p.shape.occ, p.shape.grid, p.shape.norm,
+                             p.frames_per_stage, p.checkpointed ? p.nck : -1, r->C});
     }
     for (size_t k = 0; k < ctx->graphs.size(); ++k)
       if (ctx->graphs[k].key == key) gi = static_cast<int>(k);
@@ -588,6 +605,7 @@ int launch_queued(align_ctx* ctx) {
     j.L = static_cast<int32_t>(r.L);
     j.S = static_cast<int32_t>(2 * r.L + 1);
     j.flags = (rows_bulk_ok(j.lp, r.C) ? kJobBulkRows : 0u) | ((ctx->flags & ALIGN_F_TEST_STALL) ? kJobTestStall : 0u);
+    j.lse = r.logits ? reinterpret_cast<float*>(ctx->d_bp + r.bp.off + plan_lse_off(r.plan)) : nullptr;
     return j;
   };
 
@@ -631,6 +649,7 @@ int launch_queued(align_ctx* ctx) {
   for (auto& kv : groups) {
     GroupLaunch gl{};
     gl.shape = LaunchShape{std::get<0>(kv.first), std::get<1>(kv.first), std::get<2>(kv.first), std::get<5>(kv.first)};
+    gl.shape.norm = std::get<6>(kv.first);
     gl.F = std::get<3>(kv.first);
     gl.first = jn;
     gl.count = kv.second.size();
@@ -886,7 +905,7 @@ int pump(align_ctx* ctx, bool launch) {
 }
 
 int submit_common(align_ctx* ctx, const float* lp, int64_t T, int64_t C, const int32_t* targets, int64_t L,
-                  int32_t blank, align_out out, uint64_t* request_id, bool host_io) {
+                  int32_t blank, align_out out, uint64_t* request_id, bool host_io, bool logits = false) {
   if (!ctx || !lp || !request_id || !out.path || !out.scores || !out.total) return ALIGN_E_INVAL;
   if (L > 0 && !targets) return ALIGN_E_INVAL;
   // Frame tags in the ring words have 24 bits; 2^24 frames of 20 ms are 93 hours.
@@ -900,9 +919,10 @@ int submit_common(align_ctx* ctx, const float* lp, int64_t T, int64_t C, const i
     if (static_cast<int64_t>(inflight_count(ctx)) >= ctx->max_inflight) return ALIGN_E_AGAIN;
   }
   Plan p{};
-  rc = make_plan(ctx->tune, T, C, L, ctx->bp_arena.cap(), (ctx->flags & ALIGN_F_FORCE_CHECKPOINT) != 0, &p);
+  rc = plan_request(ctx, ctx->tune, T, C, L, logits, &p);
   if (rc != ALIGN_OK) return rc;
   Request r;
+  r.logits = logits;
   if (host_io) {
     align_out al{};
     const void* la = device_alias(ctx, lp);
@@ -1060,8 +1080,10 @@ int align_submit_batch(align_ctx* ctx, int32_t n, const align_request* reqs, uin
   int first_err = ALIGN_OK;
   for (int32_t i = 0; i < n; ++i) {
     const align_request& q = reqs[i];
-    int rc = submit_common(ctx, q.log_probs, q.T, q.C, q.targets, q.L, q.blank, q.out, &request_ids[i],
-                           (q.flags & ALIGN_REQ_HOST) != 0);
+    int rc = (q.flags & ~(ALIGN_REQ_HOST | ALIGN_REQ_LOGITS))
+                 ? ALIGN_E_INVAL
+                 : submit_common(ctx, q.log_probs, q.T, q.C, q.targets, q.L, q.blank, q.out, &request_ids[i],
+                                 (q.flags & ALIGN_REQ_HOST) != 0, (q.flags & ALIGN_REQ_LOGITS) != 0);
     if (rc != ALIGN_OK) request_ids[i] = 0;
     if (submit_status) submit_status[i] = rc;
     if (rc != ALIGN_OK && first_err == ALIGN_OK) first_err = rc;

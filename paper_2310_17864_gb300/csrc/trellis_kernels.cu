@@ -120,10 +120,10 @@ __device__ __forceinline__ void cp_async_mbar_arrive(uint64_t* bar) {
 struct SmemHead {
   uint64_t full[kMaxStages];   // emission stage filled
   uint64_t empty[kMaxStages];  // emission stage released by every warp
+  uint64_t normd[kMaxStages];  // logits mode: stage normalised by the normaliser warp
   int32_t abort;            // set by any thread of this CTA whose wait hit the limit
   uint32_t unused;
   uint64_t sink;            // scratch slot written by the last warp of the team
-  int32_t pad[(256 - 16 * kMaxStages - 16) / 4];
 };
 static_assert(sizeof(SmemHead) == 256, "head size");
 
@@ -299,6 +299,52 @@ __device__ __forceinline__ void store_bp_words_if(uint32_t* dst, const uint32_t 
   }
 }
 
+// The log_softmax shift lse = m + logf(sum __expf(x - m)) of nf rows of C
+// logits (m the row maximum; the fast exponential intrinsic, whose error is
+// part of the stated tolerance), by one warp: lanes split into groups of lpr
+// lanes, one group per row (lpr = 32 / rows per pass); each lane takes every
+// lpr-th column. With one lane per row the lane starts its sweep at its own
+// column offset (rows of an even number of classes would otherwise put every
+// lane in the same shared-memory bank). Lane 0 of a group stores the row's
+// shift to lse_s[r] and, when given, lse_out[r]. The readers subtract it:
+// log-probability = x - lse, one FP32 subtraction.
+__device__ void log_softmax_shifts(const float* rows, int nf, int C, int lane, float* lse_s, float* lse_out) {
+  const int rpp = nf < 32 ? (nf < 1 ? 1 : nf) : 32;  // rows per pass
+  int lpr = 1;                                       // lanes per row: a power of two
+  while (lpr * 2 * rpp <= 32) lpr *= 2;
+  const int grp = lane / lpr, sub = lane % lpr;
+  const int groups = 32 / lpr;
+  const int rot = (lpr == 1 && (C & 1) == 0) ? lane % C : 0;  // first column of this lane's sweep
+  for (int r0 = 0; r0 < nf; r0 += groups) {
+    const int r = r0 + grp;
+    const bool live = r < nf;
+    const float* x = rows + static_cast<size_t>(live ? r : 0) * C;
+    float m = -INFINITY;
+    if (live) {
+      int c = sub + rot;
+      for (int k = sub; k < C; k += lpr, c += lpr) {
+        if (c >= C) c -= C;
+        m = fmaxf(m, x[c]);
+      }
+    }
+    for (int k = lpr >> 1; k > 0; k >>= 1) m = fmaxf(m, __shfl_xor_sync(kFull, m, k, lpr));
+    float sum = 0.0f;
+    if (live) {
+      int c = sub + rot;
+      for (int k = sub; k < C; k += lpr, c += lpr) {
+        if (c >= C) c -= C;
+        sum += __expf(x[c] - m);
+      }
+    }
+    for (int k = lpr >> 1; k > 0; k >>= 1) sum += __shfl_xor_sync(kFull, sum, k, lpr);
+    const float lse = m + logf(sum);
+    if (live && sub == 0) {
+      lse_s[r] = lse;
+      if (lse_out) lse_out[r] = lse;
+    }
+  }
+}
+
 // One backpointer row (NW = 3 or 6 words) stored by the lane that buffered it.
 template <int K, int NWB>
 __device__ __forceinline__ void store_bp_row(uint32_t* dst, const uint32_t (&w)[NWB]) {
@@ -320,7 +366,11 @@ __device__ __forceinline__ void store_bp_row(uint32_t* dst, const uint32_t (&w)[
 // kGrid: the team is P.grid_ctas consecutive CTAs of a cooperative launch
 // (one per SM) instead of a thread-block cluster; the links between CTAs (the
 // boundary rings, progress words, barrier) are in global memory.
-template <int K, bool kOcc, bool kGrid>
+//
+// kNorm: log_probs hold raw logits; each CTA has one more warp, the
+// normaliser (a separate instantiation so the log-probability path keeps its
+// own code).
+template <int K, bool kOcc, bool kGrid, bool kNorm>
 __global__ void __launch_bounds__(512, (kOcc && K <= 4) ? 2 : 1)
     trellis_kernel(const FwdJob* __restrict__ jobs, const FwdParams P) {
   static_assert(K % 2 == 0 && K >= 2 && K <= 16, "K must be even, 2..16");
@@ -334,8 +384,12 @@ __global__ void __launch_bounds__(512, (kOcc && K <= 4) ? 2 : 1)
 
   const uint32_t ncta = kGrid ? static_cast<uint32_t>(max(P.grid_ctas, 1)) : cluster_nctarank();
   const uint32_t crank = kGrid ? blockIdx.x % ncta : cluster_ctarank();
-  const int W = blockDim.x >> 5;
+  // Logits mode (kNorm): the last warp of each CTA is a normaliser that
+  // turns each staged chunk of raw logits into log-probabilities in place
+  // before the W compute warps read it; it computes no states.
+  const int W = (blockDim.x >> 5) - (kNorm ? 1 : 0);
   const int warp = threadIdx.x >> 5;
+  const bool is_norm = kNorm && warp == W;
   const int lane = threadIdx.x & 31;
   const FwdJob& J = jobs[blockIdx.x / ncta];
   const int g = static_cast<int>(crank) * W + warp;  // warp index in the team
@@ -360,6 +414,7 @@ __global__ void __launch_bounds__(512, (kOcc && K <= 4) ? 2 : 1)
   float* const scores_out = J.scores;
   int32_t* const states_out = J.states;
   const int32_t* const tgt = J.tgt;
+  float* const lse_g = J.lse;  // logits mode: per-frame log_softmax shift
 
   // Launch parameters must fit the job: a stage holds F rows of C floats and
   // the team holds every state. The check is uniform over the cluster (same
@@ -382,6 +437,7 @@ __global__ void __launch_bounds__(512, (kOcc && K <= 4) ? 2 : 1)
     for (int st = 0; st < P.stages; ++st) {
       mbar_init(&head->full[st], bulk ? 1u : 32u);
       mbar_init(&head->empty[st], static_cast<uint32_t>(W));
+      mbar_init(&head->normd[st], 1u);
     }
     head->abort = 0;
     fence_barrier_init();
@@ -455,10 +511,24 @@ __global__ void __launch_bounds__(512, (kOcc && K <= 4) ? 2 : 1)
   if (J.alpha_in == nullptr) {
     // alpha_0: paths start in the blank (state 0) or the first label (state 1).
     const float* row = lp + static_cast<size_t>(t_begin) * C;
+    float lse0 = 0.0f;
+    if (kNorm && g == 0) {  // logits mode: this row's log_softmax shift, by the first warp
+      float m = -INFINITY;
+      for (int c = lane; c < C; c += 32) m = fmaxf(m, __ldg(row + c));
+      for (int k = 16; k > 0; k >>= 1) m = fmaxf(m, __shfl_xor_sync(kFull, m, k));
+      float sum = 0.0f;
+      for (int c = lane; c < C; c += 32) sum += __expf(__ldg(row + c) - m);
+      for (int k = 16; k > 0; k >>= 1) sum += __shfl_xor_sync(kFull, sum, k);
+      lse0 = m + logf(sum);
+      if (lane == 0 && lse_g) lse_g[t_begin] = lse0;
+    }
 #pragma unroll
     for (int j = 0; j < K; ++j) {
       const int s = s0 + j;
-      a[j] = (s == 0) ? __ldg(row + blank) : ((s == 1 && S > 1) ? __ldg(row + col[0]) : -INFINITY);
+      if constexpr (kNorm)
+        a[j] = (s == 0) ? __ldg(row + blank) - lse0 : ((s == 1 && S > 1) ? __ldg(row + col[0]) - lse0 : -INFINITY);
+      else
+        a[j] = (s == 0) ? __ldg(row + blank) : ((s == 1 && S > 1) ? __ldg(row + col[0]) : -INFINITY);
     }
   } else {
 #pragma unroll
@@ -575,7 +645,7 @@ __global__ void __launch_bounds__(512, (kOcc && K <= 4) ? 2 : 1)
       *reinterpret_cast<uint4*>(dst) = make_uint4(packed[0], packed[1], packed[2], packed[3]);
     }
   };
-  if (ok) {
+  if (ok && !is_norm) {
     if (ckpt != nullptr && (t_begin % ck_every) == 0) store_ckpt(t_begin);
     send_one(t_begin, a[K - 1], A[K - 1]);  // slot of t_begin is fresh: no flow check needed
   }
@@ -595,6 +665,8 @@ __global__ void __launch_bounds__(512, (kOcc && K <= 4) ? 2 : 1)
   const bool write_bp = (bp != nullptr) && is_l0;
   const float* stage_f = reinterpret_cast<const float*>(stages);
   const int stage_floats = P.stage_bytes / 4;
+  float* const lse_s = reinterpret_cast<float*>(smem + P.off_lse);  // logits mode: [stages * F + 1]
+  int lidx = 0;           // logits mode: shift of frame t in lse_s
   constexpr bool kBufBp = NW <= 6;  // K = 2, 4: a window's backpointer rows buffered in registers
   uint32_t wb[kBufBp ? NW : 1];
 #pragma unroll
@@ -606,6 +678,26 @@ __global__ void __launch_bounds__(512, (kOcc && K <= 4) ? 2 : 1)
   int roff = 0;
   int bi = 0;             // frame index within the current block
   int t = t_begin + 1;
+  if (kNorm && is_norm) {
+    // The normaliser: every chunk, once it has arrived, in stage order. The lse
+    // of each frame goes to J.lse (CTA 0 only) for the score gather.
+    int n_stage = 0;
+    uint32_t n_round = 0;
+    const float* const rows_all = reinterpret_cast<const float*>(stages);
+    for (int c = 0; c < nchunks; ++c) {
+      if (!warp_wait_phase(&head->full[n_stage], n_round & 1u, abort, limit, lane)) break;
+      const int f0 = t_begin + 1 + c * F;
+      log_softmax_shifts(rows_all + n_stage * stage_floats, min(F, t_end - f0), C, lane, lse_s + n_stage * F,
+                         (crank == 0 && lse_g) ? lse_g + f0 : nullptr);
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&head->normd[n_stage]);  // release: the shifts of this stage
+      if (++n_stage == P.stages) {
+        n_stage = 0;
+        ++n_round;
+      }
+    }
+    t = t_end;  // computes no frames
+  }
   while (t < t_end) {
     const int ft = t - t_begin - 1;  // frames computed so far
     if ((ft & (F - 1)) == 0) {       // first frame of a chunk
@@ -624,8 +716,10 @@ __global__ void __launch_bounds__(512, (kOcc && K <= 4) ? 2 : 1)
         }
       }
       if (__any_sync(kFull, *abort != 0)) break;
-      if (!warp_wait_phase(&head->full[c_stage], c_round & 1u, abort, limit, lane)) break;
+      if (!warp_wait_phase(kNorm ? &head->normd[c_stage] : &head->full[c_stage], c_round & 1u, abort, limit, lane))
+        break;
       ridx = c_stage * stage_floats;
+      if constexpr (kNorm) lidx = c_stage * F;
     }
     if ((ft & (B - 1)) == 0) {  // first frame of a receive block
       const int nb = min(B, t_end - t);
@@ -664,6 +758,12 @@ __global__ void __launch_bounds__(512, (kOcc && K <= 4) ? 2 : 1)
     float el_n[K / 2];
 #pragma unroll
     for (int q = 0; q < K / 2; ++q) el_n[q] = stage_f[ridx + col[q]];
+    if constexpr (kNorm) {  // log-probability = logit - the row's shift
+      const float sh = lse_s[lidx];
+      eb_n -= sh;
+#pragma unroll
+      for (int q = 0; q < K / 2; ++q) el_n[q] -= sh;
+    }
     // Backpointer words. NW <= 6: lane i keeps the words of the window's
     // frame i in registers and the warp stores a whole window at once (one
     // row per lane). Wider rows: lane 0 stores the words of the previous
@@ -686,6 +786,12 @@ __global__ void __launch_bounds__(512, (kOcc && K <= 4) ? 2 : 1)
       eb_n = stage_f[ridx + blank];
 #pragma unroll
       for (int q = 0; q < K / 2; ++q) el_n[q] = stage_f[ridx + col[q]];
+      if constexpr (kNorm) {
+        const float sh = lse_s[++lidx];
+        eb_n -= sh;
+#pragma unroll
+        for (int q = 0; q < K / 2; ++q) el_n[q] -= sh;
+      }
 
       // alpha_{t-1}(s0 - 1) and its anchor: lane below by shuffle, lane 0 from the block.
       const float shf = __shfl_up_sync(kFull, a[K - 1], 1);
@@ -762,12 +868,12 @@ __global__ void __launch_bounds__(512, (kOcc && K <= 4) ? 2 : 1)
   }
   // Last, partial window.
   const int nwin = (t_end - 1 - t_begin + kAnchorD - 1) / kAnchorD;  // anchor rows of this pass
-  if (ok && *abort == 0 && t_end - 1 > t_begin && ((t_end - 1 - t_begin) % kAnchorD) != 0)
+  if (ok && !is_norm && *abort == 0 && t_end - 1 > t_begin && ((t_end - 1 - t_begin) % kAnchorD) != 0)
     store_anchor_row(nwin - 1);
 
   // ---- alpha_{T-1} of the two final states ----
   const bool aborted_here = (*abort != 0);
-  if (!aborted_here && t_end == J.T && J.final2 != nullptr) {
+  if (!aborted_here && !is_norm && t_end == J.T && J.final2 != nullptr) {
 #pragma unroll
     for (int j = 0; j < K; ++j) {
       if (s0 + j == S - 1) J.final2[1] = a[j];
@@ -854,7 +960,7 @@ __global__ void __launch_bounds__(512, (kOcc && K <= 4) ? 2 : 1)
   // cache lines.
   const int G = static_cast<int>(ncta) * W;
   const int nwalk = max(nwin, 1);
-  for (int m = g * 32 + lane; m < nwalk; m += G * 32) {
+  for (int m = g * 32 + lane; !is_norm && m < nwalk; m += G * 32) {
     const int b = t_begin + m * kAnchorD;
     const int e = (nwin == 0) ? t_begin : min(b + kAnchorD, t_end - 1);
     int sc = path[e];
@@ -881,7 +987,7 @@ __global__ void __launch_bounds__(512, (kOcc && K <= 4) ? 2 : 1)
     constexpr int kT3 = 8;
     const int tid = g * 32 + lane;
     const int nthr = G * 32;
-    for (int f0 = t_begin + tid; f0 < t_end; f0 += kT3 * nthr) {
+    for (int f0 = t_begin + tid; !is_norm && f0 < t_end; f0 += kT3 * nthr) {
       int st[kT3], tok[kT3];
       float sv[kT3];
 #pragma unroll
@@ -894,7 +1000,10 @@ __global__ void __launch_bounds__(512, (kOcc && K <= 4) ? 2 : 1)
 #pragma unroll
       for (int k = 0; k < kT3; ++k) {
         const int f = f0 + k * nthr;
-        sv[k] = (f < t_end) ? __ldg(lp + static_cast<size_t>(f) * C + tok[k]) : 0.0f;
+        if constexpr (kNorm)
+          sv[k] = (f < t_end) ? __ldg(lp + static_cast<size_t>(f) * C + tok[k]) - lse_g[f] : 0.0f;
+        else
+          sv[k] = (f < t_end) ? __ldg(lp + static_cast<size_t>(f) * C + tok[k]) : 0.0f;
       }
 #pragma unroll
       for (int k = 0; k < kT3; ++k) {
@@ -939,7 +1048,7 @@ __global__ void __launch_bounds__(1024) frame_probe_kernel(int frames, uint64_t 
   }
 }
 
-template <int K, bool kOcc, bool kGrid>
+template <int K, bool kOcc, bool kGrid, bool kNorm>
 cudaError_t launch_k(const LaunchShape& shape, const FwdParams& p, const FwdJob* d_jobs, int njobs,
                      cudaStream_t stream) {
   int dev = 0;
@@ -953,7 +1062,7 @@ cudaError_t launch_k(const LaunchShape& shape, const FwdParams& p, const FwdJob*
     smem = std::max(smem, smem_max);
     if (njobs != 1) return cudaErrorInvalidValue;  // one team per cooperative launch
   }
-  auto fn = trellis_kernel<K, kOcc, kGrid>;
+  auto fn = trellis_kernel<K, kOcc, kGrid, kNorm>;
   // The allowed maximum is always the device's opt-in limit, never the size
   // of the launch at hand: launches of one kernel captured into a graph ask
   // for different sizes, and none may see a limit lowered by another.
@@ -962,7 +1071,7 @@ cudaError_t launch_k(const LaunchShape& shape, const FwdParams& p, const FwdJob*
   if (smem > smem_max) return cudaErrorInvalidValue;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(static_cast<unsigned>(njobs * shape.ncta), 1, 1);
-  cfg.blockDim = dim3(static_cast<unsigned>(shape.warps * 32), 1, 1);
+  cfg.blockDim = dim3(static_cast<unsigned>((shape.warps + (kNorm ? 1 : 0)) * 32), 1, 1);
   cfg.dynamicSmemBytes = static_cast<size_t>(smem);
   cfg.stream = stream;
   cudaLaunchAttribute attr[1];
@@ -986,6 +1095,20 @@ cudaError_t launch_k(const LaunchShape& shape, const FwdParams& p, const FwdJob*
   return cudaLaunchKernelEx(&cfg, fn, d_jobs, p);
 }
 
+// The instantiation of a launch shape: latency or occupancy build (K <= 4),
+// cluster or grid team, log-probabilities or logits.
+template <int K>
+cudaError_t launch_shape(const LaunchShape& shape, const FwdParams& p, const FwdJob* d_jobs, int njobs,
+                         cudaStream_t s) {
+  if (shape.norm) {
+    if (shape.grid) return launch_k<K, false, true, true>(shape, p, d_jobs, njobs, s);
+    return launch_k<K, false, false, true>(shape, p, d_jobs, njobs, s);
+  }
+  if (shape.grid) return launch_k<K, false, true, false>(shape, p, d_jobs, njobs, s);
+  if (K <= 4 && shape.occ) return launch_k<K, (K <= 4), false, false>(shape, p, d_jobs, njobs, s);
+  return launch_k<K, false, false, false>(shape, p, d_jobs, njobs, s);
+}
+
 }  // namespace
 
 FwdParams plan_params(const LaunchShape& shape, int C, int frames_per_stage, uint64_t wait_limit_ns) {
@@ -1006,6 +1129,7 @@ FwdParams plan_params(const LaunchShape& shape, int C, int frames_per_stage, uin
   while (p.block * 2 <= room) p.block *= 2;
   p.stages = kLead + (hops * p.block + F - 1) / F;
   p.grid_ctas = shape.grid ? shape.ncta : 0;
+  p.norm = shape.norm ? 1 : 0;
   int rb = 8;
   while (rb < 2 * p.block + 2) rb <<= 1;
   p.rb = rb;
@@ -1015,7 +1139,8 @@ FwdParams plan_params(const LaunchShape& shape, int C, int frames_per_stage, uin
   p.off_stage = (p.off_ring + shape.warps * rb * 8 + 127) & ~127;
   // One spare row after the last stage: the emission look-ahead of a chunk's
   // last frame reads (and discards) the row after it.
-  p.off_bt = (p.off_stage + p.stages * p.stage_bytes + C * 4 + 127) & ~127;  // end of the forward region
+  p.off_lse = (p.off_stage + p.stages * p.stage_bytes + C * 4 + 15) & ~15;
+  p.off_bt = (p.off_lse + (shape.norm ? (p.stages * F + 1) * 4 : 0) + 127) & ~127;  // end of the forward region
   p.wait_limit_ns = wait_limit_ns;
   return p;
 }
@@ -1032,20 +1157,10 @@ int launch_trellis(const LaunchShape& shape, const FwdParams& p, const FwdJob* d
   if (njobs <= 0) return cudaSuccess;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   switch (shape.K) {
-    case 2:
-      if (shape.grid) return launch_k<2, false, true>(shape, p, d_jobs, njobs, s);
-      return shape.occ ? launch_k<2, true, false>(shape, p, d_jobs, njobs, s)
-                       : launch_k<2, false, false>(shape, p, d_jobs, njobs, s);
-    case 4:
-      if (shape.grid) return launch_k<4, false, true>(shape, p, d_jobs, njobs, s);
-      return shape.occ ? launch_k<4, true, false>(shape, p, d_jobs, njobs, s)
-                       : launch_k<4, false, false>(shape, p, d_jobs, njobs, s);
-    case 8:
-      if (shape.grid) return launch_k<8, false, true>(shape, p, d_jobs, njobs, s);
-      return launch_k<8, false, false>(shape, p, d_jobs, njobs, s);
-    case 16:
-      if (shape.grid) return launch_k<16, false, true>(shape, p, d_jobs, njobs, s);
-      return launch_k<16, false, false>(shape, p, d_jobs, njobs, s);
+    case 2: return launch_shape<2>(shape, p, d_jobs, njobs, s);
+    case 4: return launch_shape<4>(shape, p, d_jobs, njobs, s);
+    case 8: return launch_shape<8>(shape, p, d_jobs, njobs, s);
+    case 16: return launch_shape<16>(shape, p, d_jobs, njobs, s);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -215,8 +215,9 @@ class Batch:
                        for i in range(len(self))))
 
 
-def make_batch(spec_list: list[Spec], device="cpu") -> Batch:
-    """Generate every utterance into one packed [sum T, C] buffer."""
+def make_batch(spec_list: list[Spec], device="cpu", logits: bool = False) -> Batch:
+    """Generate every utterance into one packed [sum T, C] buffer (the raw
+    scores before log_softmax when logits=True)."""
     Cs = {s.C for s in spec_list}
     if len(Cs) != 1:
         raise ValueError("a packed batch needs one vocabulary size")
@@ -229,8 +230,11 @@ def make_batch(spec_list: list[Spec], device="cpu") -> Batch:
         rng = np.random.default_rng(s.seed)
         tg = make_targets(rng, s.L, s.C, s.repeat_frac)
         pl = plant_state_path(rng, s.T, tg)
-        emissions(s.seed, s.T, s.C, expand_tokens(tg)[pl], device=device,
-                  out=lp[int(offs[i]):int(offs[i + 1])])
+        if logits:
+            lp[int(offs[i]):int(offs[i + 1])].copy_(raw_logits(s.seed, s.T, s.C, expand_tokens(tg)[pl], device=device))
+        else:
+            emissions(s.seed, s.T, s.C, expand_tokens(tg)[pl], device=device,
+                      out=lp[int(offs[i]):int(offs[i + 1])])
         targets.append(tg)
         planted.append(pl)
     return Batch(lp=lp, offsets=offs, targets=targets, planted=planted, specs=spec_list)
