@@ -7,7 +7,10 @@ nothing from the product package.
 
 Contents:
   * ``viterbi.c``  -- plain C Viterbi over the CTC trellis, FP32 and FP64
-    (paper Sec. 4, "CTC-based forced alignment"; trellis of the cited CTC work).
+    (paper Sec. 4, "CTC-based forced alignment"; trellis of the cited CTC work),
+    and the sum-product forward score over the same trellis in FP64.
+  * ``spans.py``   -- token spans of an alignment (start, end, mean score).
+  * ``normalize.py`` -- per-frame log_softmax in FP64.
   * ``brute.py``   -- exhaustive enumeration of state paths for tiny inputs.
   * ``checks.py``  -- invariants: collapse, legal moves, fold sums, a max-plus
     backward pass, the FP32 summation error bound.
@@ -66,6 +69,8 @@ def _bind(lib: ctypes.CDLL) -> ctypes.CDLL:
     lib.oracle_viterbi_total_f32.restype = ctypes.c_int
     lib.oracle_viterbi_f64.argtypes = [p, i64, i64, p, i64, i32, p, p, p, p]
     lib.oracle_viterbi_f64.restype = ctypes.c_int
+    lib.oracle_ctc_forward_f64.argtypes = [p, i64, i64, p, i64, i32, p]
+    lib.oracle_ctc_forward_f64.restype = ctypes.c_int
     return lib
 
 
@@ -139,3 +144,13 @@ def viterbi_f64(lp, targets, blank: int = 0) -> dict:
     rc = lib().oracle_viterbi_f64(_ptr(lp), T, C, _ptr(tg), tg.size, int(blank), _ptr(path),
                                   _ptr(states), _ptr(scores), _ptr(total))
     return {"status": rc, "path": path, "states": states, "scores": scores, "total": total[0]}
+
+
+def ctc_forward_f64(lp, targets, blank: int = 0) -> dict:
+    """Sum-product over the same trellis (log-add in place of max), binary64:
+    the log of the total probability of the transcript's CTC paths."""
+    lp, tg = _prep(lp, targets)
+    T, C = lp.shape
+    total = np.zeros(1, np.float64)
+    rc = lib().oracle_ctc_forward_f64(_ptr(lp), T, C, _ptr(tg), tg.size, int(blank), _ptr(total))
+    return {"status": rc, "total": float(total[0])}

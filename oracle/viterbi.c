@@ -294,3 +294,53 @@ int oracle_viterbi_f64(const float *lp, int64_t T, int64_t C, const int32_t *tar
     free(bp);
     return (*total == -INFINITY) ? OR_E_NOPATH : OR_OK;
 }
+
+/*
+ * Sum-product variant (the same trellis with log-add in place of max): the
+ * log of the total probability of every CTC path that collapses to the
+ * transcript, the forward score of the CTC work the paper cites:
+ *   beta_0(0) = lp[0][blank], beta_0(1) = lp[0][ext[1]] (if L >= 1), else -inf;
+ *   beta_t(s) = log( exp beta_{t-1}(s) + exp beta_{t-1}(s-1)
+ *                    + [skip allowed] exp beta_{t-1}(s-2) ) + lp[t][ext[s]];
+ *   total = log( exp beta_{T-1}(S-1) + [S > 1] exp beta_{T-1}(S-2) ).
+ * In binary64 with the maximum factored out of each log-sum (log sum exp(x) =
+ * m + log sum exp(x - m)); a sum of only -inf terms is -inf.
+ */
+static double log_add3(double x, double y, double z) {
+    double m = x;
+    if (y > m) m = y;
+    if (z > m) m = z;
+    if (m == -INFINITY) return -INFINITY;
+    return m + log(exp(x - m) + exp(y - m) + exp(z - m));
+}
+
+int oracle_ctc_forward_f64(const float *lp, int64_t T, int64_t C, const int32_t *targets, int64_t L,
+                           int32_t blank, double *total) {
+    int64_t R, S = 2 * L + 1, t, s;
+    int rc = oracle_validate(targets, L, C, blank, T, &R);
+    double *prev, *cur, *tmp;
+    if (rc != OR_OK) return rc;
+    prev = (double *)malloc(sizeof(double) * S);
+    cur = (double *)malloc(sizeof(double) * S);
+    if (!prev || !cur) {
+        free(prev);
+        free(cur);
+        return OR_E_NOMEM;
+    }
+    for (s = 0; s < S; ++s) prev[s] = -INFINITY;
+    prev[0] = (double)lp[blank];
+    if (S > 1) prev[1] = (double)lp[ext_of(targets, blank, 1)];
+    for (t = 1; t < T; ++t) {
+        const float *row = lp + t * C;
+        for (s = 0; s < S; ++s) {
+            double a1 = (s >= 1) ? prev[s - 1] : -INFINITY;
+            double a2 = skip_allowed(targets, blank, s) ? prev[s - 2] : -INFINITY;
+            cur[s] = log_add3(prev[s], a1, a2) + (double)row[ext_of(targets, blank, s)];
+        }
+        tmp = prev, prev = cur, cur = tmp;
+    }
+    *total = log_add3(prev[S - 1], (S > 1) ? prev[S - 2] : -INFINITY, -INFINITY);
+    free(prev);
+    free(cur);
+    return (*total == -INFINITY) ? OR_E_NOPATH : OR_OK;
+}
