@@ -63,6 +63,7 @@ def parse():
     ap.add_argument("--workload", default="batch64", choices=sorted(WORKLOADS))
     ap.add_argument("--no-spans", action="store_true", help="skip the token-span leg")
     ap.add_argument("--no-logits", action="store_true", help="skip the fused log_softmax leg")
+    ap.add_argument("--no-sum", action="store_true", help="skip the sum-product (CTC forward) leg")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the CPU oracle baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
@@ -432,6 +433,35 @@ def main():
                        "logit_bytes": int(lb.lp.numel()) * 4}
         del lb, lp_buf
 
+    # Sum-product (ALIGN_REQ_SUM): the CTC forward score of every utterance of
+    # the same batch over the same trellis (log-add in place of the max, no
+    # backpointers, no backtrack), as one packed submit; device time.
+    sum_line = None
+    if not args.no_sum:
+        tg_pk = np.concatenate([np.asarray(t, np.int32) for t in batch.targets])
+        tgo_pk = np.concatenate([[0], np.cumsum(L_of)]).astype(np.int64)
+        tot_sum = torch.empty(n, dtype=torch.float32, device=dev)
+        su_times = []
+        for k in range(3 + args.steps):
+            flush_buf.fill_(1)
+            with torch.cuda.stream(stream):
+                torch.cuda._sleep(hold["cycles"])
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                pr = al.ctc_forward_packed(batch.lp, batch.offsets, tg_pk, tgo_pk, tot_sum)
+                al.flush()
+                al.join(stream)
+                e1.record(stream)
+            al.wait_packed(pr)
+            assert (pr.status == 0).all()
+            e1.synchronize()
+            if k >= 3:
+                su_times.append(e0.elapsed_time(e1))
+        su_ms = statistics.mean(su_times)
+        sum_line = {"ms": su_ms, "cells_per_s": cells / (su_ms / 1e3), "viterbi_ms": ms,
+                    "note": "log-add (max factored out, __expf/__logf) in place of the max; total only"}
+
     # Plain: one synchronous submit + poll per utterance (at most 256 utterances).
     plain = None
     if not args.no_plain:
@@ -564,6 +594,7 @@ def main():
         "serving": serving,
         "token_spans": spans_line,
         "logits": logits_line,
+        "ctc_forward": sum_line,
         "cpu_baseline": cpu,
         "clocks": clk.summary(),
     }

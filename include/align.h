@@ -124,6 +124,14 @@ int align_submit_host(align_ctx *ctx, const float *log_probs, int64_t T, int64_t
 
 /* One request of a batch submission. */
 #define ALIGN_REQ_HOST 0x1u  /* log_probs and out.* are HOST pointers (as align_submit_host) */
+#define ALIGN_REQ_SUM 0x4u    /* sum-product instead of Viterbi: the same trellis with log-add in
+                                 place of max (the forward score of the CTC work the paper cites);
+                                 out.total = log of the total probability of every CTC path of the
+                                 transcript (minus the CTC loss); out.path / scores / states are not
+                                 used (may be NULL). FP32 with the fast exponential / logarithm
+                                 intrinsics, the maximum factored out of every log-add; no
+                                 backpointers (no backpointer memory). Not combined with
+                                 ALIGN_REQ_LOGITS (ALIGN_E_INVAL). */
 #define ALIGN_REQ_LOGITS 0x2u /* log_probs holds raw per-frame scores (logits): the kernel
                                  applies log_softmax over each row as it stages it (one extra
                                  warp per CTA: lse = m + logf(sum expf(x - m)), m the row
@@ -185,6 +193,8 @@ typedef struct {
     uint64_t checkpointed;      /* requests that ran with checkpointed recompute */
     uint64_t bp_bytes_peak;     /* peak arena use */
     uint64_t throughput_batches; /* batches planned with the throughput tuning table */
+    uint64_t grid_teams;        /* finished requests that ran as a grid team */
+    uint64_t sum_requests;      /* finished sum-product (ALIGN_REQ_SUM) requests */
 } align_stats;
 
 int align_get_stats(align_ctx *ctx, align_stats *out, int32_t reset);

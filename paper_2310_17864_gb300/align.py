@@ -59,6 +59,7 @@ class AlignOut(ctypes.Structure):
 
 ALIGN_REQ_HOST = 0x1
 ALIGN_REQ_LOGITS = 0x2   # log_probs holds raw logits: log_softmax is applied inside the kernel
+ALIGN_REQ_SUM = 0x4      # sum-product forward score (total only) instead of the Viterbi alignment
 
 
 class AlignRequest(ctypes.Structure):
@@ -71,7 +72,8 @@ class AlignStats(ctypes.Structure):
     _fields_ = [("kernel_launches", ctypes.c_uint64), ("graph_launches", ctypes.c_uint64),
                 ("requests_done", ctypes.c_uint64), ("cells", ctypes.c_uint64),
                 ("checkpointed", ctypes.c_uint64), ("bp_bytes_peak", ctypes.c_uint64),
-                ("throughput_batches", ctypes.c_uint64)]
+                ("throughput_batches", ctypes.c_uint64), ("grid_teams", ctypes.c_uint64),
+                ("sum_requests", ctypes.c_uint64)]
 
 
 class AlignPlanInfo(ctypes.Structure):
@@ -552,6 +554,51 @@ class Aligner:
             return None
         target.status = code
         return target
+
+    def ctc_forward_packed(self, log_probs, offsets, targets, target_offsets, total, blank: int = 0,
+                           host: bool = False) -> PackedResult:
+        """Sum-product forward scores of a packed batch (ALIGN_REQ_SUM): total[i]
+        = log of the total probability of utterance i's transcript (minus its
+        CTC loss). Same packing as submit_packed; no path or scores outputs."""
+        offsets = np.asarray(offsets, dtype=np.int64)
+        target_offsets = np.asarray(target_offsets, dtype=np.int64)
+        tg = _i32(targets)
+        n = offsets.size - 1
+        T, C = log_probs.shape
+        if offsets[-1] != T or target_offsets.size != n + 1 or total.numel() < n:
+            raise ValueError("offsets / target_offsets do not match the packed tensors")
+        f0 = offsets[:-1].astype(np.uint64)
+        reqs = np.zeros(n, dtype=_REQ_DTYPE)
+        reqs["lp"] = np.uint64(log_probs.data_ptr()) + f0 * np.uint64(4 * C)
+        reqs["T"] = np.diff(offsets)
+        reqs["C"] = C
+        reqs["tg"] = np.uint64(tg.ctypes.data) + target_offsets[:-1].astype(np.uint64) * np.uint64(4)
+        reqs["L"] = np.diff(target_offsets)
+        reqs["blank"] = blank
+        reqs["flags"] = ALIGN_REQ_SUM | (ALIGN_REQ_HOST if host else 0)
+        reqs["total"] = np.uint64(total.data_ptr()) + np.arange(n, dtype=np.uint64) * np.uint64(4)
+        ids, st = align_submit_batch(self.ctx, reqs)
+        ids = np.asarray(ids, dtype=np.uint64)
+        st = np.asarray(st, dtype=np.int32)
+        if (st < 0).any():
+            raise AlignError(int(st[st < 0][0]), "align_submit_batch")
+        res = PackedResult(ids, np.full(n, ALIGN_PENDING, dtype=np.int32), (log_probs, tg, total))
+        for i, rid in enumerate(ids.tolist()):
+            self._live[rid] = (None, (res, i))
+        return res
+
+    def ctc_forward(self, log_probs, targets, blank: int = 0) -> tuple[int, float]:
+        """Sum-product forward score of one utterance: (status, log total probability)."""
+        dev = log_probs.is_cuda
+        total = self.torch.empty(1, dtype=self.torch.float32, device=log_probs.device if dev else "cpu")
+        if not dev:
+            total = total.pin_memory()
+        tg = _i32(targets)
+        res = self.ctc_forward_packed(log_probs.contiguous(), [0, log_probs.shape[0]], tg, [0, tg.size], total,
+                                      blank, host=not dev)
+        self.flush()
+        self.wait_packed(res)
+        return int(res.status[0]), float(total.cpu()[0])
 
     def wait_packed(self, res: PackedResult) -> None:
         """Block until every request of a packed batch is done; fills res.status."""

@@ -139,6 +139,7 @@ struct Request {
   const void* lp_alias = nullptr;
   align_out out_alias{};
   bool logits = false;  // lp holds raw logits (ALIGN_REQ_LOGITS)
+  bool sum = false;     // sum-product forward score only (ALIGN_REQ_SUM)
   align_out out{};            // caller outputs (device or host)
   int64_t T = 0, C = 0, L = 0;
   int32_t blank = 0;
@@ -223,11 +224,19 @@ uint64_t inflight_count(const align_ctx* ctx) { return ctx->reqs.size(); }
 // Plan of a request with one tuning table. Logits requests get a normaliser
 // warp per CTA (so at most 15 compute warps) and a per-frame shift buffer.
 int plan_request(const align_ctx* ctx, const TuneTable& table, int64_t T, int64_t C, int64_t L, bool logits,
-                 Plan* out) {
+                 Plan* out, bool sum = false) {
   TuneTable t = table;
   if (logits) t.max_warps = std::min(t.max_warps, 15);
-  const int rc = make_plan(t, T, C, L, ctx->bp_arena.cap(), (ctx->flags & ALIGN_F_FORCE_CHECKPOINT) != 0, out);
+  const int rc = make_plan(t, T, C, L, sum ? ~0ull : ctx->bp_arena.cap(),
+                           !sum && (ctx->flags & ALIGN_F_FORCE_CHECKPOINT) != 0, out);
   if (rc != ALIGN_OK) return rc;
+  if (sum) {  // the forward pass only: no backpointers, anchor rows or checkpoints
+    out->shape.sum = 1;
+    out->checkpointed = false;
+    out->bp_bytes = 0;
+    out->z_off = 0;
+    if (plan_device_bytes(*out) > ctx->bp_arena.cap()) return ALIGN_E_TOO_LARGE;
+  }
   if (logits) {
     out->shape.norm = 1;
     out->lse_bytes = (static_cast<uint64_t>(T) * 4 + 255) & ~255ull;
@@ -276,6 +285,8 @@ int finish_batch(align_ctx* ctx, Batch& b) {
     ctx->stats.requests_done++;
     ctx->stats.cells += static_cast<uint64_t>(r.T) * static_cast<uint64_t>(2 * r.L + 1);
     if (r.plan.checkpointed) ctx->stats.checkpointed++;
+    if (r.plan.shape.grid) ctx->stats.grid_teams++;
+    if (r.sum) ctx->stats.sum_requests++;
   }
   if (b.meta.live) ctx->meta_arena.release(b.meta.off, b.meta.bytes), b.meta.live = false;
   if (b.pinned.live) ctx->pinned_arena.release(b.pinned.off, b.pinned.bytes), b.pinned.live = false;
@@ -330,7 +341,7 @@ bool choose_tables(align_ctx* ctx) {
     Request& r = ctx->reqs.at(id);
     if (r.plan_table == want) continue;
     Plan p{};
-    if (plan_request(ctx, tp ? ctx->tune_tp : ctx->tune, r.T, r.C, r.L, r.logits, &p) == ALIGN_OK) {
+    if (plan_request(ctx, tp ? ctx->tune_tp : ctx->tune, r.T, r.C, r.L, r.logits, &p, r.sum) == ALIGN_OK) {
       p.shape.occ = tp ? 1 : 0;
       r.plan = p;
       r.plan_table = want;
@@ -405,7 +416,7 @@ int launch_queued(align_ctx* ctx) {
   // get 1 + nck descriptors each.
   // (K, warps, ncta, F, C) -> request indices. C is part of the key: the launch
   // parameters (emission stage size) depend on it.
-  std::map<std::tuple<int, int, int, int, int, int, int>, std::vector<int>> groups;
+  std::map<std::tuple<int, int, int, int, int, int, int, int>, std::vector<int>> groups;
   size_t njobs = 0;
   for (size_t i = 0; i < take.size(); ++i) {
     const Plan& p = take[i]->plan;
@@ -413,7 +424,7 @@ int launch_queued(align_ctx* ctx) {
       njobs += p.checkpointed ? 1 + static_cast<size_t>(p.nck) : 1;
     } else {
       groups[{p.shape.K, p.shape.warps, p.shape.ncta, p.frames_per_stage, static_cast<int>(take[i]->C), p.shape.occ,
-              p.shape.norm}].push_back(
+              p.shape.norm, p.shape.sum}].push_back(
           static_cast<int>(i));
       njobs += 1;
     }
@@ -453,13 +464,13 @@ int launch_queued(align_ctx* ctx) {
     for (auto& kv : groups) {
       key.insert(key.end(), {std::get<0>(kv.first), std::get<1>(kv.first), std::get<2>(kv.first),
                              std::get<3>(kv.first), std::get<4>(kv.first), std::get<5>(kv.first),
-                             std::get<6>(kv.first), static_cast<int64_t>(kv.second.size())});
+                             std::get<6>(kv.first), std::get<7>(kv.first), static_cast<int64_t>(kv.second.size())});
     }
     for (auto* r : take) {
       const Plan& p = r->plan;
       if (!p.checkpointed && !p.shape.grid) continue;
       key.insert(key.end(), {-1, p.shape.K, p.shape.warps, p.shape.ncta, p.shape.occ, p.shape.grid, p.shape.norm,
-                             p.frames_per_stage, p.checkpointed ? p.nck : -1, r->C});
+                             p.shape.sum, p.frames_per_stage, p.checkpointed ? p.nck : -1, r->C});
     }
     for (size_t k = 0; k < ctx->graphs.size(); ++k)
       if (ctx->graphs[k].key == key) gi = static_cast<int>(k);
@@ -622,8 +633,8 @@ int launch_queued(align_ctx* ctx) {
     if (!r.host_io || !r.lp_alias) return;
     const uint64_t T = static_cast<uint64_t>(r.T);
     add_chunks(hh2d, ih2d, r.lp_alias, const_cast<float*>(req_lp[i]), T * static_cast<uint64_t>(r.C) * 4);
-    add_chunks(hd2h, id2h, req_out[i].path, r.out_alias.path, T * 4);
-    add_chunks(hd2h, id2h, req_out[i].scores, r.out_alias.scores, T * 4);
+    if (r.out.path) add_chunks(hd2h, id2h, req_out[i].path, r.out_alias.path, T * 4);
+    if (r.out.scores) add_chunks(hd2h, id2h, req_out[i].scores, r.out_alias.scores, T * 4);
     add_chunks(hd2h, id2h, req_out[i].total, r.out_alias.total, 4);
     if (r.out.states) add_chunks(hd2h, id2h, req_out[i].states, r.out_alias.states, T * 4);
     cr.in_count = ih2d - cr.in_first;
@@ -650,6 +661,7 @@ int launch_queued(align_ctx* ctx) {
     GroupLaunch gl{};
     gl.shape = LaunchShape{std::get<0>(kv.first), std::get<1>(kv.first), std::get<2>(kv.first), std::get<5>(kv.first)};
     gl.shape.norm = std::get<6>(kv.first);
+    gl.shape.sum = std::get<7>(kv.first);
     gl.F = std::get<3>(kv.first);
     gl.first = jn;
     gl.count = kv.second.size();
@@ -661,13 +673,13 @@ int launch_queued(align_ctx* ctx) {
       const Request& r = *take[static_cast<size_t>(i)];
       gl.t_max = std::max(gl.t_max, r.T);
       FwdJob j = base_job(static_cast<size_t>(i));
-      j.bp = reinterpret_cast<uint32_t*>(ctx->d_bp + r.bp.off);
-      j.ztab = reinterpret_cast<uint8_t*>(ctx->d_bp + r.bp.off + r.plan.z_off);
+      j.bp = r.sum ? nullptr : reinterpret_cast<uint32_t*>(ctx->d_bp + r.bp.off);
+      j.ztab = r.sum ? nullptr : reinterpret_cast<uint8_t*>(ctx->d_bp + r.bp.off + r.plan.z_off);
       j.zstride = r.plan.zstride;
       j.t_begin = 0;
       j.t_end = j.T;
       j.bp_rows = std::max(j.T - 1, 0);
-      j.flags |= kJobWriteFinal | kJobChase;
+      j.flags |= kJobWriteFinal | (r.sum ? 0u : kJobChase);
       hjobs[jn++] = j;
     }
     glaunch.push_back(gl);
@@ -685,15 +697,15 @@ int launch_queued(align_ctx* ctx) {
     cl.cr.in_first = ih2d;
     cl.cr.out_first = id2h;
     add_request_chunks(i, cl.cr);
-    if (!p.checkpointed) {  // grid team, full backpointers
+    if (!p.checkpointed) {  // grid team, full backpointers (none for the sum-product)
       FwdJob j = base_job(i);
-      j.bp = reinterpret_cast<uint32_t*>(ctx->d_bp + r.bp.off);
-      j.ztab = reinterpret_cast<uint8_t*>(ctx->d_bp + r.bp.off + p.z_off);
+      j.bp = r.sum ? nullptr : reinterpret_cast<uint32_t*>(ctx->d_bp + r.bp.off);
+      j.ztab = r.sum ? nullptr : reinterpret_cast<uint8_t*>(ctx->d_bp + r.bp.off + p.z_off);
       j.zstride = p.zstride;
       j.t_begin = 0;
       j.t_end = j.T;
       j.bp_rows = std::max(j.T - 1, 0);
-      j.flags |= kJobWriteFinal | kJobChase;
+      j.flags |= kJobWriteFinal | (r.sum ? 0u : kJobChase);
       j.xlink = xl;
       hjobs[jn++] = j;
       cklaunch.push_back(cl);
@@ -840,8 +852,8 @@ int launch_queued(align_ctx* ctx) {
     Request& r = *take[i];
     if (!r.host_io || r.lp_alias) continue;
     const size_t T = static_cast<size_t>(r.T);
-    CU(cudaMemcpyAsync(r.out.path, req_out[i].path, T * 4, cudaMemcpyDeviceToHost, s0));
-    CU(cudaMemcpyAsync(r.out.scores, req_out[i].scores, T * 4, cudaMemcpyDeviceToHost, s0));
+    if (r.out.path) CU(cudaMemcpyAsync(r.out.path, req_out[i].path, T * 4, cudaMemcpyDeviceToHost, s0));
+    if (r.out.scores) CU(cudaMemcpyAsync(r.out.scores, req_out[i].scores, T * 4, cudaMemcpyDeviceToHost, s0));
     CU(cudaMemcpyAsync(r.out.total, req_out[i].total, 4, cudaMemcpyDeviceToHost, s0));
     if (r.out.states) CU(cudaMemcpyAsync(r.out.states, req_out[i].states, T * 4, cudaMemcpyDeviceToHost, s0));
   }
@@ -905,8 +917,11 @@ int pump(align_ctx* ctx, bool launch) {
 }
 
 int submit_common(align_ctx* ctx, const float* lp, int64_t T, int64_t C, const int32_t* targets, int64_t L,
-                  int32_t blank, align_out out, uint64_t* request_id, bool host_io, bool logits = false) {
-  if (!ctx || !lp || !request_id || !out.path || !out.scores || !out.total) return ALIGN_E_INVAL;
+                  int32_t blank, align_out out, uint64_t* request_id, bool host_io, bool logits = false,
+                  bool sum = false) {
+  if (!ctx || !lp || !request_id || !out.total || (!sum && (!out.path || !out.scores))) return ALIGN_E_INVAL;
+  if (sum && logits) return ALIGN_E_INVAL;  // the sum-product path takes log-probabilities
+  if (sum) out.path = nullptr, out.scores = nullptr, out.states = nullptr;
   if (L > 0 && !targets) return ALIGN_E_INVAL;
   // Frame tags in the ring words have 24 bits; 2^24 frames of 20 ms are 93 hours.
   if (T >= (1ll << kTagBits) || L > INT32_MAX / 4) return ALIGN_E_TOO_LARGE;
@@ -919,10 +934,11 @@ int submit_common(align_ctx* ctx, const float* lp, int64_t T, int64_t C, const i
     if (static_cast<int64_t>(inflight_count(ctx)) >= ctx->max_inflight) return ALIGN_E_AGAIN;
   }
   Plan p{};
-  rc = plan_request(ctx, ctx->tune, T, C, L, logits, &p);
+  rc = plan_request(ctx, ctx->tune, T, C, L, logits, &p, sum);
   if (rc != ALIGN_OK) return rc;
   Request r;
   r.logits = logits;
+  r.sum = sum;
   if (host_io) {
     align_out al{};
     const void* la = device_alias(ctx, lp);
@@ -930,7 +946,7 @@ int submit_common(align_ctx* ctx, const float* lp, int64_t T, int64_t C, const i
     al.scores = static_cast<float*>(device_alias(ctx, out.scores));
     al.total = static_cast<float*>(device_alias(ctx, out.total));
     al.states = out.states ? static_cast<int32_t*>(device_alias(ctx, out.states)) : nullptr;
-    if (la && al.path && al.scores && al.total && (!out.states || al.states)) {
+    if (la && (al.path || !out.path) && (al.scores || !out.scores) && al.total && (!out.states || al.states)) {
       r.lp_alias = la;
       r.out_alias = al;
     }
@@ -1080,10 +1096,11 @@ int align_submit_batch(align_ctx* ctx, int32_t n, const align_request* reqs, uin
   int first_err = ALIGN_OK;
   for (int32_t i = 0; i < n; ++i) {
     const align_request& q = reqs[i];
-    int rc = (q.flags & ~(ALIGN_REQ_HOST | ALIGN_REQ_LOGITS))
+    int rc = (q.flags & ~(ALIGN_REQ_HOST | ALIGN_REQ_LOGITS | ALIGN_REQ_SUM))
                  ? ALIGN_E_INVAL
                  : submit_common(ctx, q.log_probs, q.T, q.C, q.targets, q.L, q.blank, q.out, &request_ids[i],
-                                 (q.flags & ALIGN_REQ_HOST) != 0, (q.flags & ALIGN_REQ_LOGITS) != 0);
+                                 (q.flags & ALIGN_REQ_HOST) != 0, (q.flags & ALIGN_REQ_LOGITS) != 0,
+                                 (q.flags & ALIGN_REQ_SUM) != 0);
     if (rc != ALIGN_OK) request_ids[i] = 0;
     if (submit_status) submit_status[i] = rc;
     if (rc != ALIGN_OK && first_err == ALIGN_OK) first_err = rc;

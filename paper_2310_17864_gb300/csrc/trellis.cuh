@@ -113,6 +113,7 @@ struct LaunchShape {
   int grid = 0;            // 1: the team is ncta CTAs of one cooperative launch, one per SM,
                            // linked through global memory (transcripts beyond a cluster)
   int norm = 0;            // 1: inputs are raw logits: CTAs get a normaliser warp (warps <= 15)
+  int sum = 0;             // 1: sum-product forward score only (log-add in place of max)
 };
 
 // Bytes of the global links of a grid team of ncta CTAs: a ring of kMaxRing

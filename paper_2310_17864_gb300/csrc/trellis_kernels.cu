@@ -345,6 +345,18 @@ __device__ void log_softmax_shifts(const float* rows, int nf, int C, int lane, f
   }
 }
 
+// log(exp x + exp y) and log(exp x + exp y + exp z) in FP32 with the maximum
+// factored out (fast exponential and logarithm intrinsics; a sum of -inf
+// terms only is -inf).
+__device__ __forceinline__ float log_add2(float x, float y) {
+  const float m = fmaxf(x, y);
+  return (m == -INFINITY) ? -INFINITY : m + __logf(__expf(x - m) + __expf(y - m));
+}
+__device__ __forceinline__ float log_add3(float x, float y, float z) {
+  const float m = fmaxf(fmaxf(x, y), z);
+  return (m == -INFINITY) ? -INFINITY : m + __logf(__expf(x - m) + __expf(y - m) + __expf(z - m));
+}
+
 // One backpointer row (NW = 3 or 6 words) stored by the lane that buffered it.
 template <int K, int NWB>
 __device__ __forceinline__ void store_bp_row(uint32_t* dst, const uint32_t (&w)[NWB]) {
@@ -370,7 +382,11 @@ __device__ __forceinline__ void store_bp_row(uint32_t* dst, const uint32_t (&w)[
 // kNorm: log_probs hold raw logits; each CTA has one more warp, the
 // normaliser (a separate instantiation so the log-probability path keeps its
 // own code).
-template <int K, bool kOcc, bool kGrid, bool kNorm>
+//
+// kSum: the sum-product variant: log-add in place of the max (no
+// backpointers, anchors or backtrack); the job's total is the log-add of the
+// two final states.
+template <int K, bool kOcc, bool kGrid, bool kNorm, bool kSum>
 __global__ void __launch_bounds__(512, (kOcc && K <= 4) ? 2 : 1)
     trellis_kernel(const FwdJob* __restrict__ jobs, const FwdParams P) {
   static_assert(K % 2 == 0 && K >= 2 && K <= 16, "K must be even, 2..16");
@@ -795,10 +811,25 @@ __global__ void __launch_bounds__(512, (kOcc && K <= 4) ? 2 : 1)
 
       // alpha_{t-1}(s0 - 1) and its anchor: lane below by shuffle, lane 0 from the block.
       const float shf = __shfl_up_sync(kFull, a[K - 1], 1);
-      const int shA = __shfl_up_sync(kFull, A[K - 1], 1);
       const float blk = __shfl_sync(kFull, rv, bi + i);
-      const int blko = __shfl_sync(kFull, roff, bi + i);
       const float left = is_l0 ? blk : shf;
+      if constexpr (kSum) {  // sum-product: log-add of the allowed predecessors
+#pragma unroll
+        for (int j = K - 1; j >= 0; --j) {  // descending: a[j-1], a[j-2] still hold frame t-1
+          const float p1 = (j == 0) ? left : a[j - 1];
+          if ((j & 1) == 0) {
+            a[j] = log_add2(a[j], p1) + eb;
+          } else {
+            const float p2raw = (j == 1) ? left : a[j - 2];
+            const float p2 = __uint_as_float((__float_as_uint(p2raw) & skeep[j >> 1]) | sfill[j >> 1]);
+            a[j] = log_add3(a[j], p1, p2) + el[j >> 1];
+          }
+        }
+        send_one(t, a[K - 1], s_last);
+        continue;
+      }
+      const int shA = __shfl_up_sync(kFull, A[K - 1], 1);
+      const int blko = __shfl_sync(kFull, roff, bi + i);
       const int Aleft = is_l0 ? (s0 - 1 - blko) : shA;
       if constexpr (!kBufBp) store_bp_words_if<K>(bpw - NW, padv, pskp, write_bp && pend);
 
@@ -904,7 +935,7 @@ __global__ void __launch_bounds__(512, (kOcc && K <= 4) ? 2 : 1)
       const float f_blank = __ldcg(J.final2 + 1);
       const float f_lab = (S > 1) ? __ldcg(J.final2 + 0) : -INFINITY;
       s_cur = (S > 1 && f_lab > f_blank) ? S - 2 : S - 1;
-      const float tot = (S > 1 && f_lab > f_blank) ? f_lab : f_blank;
+      const float tot = kSum ? log_add2(f_lab, f_blank) : ((S > 1 && f_lab > f_blank) ? f_lab : f_blank);
       if (lane == 0) {
         if (J.total) *J.total = tot;
         atomicCAS(J.status, kStPending, tot == -INFINITY ? kStNoPath : kStOk);
@@ -1048,7 +1079,7 @@ __global__ void __launch_bounds__(1024) frame_probe_kernel(int frames, uint64_t 
   }
 }
 
-template <int K, bool kOcc, bool kGrid, bool kNorm>
+template <int K, bool kOcc, bool kGrid, bool kNorm, bool kSum = false>
 cudaError_t launch_k(const LaunchShape& shape, const FwdParams& p, const FwdJob* d_jobs, int njobs,
                      cudaStream_t stream) {
   int dev = 0;
@@ -1062,7 +1093,7 @@ cudaError_t launch_k(const LaunchShape& shape, const FwdParams& p, const FwdJob*
     smem = std::max(smem, smem_max);
     if (njobs != 1) return cudaErrorInvalidValue;  // one team per cooperative launch
   }
-  auto fn = trellis_kernel<K, kOcc, kGrid, kNorm>;
+  auto fn = trellis_kernel<K, kOcc, kGrid, kNorm, kSum>;
   // The allowed maximum is always the device's opt-in limit, never the size
   // of the launch at hand: launches of one kernel captured into a graph ask
   // for different sizes, and none may see a limit lowered by another.
@@ -1100,6 +1131,11 @@ cudaError_t launch_k(const LaunchShape& shape, const FwdParams& p, const FwdJob*
 template <int K>
 cudaError_t launch_shape(const LaunchShape& shape, const FwdParams& p, const FwdJob* d_jobs, int njobs,
                          cudaStream_t s) {
+  if (shape.sum) {
+    if (shape.norm) return cudaErrorInvalidValue;  // not built: sum-product takes log-probabilities
+    if (shape.grid) return launch_k<K, false, true, false, true>(shape, p, d_jobs, njobs, s);
+    return launch_k<K, false, false, false, true>(shape, p, d_jobs, njobs, s);
+  }
   if (shape.norm) {
     if (shape.grid) return launch_k<K, false, true, true>(shape, p, d_jobs, njobs, s);
     return launch_k<K, false, false, true>(shape, p, d_jobs, njobs, s);

@@ -1,0 +1,174 @@
+"""GPU parity of the sum-product variant (ALIGN_REQ_SUM): the CTC forward
+score over the same trellis, with log-add in place of the max.
+
+Tolerance. The kernel works in FP32: every cell is m + log(1 + e^(d1) + e^(d2))
+(m the largest predecessor, d <= 0) followed by one add of the emission. With
+__expf (relative error at most 2 + 1.173|d| ulp, so at most 2 ulp weighted by
+e^d) and __logf (absolute error at most 2^-21.41 on [0.5, 2], 3 ulp above), one
+log-add term is off by at most 2^-20 in absolute terms, and the two FP32 adds
+by 2^-24 of |alpha| each. The log-sum-exp is a convex combination in its
+inputs (its partial derivatives are non-negative and sum to one), so errors
+carried from frame t-1 do not grow: after frame t the error is at most
+err_{t-1} + 2^-23 A_t + 2^-20, where A_t = sum over tau <= t of
+max_c |lp[tau, c]| bounds every finite |alpha_t(s)|. The final log-add of
+the two end states adds one more term. The test uses that bound, summed over
+the frames, against the binary64 oracle.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2310_17864_gb300 import align, build, synth
+
+pytestmark = pytest.mark.gpu
+
+
+def tolerance(lp: np.ndarray) -> float:
+    m = np.abs(np.where(np.isfinite(lp), lp, 0.0)).max(axis=1).astype(np.float64)
+    A = np.cumsum(m)
+    return float(np.sum(2.0 ** -23 * A + 2.0 ** -20) + 2.0 ** -23 * A[-1] + 2.0 ** -20)
+
+
+def check(status, total, lp, targets, blank, label=""):
+    o = oracle.ctc_forward_f64(lp, np.asarray(targets, np.int32), blank)
+    assert status == o["status"], (label, status, o["status"])
+    if o["status"] != 0:
+        assert total == -np.inf, (label, total)
+        return o
+    tol = tolerance(lp)
+    assert abs(total - o["total"]) <= tol, (label, total, o["total"], tol)
+    return o
+
+
+@pytest.fixture(scope="module")
+def al():
+    build.build()
+    a = align.Aligner(device=0, batched=True, bp_budget_bytes=4 << 30)
+    yield a
+    a.close()
+
+
+def packed(us, device="cuda"):
+    lp = torch.cat([u.lp for u in us]).contiguous()
+    offsets = np.concatenate([[0], np.cumsum([u.lp.shape[0] for u in us])])
+    tg = np.concatenate([np.asarray(u.targets, np.int32) for u in us] + [np.zeros(0, np.int32)])
+    tg_off = np.concatenate([[0], np.cumsum([len(u.targets) for u in us])])
+    return lp.to(device), offsets, tg, tg_off
+
+
+@pytest.mark.parametrize("T,C,L", [
+    (1, 2, 0), (1, 4, 1), (2, 2, 1), (3, 3, 2), (7, 5, 3), (50, 2, 1), (64, 32, 0),
+    (300, 32, 63), (300, 32, 64), (900, 32, 255), (900, 32, 256), (3000, 32, 1023),
+    (3000, 32, 1024), (400, 29, 90), (333, 3, 100), (2000, 500, 400),
+])
+def test_shapes(al, T, C, L):
+    u = synth.make_utterance(T * 37 + L, T, C, L, repeat_frac=0.1)
+    st, tot = al.ctc_forward(u.lp.cuda(), u.targets, 0)
+    check(st, tot, u.lp.numpy(), u.targets, 0, f"T{T}C{C}L{L}")
+
+
+def test_packed_batch_device_and_host(al):
+    """A ragged packed batch (device and pinned host buffers): every total
+    within the bound of the oracle's, one request per utterance."""
+    specs = synth.specs(4, C=32, n=24)
+    us = [synth.make_utterance(s.seed, s.T, s.C, s.L, s.repeat_frac) for s in specs]
+    for host in (False, True):
+        lp, off, tg, tg_off = packed(us, "cpu" if host else "cuda")
+        if host:
+            lp = lp.pin_memory()
+            total = torch.empty(len(us), dtype=torch.float32).pin_memory()
+        else:
+            total = torch.empty(len(us), dtype=torch.float32, device="cuda")
+        pr = al.ctc_forward_packed(lp, off, tg, tg_off, total, host=host)
+        al.flush()
+        al.wait_packed(pr)
+        tt = total.cpu().numpy()
+        for i, u in enumerate(us):
+            check(int(pr.status[i]), float(tt[i]), u.lp.numpy(), u.targets, 0, f"host{host}utt{i}")
+
+
+@pytest.mark.parametrize("K,cw", [(2, 1), (2, 16), (4, 4), (8, 4), (16, 2)])
+def test_launch_shapes(K, cw):
+    """Every (states per lane, warps per CTA) shape, clusters of one-warp CTAs
+    included, and wide rows (C = 500)."""
+    build.build()
+    a = align.Aligner(device=0, bp_budget_bytes=4 << 30)
+    try:
+        a.set_tuning(K, cw, 16)
+        for (T, C, L, seed) in [(700, 32, 300, 11), (333, 500, 120, 12), (95, 29, 40, 13), (1200, 32, 500, 15)]:
+            u = synth.make_utterance(seed * 1000 + K * 10 + cw, T, C, L, repeat_frac=0.1)
+            st, tot = a.ctc_forward(u.lp.cuda(), u.targets, 0)
+            check(st, tot, u.lp.numpy(), u.targets, 0, f"K{K}cw{cw}T{T}C{C}")
+    finally:
+        a.close()
+
+
+def test_grid_team():
+    """With clusters limited to one CTA, a transcript beyond one CTA runs as a
+    grid team of one-warp CTAs linked through global memory."""
+    build.build()
+    a = align.Aligner(device=0, bp_budget_bytes=4 << 30)
+    try:
+        a.set_tuning(4, 1, 1)
+        for (T, L, seed) in [(1500, 700, 3), (600, 290, 4)]:
+            u = synth.make_utterance(seed, T, 32, L, repeat_frac=0.1)
+            st, tot = a.ctc_forward(u.lp.cuda(), u.targets, 0)
+            check(st, tot, u.lp.numpy(), u.targets, 0, f"grid T{T}")
+        stt = a.stats()
+        assert stt["grid_teams"] == 2 and stt["sum_requests"] == 2, stt
+    finally:
+        a.close()
+
+
+def test_minus_inf_and_nopath(al):
+    """-inf emissions prune paths; when none is left the status is no-path
+    and the total -inf, as in the oracle."""
+    rng = np.random.default_rng(9)
+    lp = rng.standard_normal((40, 6)).astype(np.float32)
+    lp[rng.random(lp.shape) < 0.3] = -np.inf
+    tg = np.array([1, 2, 3], np.int32)
+    st, tot = al.ctc_forward(torch.from_numpy(lp).cuda(), tg, 0)
+    check(st, tot, lp, tg, 0, "pruned")
+    lp2 = rng.standard_normal((10, 6)).astype(np.float32)
+    lp2[4, :] = -np.inf
+    st, tot = al.ctc_forward(torch.from_numpy(lp2).cuda(), tg, 0)
+    assert st == align.ALIGN_E_NOPATH and tot == -np.inf
+
+
+def test_sum_and_viterbi_in_one_batch(al):
+    """Sum-product and Viterbi requests of one flush run as separate shape
+    groups: each result equals the oracle's."""
+    us = [synth.make_utterance(70 + i, 400 + 50 * i, 32, 100 + 20 * i) for i in range(6)]
+    lp, off, tg, tg_off = packed(us)
+    TT, n = int(off[-1]), len(us)
+    tot_sum = torch.empty(n, dtype=torch.float32, device="cuda")
+    out = (torch.empty(TT, dtype=torch.int32, device="cuda"), torch.empty(TT, device="cuda"),
+           torch.empty(n, device="cuda"), torch.empty(TT, dtype=torch.int32, device="cuda"))
+    p1 = al.ctc_forward_packed(lp, off, tg, tg_off, tot_sum)
+    p2 = al.submit_packed(lp, off, tg, tg_off, out)
+    al.flush()
+    al.wait_packed(p1)
+    al.wait_packed(p2)
+    for i, u in enumerate(us):
+        check(int(p1.status[i]), float(tot_sum[i].item()), u.lp.numpy(), u.targets, 0, f"sum{i}")
+        o = oracle.viterbi_f32(u.lp.numpy(), np.asarray(u.targets, np.int32), 0)
+        f0, f1 = int(off[i]), int(off[i + 1])
+        assert np.array_equal(out[0][f0:f1].cpu().numpy(), o["path"])
+        assert np.float32(out[2][i].item()).tobytes() == np.float32(o["total"]).tobytes()
+        assert tot_sum[i].item() >= out[2][i].item()  # the sum is at least its largest term
+
+
+def test_logits_flag_rejected(al):
+    """The sum-product takes log-probabilities only."""
+    u = synth.make_utterance(5, 50, 8, 5)
+    reqs = np.zeros(1, dtype=align._REQ_DTYPE)
+    tg = np.asarray(u.targets, np.int32)
+    lp = u.lp.cuda()
+    total = torch.empty(1, device="cuda")
+    reqs["lp"], reqs["T"], reqs["C"], reqs["tg"], reqs["L"] = lp.data_ptr(), 50, 8, tg.ctypes.data, tg.size
+    reqs["flags"] = align.ALIGN_REQ_SUM | align.ALIGN_REQ_LOGITS
+    reqs["total"] = total.data_ptr()
+    with pytest.raises(align.AlignError) as e:
+        align.align_submit_batch(al.ctx, reqs)
+    assert e.value.code == align.ALIGN_E_INVAL
