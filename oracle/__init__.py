@@ -11,6 +11,8 @@ Contents:
     and the sum-product forward score over the same trellis in FP64.
   * ``spans.py``   -- token spans of an alignment (start, end, mean score).
   * ``normalize.py`` -- per-frame log_softmax in FP64.
+  * ``beam.py``    -- CTC prefix beam search with blank collapse (paper Sec. 5,
+    CUDA CTC decoder), binary32 in a fixed operation order.
   * ``brute.py``   -- exhaustive enumeration of state paths for tiny inputs.
   * ``checks.py``  -- invariants: collapse, legal moves, fold sums, a max-plus
     backward pass, the FP32 summation error bound.
