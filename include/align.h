@@ -243,6 +243,48 @@ int align_set_tuning_bucket(align_ctx *ctx, int32_t s_max, int32_t states_per_la
 int align_set_tuning_bucket_for(align_ctx *ctx, int32_t table, int32_t s_max, int32_t states_per_lane,
                                 int32_t cta_warps);
 
+/* ---- CTC prefix beam search with blank collapse -------------------------- */
+
+/* Beam search decoding of CTC outputs (paper Sec. 5, "CUDA CTC decoder": beam
+   search parallel over batch, hypotheses and vocabulary, with the blank
+   collapse of the cited work, frame-skip threshold a; no language model).
+   Blank collapse: frame t is a blank frame when probs[t][blank] > threshold;
+   a blank frame right after a blank frame is skipped (threshold >= 1 keeps
+   every frame). Prefix beam search over the kept frames: each hypothesis is
+   a label prefix with pb (paths ending in blank) and pnb (ending in its last
+   label z); per frame with probabilities y it stays (pb' = (pb + pnb) *
+   y[blank], pnb' = pnb * y[z]) or grows by a non-blank label c (pnb = (pb +
+   pnb) * y[c], or pb * y[c] when c == z); a growth equal to a hypothesis of
+   the beam adds into its pnb; the beam keeps the `beam` largest totals pb +
+   pnb, ties to the smaller candidate index (stays by beam slot first, then
+   growths by slot and label). Binary32, one rounding per operation in that
+   order; after each frame every probability is multiplied by the power of
+   two that brings the largest total into [0.5, 1), the exponents summed.
+   Inputs (DEVICE pointers): probs float32 [total_frames][V] (probabilities,
+   finite and >= 0; rows need not sum to 1), frame_offsets int64 [n+1]
+   (utterance u = rows frame_offsets[u] .. frame_offsets[u+1]-1,
+   frame_offsets[n] = total_frames). 2 <= V, 0 <= blank < V, 1 <= beam <= 16.
+   workspace: at least align_ctc_beam_workspace_bytes(n, total_frames, beam)
+   device bytes (kept frame lists and the prefix tree), owned by the caller.
+   Outputs (DEVICE, caller-owned): for utterance u with T_u frames and
+   hypothesis b (beam order, largest total first): tokens / timesteps int32
+   at [frame_offsets[u] * beam + b * T_u, + lengths[u*beam + b]) = labels and
+   the frame of each label's emission (frame index within the utterance);
+   lengths int32 [n*beam] (-1: no hypothesis in that slot); totals float32
+   [n*beam] = pb + pnb after the last rescale; scale_exp int32 [n] = E, so
+   the probability of a hypothesis is totals * 2^E; scores float32 [n*beam]
+   = logf(total) + E ln 2 (-inf for a zero total); kept int32 [n] = frames
+   kept by blank collapse. One kernel (one CTA per utterance) on cuda_stream,
+   asynchronous. ALIGN_E_INVAL for bad sizes, pointers or a small workspace,
+   ALIGN_E_TOO_LARGE when V is beyond the shared memory, ALIGN_E_CUDA if the
+   launch fails. Results for NaN, negative or infinite probabilities are
+   unspecified (the kernel stays within its buffers). */
+uint64_t align_ctc_beam_workspace_bytes(int32_t n, int64_t total_frames, int32_t beam);
+int align_ctc_beam_decode(const float *probs, const int64_t *frame_offsets, int32_t n, int64_t total_frames,
+                          int32_t V, int32_t blank, int32_t beam, float threshold, void *workspace,
+                          uint64_t workspace_bytes, int32_t *tokens, int32_t *timesteps, int32_t *lengths,
+                          float *totals, int32_t *scale_exp, float *scores, int32_t *kept, void *cuda_stream);
+
 /* ---- token spans: the alignment per transcript token -------------------- */
 
 /* Token spans of one or more finished alignments, packed: utterance u owns

@@ -42,7 +42,8 @@ ALIGN_F_TEST_STALL = 0x80000000
 EXPORTS = ("align_create", "align_destroy", "align_submit", "align_submit_host", "align_submit_batch", "align_flush",
            "align_poll", "align_poll_done", "align_join", "align_get_stats", "align_status_string", "align_last_error",
            "align_set_tuning", "align_set_tuning_bucket", "align_set_tuning_bucket_for", "align_validate", "align_plan", "align_probe_frame_latency",
-           "align_forced_noalloc", "align_noalloc_last_error", "align_token_spans")
+           "align_forced_noalloc", "align_noalloc_last_error", "align_token_spans",
+           "align_ctc_beam_workspace_bytes", "align_ctc_beam_decode")
 
 
 class AlignConfig(ctypes.Structure):
@@ -123,6 +124,10 @@ def lib() -> ctypes.CDLL:
         L.align_set_tuning_bucket.argtypes = [vp, i32, i32, i32]
         L.align_set_tuning_bucket_for.argtypes = [vp, i32, i32, i32, i32]
         L.align_token_spans.argtypes = [vp, vp, vp, vp, i32, i64, i64, vp, vp, vp, vp]
+        L.align_ctc_beam_workspace_bytes.argtypes = [i32, i64, i32]
+        L.align_ctc_beam_workspace_bytes.restype = u64
+        L.align_ctc_beam_decode.argtypes = [vp, vp, i32, i64, i32, i32, i32, ctypes.c_float, vp, u64,
+                                            vp, vp, vp, vp, vp, vp, vp, vp]
         L.align_probe_frame_latency.argtypes = [i32, i32, i32, i32, ctypes.POINTER(ctypes.c_double)]
         L.align_forced_noalloc.argtypes = [vp, i64, i64, vp, i64, i32, AlignOut, vp, ctypes.POINTER(i32)]
         L.align_noalloc_last_error.argtypes = []
@@ -313,6 +318,82 @@ def token_spans(states, scores, frame_offsets, token_offsets, stream=None, total
     align_token_spans(states.data_ptr(), scores.data_ptr(), fo.data_ptr(), to.data_ptr(), n, total_T, total_L,
                       start.data_ptr(), end.data_ptr(), score.data_ptr(), st.cuda_stream)
     return start, end, score
+
+
+def align_ctc_beam_workspace_bytes(n: int, total_frames: int, beam: int) -> int:
+    return int(lib().align_ctc_beam_workspace_bytes(n, total_frames, beam))
+
+
+def align_ctc_beam_decode(probs, frame_offsets, n: int, total_frames: int, V: int, blank: int, beam: int,
+                          threshold: float, workspace, workspace_bytes: int, tokens, timesteps, lengths, totals,
+                          scale_exp, scores, kept, stream_ptr: int | None = None) -> None:
+    """Same-named call: every pointer argument is a device address (int)."""
+    _check(lib().align_ctc_beam_decode(probs, frame_offsets, n, total_frames, V, blank, beam, threshold, workspace,
+                                       workspace_bytes, tokens, timesteps, lengths, totals, scale_exp, scores, kept,
+                                       stream_ptr), "align_ctc_beam_decode")
+
+
+@dataclass
+class BeamResult:
+    """Outputs of ctc_beam_decode (CUDA tensors); hypothesis b of utterance u
+    lives at tokens[offsets[u] * beam + b * T_u :][:lengths[u, b]]."""
+    offsets: np.ndarray     # int64 [n+1] host copy of the frame offsets
+    beam: int
+    tokens: object          # int32 [sum T * beam]
+    timesteps: object       # int32 [sum T * beam]
+    lengths: object         # int32 [n, beam]
+    totals: object          # float32 [n, beam]
+    scale_exp: object       # int32 [n]
+    scores: object          # float32 [n, beam]
+    kept: object            # int32 [n]
+    workspace: object
+
+    def hypotheses(self, u: int) -> list[tuple[list[int], list[int], float]]:
+        """(tokens, timesteps, score) of utterance u's hypotheses, best first (host)."""
+        f0, f1 = int(self.offsets[u]), int(self.offsets[u + 1])
+        T = f1 - f0
+        lens = self.lengths[u].cpu().tolist()
+        sc = self.scores[u].cpu().tolist()
+        base = f0 * self.beam
+        tk = self.tokens[base:base + self.beam * T].cpu().view(self.beam, T) if T else None
+        tm = self.timesteps[base:base + self.beam * T].cpu().view(self.beam, T) if T else None
+        out = []
+        for b, L in enumerate(lens):
+            if L < 0:
+                continue
+            out.append((tk[b, :L].tolist() if L else [], tm[b, :L].tolist() if L else [], sc[b]))
+        return out
+
+
+def ctc_beam_decode(probs, offsets, beam: int = 10, blank: int = 0, threshold: float = 1.0, stream=None,
+                    workspace=None) -> BeamResult:
+    """CTC prefix beam search with blank collapse over a packed batch:
+    probs float32 CUDA tensor [sum T, V] (probabilities), offsets host int64
+    [n+1]. threshold = the blank frame-skip threshold a (1.0: no collapse).
+    One kernel launch on `stream` (default: current stream)."""
+    import torch
+    dev = probs.device
+    off = np.asarray(offsets, dtype=np.int64)
+    n = off.size - 1
+    TT, V = probs.shape
+    if off[-1] != TT:
+        raise ValueError("offsets do not match the packed probabilities")
+    fo = torch.from_numpy(off).to(dev)
+    wb = align_ctc_beam_workspace_bytes(n, TT, beam)
+    if workspace is None or workspace.numel() < wb:
+        workspace = torch.empty(max(wb, 1), dtype=torch.uint8, device=dev)
+    i32 = dict(dtype=torch.int32, device=dev)
+    res = BeamResult(off, beam, torch.empty(max(TT * beam, 1), **i32), torch.empty(max(TT * beam, 1), **i32),
+                     torch.empty((n, beam), **i32), torch.empty((n, beam), dtype=torch.float32, device=dev),
+                     torch.empty(n, **i32), torch.empty((n, beam), dtype=torch.float32, device=dev),
+                     torch.empty(n, **i32), workspace)
+    st = stream if stream is not None else torch.cuda.current_stream(dev)
+    align_ctc_beam_decode(probs.data_ptr(), fo.data_ptr(), n, TT, V, blank, beam, float(threshold),
+                          workspace.data_ptr(), wb, res.tokens.data_ptr(), res.timesteps.data_ptr(),
+                          res.lengths.data_ptr(), res.totals.data_ptr(), res.scale_exp.data_ptr(),
+                          res.scores.data_ptr(), res.kept.data_ptr(), st.cuda_stream)
+    res._keep = fo  # the offsets must outlive the launch
+    return res
 
 
 ALIGN_TUNE_LATENCY = 0

@@ -238,3 +238,47 @@ def make_batch(spec_list: list[Spec], device="cpu", logits: bool = False) -> Bat
         targets.append(tg)
         planted.append(pl)
     return Batch(lp=lp, offsets=offs, targets=targets, planted=planted, specs=spec_list)
+
+
+# ---- decoder inputs (CTC beam search with blank collapse) ----
+#
+# Probabilities of a peaky CTC model over a V-token vocabulary (the paper's
+# CUDA decoder experiment uses a 500-token vocabulary): a transcript of about
+# T/10 tokens, each label on 1-2 frames, the other frames spread over the
+# blanks around them; logits N(0,1) with a per-frame peak U[8, 16] added on
+# the planted token, softmax in FP32. With V = 500 about 80 % of the planted
+# frames get a probability above 0.95.
+
+def decoder_probs(seed: int, T: int, V: int, device="cpu") -> torch.Tensor:
+    rng = np.random.default_rng(seed)
+    L = T // 10
+    tg = make_targets(rng, L, V)
+    lab = 1 + rng.integers(0, 2, size=L)
+    blank_frames = T - int(lab.sum()) - int(np.sum(tg[1:] == tg[:-1]))
+    if blank_frames < 0:
+        raise ValueError("T too small for the planted transcript")
+    eq = np.zeros(L + 1, dtype=np.int64)
+    if L > 1:
+        eq[1:L][tg[1:] == tg[:-1]] = 1      # a blank between equal labels
+    bl = eq + rng.multinomial(blank_frames, np.full(L + 1, 1.0 / (L + 1)))
+    tokens = []
+    for i in range(L):
+        tokens += [BLANK] * int(bl[i]) + [int(tg[i])] * int(lab[i])
+    tokens += [BLANK] * int(bl[L])
+    planted = np.asarray(tokens, dtype=np.int64)
+    assert planted.size == T
+    g = torch.Generator(device="cpu")
+    g.manual_seed(seed)
+    logits = torch.randn((T, V), generator=g, dtype=torch.float32)
+    peak = torch.from_numpy(rng.uniform(8.0, 16.0, size=T).astype(np.float32))
+    logits[torch.arange(T), torch.from_numpy(planted)] += peak
+    return torch.softmax(logits, dim=-1).to(device)
+
+
+def decoder_batch(seed: int, n: int, V: int, t_lo: int = 250, t_hi: int = 1750, device="cpu"):
+    """n utterances with T ~ U[t_lo, t_hi] packed: (probs [sum T, V], offsets int64 [n+1])."""
+    rng = np.random.default_rng(seed)
+    Ts = rng.integers(t_lo, t_hi + 1, size=n)
+    parts = [decoder_probs(sub_seed(seed, i), int(T), V) for i, T in enumerate(Ts)]
+    offsets = np.concatenate([[0], np.cumsum(Ts)]).astype(np.int64)
+    return torch.cat(parts).to(device), offsets
