@@ -64,6 +64,7 @@ def parse():
     ap.add_argument("--no-spans", action="store_true", help="skip the token-span leg")
     ap.add_argument("--no-logits", action="store_true", help="skip the fused log_softmax leg")
     ap.add_argument("--no-sum", action="store_true", help="skip the sum-product (CTC forward) leg")
+    ap.add_argument("--no-beam", action="store_true", help="skip the CTC beam-search decoder leg")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the CPU oracle baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
@@ -462,6 +463,43 @@ def main():
         sum_line = {"ms": su_ms, "cells_per_s": cells / (su_ms / 1e3), "viterbi_ms": ms,
                     "note": "log-add (max factored out, __expf/__logf) in place of the max; total only"}
 
+    # CTC beam search with blank collapse (the paper's CUDA decoder setting:
+    # vocabulary 500, beam 10, batch 4; and a batch of 2 utterances per SM),
+    # thresholds a = 0.95 and a = 1.0 (no collapse); device time per call,
+    # L2 flushed before each. Frames/s counts every input frame.
+    beam_line = None
+    if not args.no_beam:
+        beam_line = {"V": 500, "beam": 10, "T": "U[250,1750] frames", "runs": []}
+        for nb in (4, 2 * torch.cuda.get_device_properties(dev).multi_processor_count):
+            probs, off = synth.decoder_batch(synth.config_seed(7) + nb, nb, 500, device="cpu")
+            probs = probs.to(dev)
+            frames = int(off[-1])
+            ws = torch.empty(align.align_ctc_beam_workspace_bytes(nb, frames, 10), dtype=torch.uint8, device=dev)
+            for a in (0.95, 1.0):
+                bt = []
+                for k in range(3 + args.steps):
+                    flush_buf.fill_(1)
+                    with torch.cuda.stream(stream):
+                        e0 = torch.cuda.Event(enable_timing=True)
+                        e1 = torch.cuda.Event(enable_timing=True)
+                        e0.record(stream)
+                        r = align.ctc_beam_decode(probs, off, beam=10, blank=0, threshold=a, stream=stream,
+                                                  workspace=ws)
+                        e1.record(stream)
+                    e1.synchronize()
+                    if k >= 3:
+                        bt.append(e0.elapsed_time(e1))
+                b_ms = statistics.mean(bt)
+                kept = r.kept.cpu().numpy().astype(np.int64)
+                Ts = np.diff(off)
+                alg = int(kept.sum()) * 500 * 4 + frames * 32  # kept rows once + one sector per frame (blank column)
+                beam_line["runs"].append({
+                    "batch": nb, "a": a, "ms": b_ms, "frames": frames, "kept_frames": int(kept.sum()),
+                    "frames_per_s": frames / (b_ms / 1e3),
+                    "ns_per_kept_frame_longest": b_ms * 1e6 / int(kept.max()),
+                    "longest_T": int(Ts.max()), "alg_bytes": alg, "gbs": alg / (b_ms / 1e3) / 1e9})
+            del probs, ws
+
     # Plain: one synchronous submit + poll per utterance (at most 256 utterances).
     plain = None
     if not args.no_plain:
@@ -595,6 +633,7 @@ def main():
         "token_spans": spans_line,
         "logits": logits_line,
         "ctc_forward": sum_line,
+        "beam_decode": beam_line,
         "cpu_baseline": cpu,
         "clocks": clk.summary(),
     }

@@ -274,8 +274,9 @@ int align_set_tuning_bucket_for(align_ctx *ctx, int32_t table, int32_t s_max, in
    [n*beam] = pb + pnb after the last rescale; scale_exp int32 [n] = E, so
    the probability of a hypothesis is totals * 2^E; scores float32 [n*beam]
    = logf(total) + E ln 2 (-inf for a zero total); kept int32 [n] = frames
-   kept by blank collapse. One kernel (one CTA per utterance) on cuda_stream,
-   asynchronous. ALIGN_E_INVAL for bad sizes, pointers or a small workspace,
+   kept by blank collapse. Two kernels on cuda_stream, asynchronous: the
+   B most probable labels of every frame (one warp per frame), then the
+   search (one CTA per utterance). ALIGN_E_INVAL for bad sizes, pointers or a small workspace,
    ALIGN_E_TOO_LARGE when V is beyond the shared memory, ALIGN_E_CUDA if the
    launch fails. Results for NaN, negative or infinite probabilities are
    unspecified (the kernel stays within its buffers). */

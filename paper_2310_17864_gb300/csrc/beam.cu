@@ -2,34 +2,43 @@
 // decoder": beam search parallel over batch, hypotheses and vocabulary, after
 // the blank collapse of the cited work with frame-skip threshold a).
 //
-// One CTA per utterance, 256 threads.
+// Two kernels.
 //
+// rank_kernel (one warp per frame, every frame of the batch at once): the B
+// most probable non-blank labels of the frame (B rounds of a warp maximum
+// over per-lane heads). They only serve to bound the selection below, so
+// equal probabilities may come in any order. This work does not depend on
+// the beam and is taken off the serial frame loop.
+//
+// beam_kernel (one CTA of 256 threads per utterance):
 // Prologue (blank collapse): frame t is a blank frame when P[t, blank] > a;
 // a blank frame that follows a blank frame is dropped (every run of blank
 // frames shrinks to its first frame). A block-wide ballot scan writes the
 // kept frame indices to the workspace.
-//
-// Per kept frame (rows staged in shared memory with cp.async, two frames
-// ahead, a ring of four rows):
-//   S1 (warp 0): the two most probable non-blank labels of the frame; every
-//      hypothesis' stay (blank: (pb + pnb) * y[blank]; repeat of its last
-//      label z: pnb * y[z]; plus the growth of the hypothesis whose prefix is
-//      this one's minus its last label); a lower bound theta of the B-th best
-//      candidate key from 2n actual candidates (the n stays and each
-//      hypothesis' growth by its best non-merged label).
+// Per kept frame (the row and its ranked labels staged in shared memory with
+// cp.async, two frames ahead, a ring of four):
+//   S1 (warp 0): every hypothesis' stay (blank: (pb + pnb) * y[blank];
+//      repeat of its last label z: pnb * y[z]; plus the growth of the
+//      hypothesis whose prefix is this one's minus its last label), and
+//      theta = the B-th largest key among the stays and the growths of the
+//      best hypothesis by the ranked labels: all actual candidates, so theta
+//      is at most the B-th best key of the frame.
 //   S2 (all threads): every growth (i, c): ((c == z_i) ? pb_i : pb_i + pnb_i)
-//      * y[c]; keys >= theta go to a survivor list in shared memory.
-//   S3 (warp 0): the top B survivors (a 32-lane bitonic sort, or B rounds of
-//      warp arg-max), the new beam (new prefix-tree nodes for growths in the
-//      workspace), the power-of-two rescale, and for the next frame the
-//      growth (i, c) equal to each hypothesis j (64-bit prefix hashes as a
-//      filter, confirmed by walking both prefixes in the tree).
+//      * y[c]; keys >= theta go to a survivor list in shared memory (about B
+//      of them).
+//   S3 (warp 0): the top B survivors (rank of each key among the others, or
+//      B rounds of warp arg-max when there are more than 32), the new beam
+//      (new prefix-tree nodes for growths in the workspace), the power-of-two
+//      rescale, and for the next frame the growth (i, c) equal to each
+//      hypothesis j (64-bit prefix hashes as a filter, confirmed by walking
+//      both prefixes in the tree).
 // Keys are (value bits << 32) | (~candidate index): values are non-negative
 // binary32, so key order is value order, then the smaller index (stays i
 // < B, growths B + i * V + c). Every product and sum is one binary32
 // operation in the same order as the definition (no FMA contraction, no
 // flush to zero), so the result is the same bit for bit as a plain binary32
 // evaluation in that order.
+#include <algorithm>
 #include <cstdint>
 
 #include <cuda_runtime.h>
@@ -53,6 +62,7 @@ struct BeamArgs {
   int32_t n, V, blank, B;
   float a;
   int32_t* kept_ws;          // [total_frames] kept frame indices
+  const int32_t* topl;       // [total_frames][B] ranked labels of every frame (-1: none)
   int32_t* nparent;          // prefix-tree nodes: utterance u owns [foff[u] * B + u, + T_u * B + 1)
   int32_t* nlabel;
   int32_t* nframe;
@@ -89,22 +99,6 @@ __device__ __forceinline__ uint64_t shfl_xor_u64(uint64_t v, int m) {
   return (static_cast<uint64_t>(hi) << 32) | lo;
 }
 
-// Descending bitonic sort of one 64-bit key per lane across the warp.
-__device__ __forceinline__ uint64_t warp_sort_desc(uint64_t k, int lane) {
-#pragma unroll
-  for (int size = 2; size <= 32; size <<= 1) {
-#pragma unroll
-    for (int stride = size >> 1; stride > 0; stride >>= 1) {
-      const uint64_t o = shfl_xor_u64(k, stride);
-      const bool up = (lane & size) == 0;        // this block sorts descending when up
-      const bool lower = (lane & stride) == 0;   // this lane keeps the larger key when lower == up
-      const bool keep_max = (lower == up);
-      k = keep_max ? (k > o ? k : o) : (k < o ? k : o);
-    }
-  }
-  return k;
-}
-
 __device__ __forceinline__ uint64_t warp_max_u64(uint64_t k) {
 #pragma unroll
   for (int m = 16; m > 0; m >>= 1) {
@@ -130,7 +124,7 @@ __device__ __forceinline__ void cp_wait() {
 
 struct BeamState {
   float pb[kMaxBeam], pnb[kMaxBeam];
-  int32_t node[kMaxBeam], len[kMaxBeam], last[kMaxBeam];
+  int32_t node[kMaxBeam], pnode[kMaxBeam], len[kMaxBeam], last[kMaxBeam];
   uint64_t h[kMaxBeam], hp[kMaxBeam];
 };
 
@@ -141,11 +135,48 @@ struct BeamShared {
   int32_t match[kMaxBeam];  // current beam: the hypothesis i whose growth by last[j] is j, or -1
   int32_t mword[kMaxBeam];  // merge bit set for j (word index into mbits, or -1)
   uint64_t theta;
+  uint64_t kbuf[32];
+  uint64_t sel[kMaxBeam];
   int32_t nsurv;
   int32_t overflow;
   int32_t nlive;
   int32_t warp_tot[kThreads / 32];
 };
+
+// The B largest non-blank labels of every frame (by probability; equal
+// probabilities in any order), one warp per frame.
+__global__ void __launch_bounds__(kThreads) rank_kernel(const float* __restrict__ probs, int64_t total_frames,
+                                                        int V, int blank, int B, int32_t* __restrict__ topl) {
+  const int lane = threadIdx.x & 31;
+  const int64_t wstride = static_cast<int64_t>(gridDim.x) * (kThreads / 32);
+  for (int64_t g = static_cast<int64_t>(blockIdx.x) * (kThreads / 32) + (threadIdx.x >> 5); g < total_frames;
+       g += wstride) {
+    const float* y = probs + g * V;
+    // Lane head: its largest (value, ~label) key below the last one it gave.
+    auto head_below = [&](uint64_t lim) {
+      uint64_t h = 0;
+      for (int c = lane; c < V; c += 32) {
+        if (c == blank) continue;
+        const uint64_t kc = make_key(__ldg(y + c), static_cast<uint32_t>(c));
+        if (kc < lim && kc > h) h = kc;
+      }
+      return h;
+    };
+    uint64_t head = head_below(~0ull);
+    for (int r = 0; r < B; ++r) {
+      const unsigned hv = head ? static_cast<unsigned>(head >> 32) : 0u;
+      const unsigned m = __reduce_max_sync(kFull, hv);
+      const unsigned who = __ballot_sync(kFull, head != 0 && hv == m);
+      int c = -1;
+      if (who) {
+        const int owner = __ffs(who) - 1;
+        c = __shfl_sync(kFull, static_cast<int>(key_index(head)), owner);
+        if (lane == owner) head = head_below(head);
+      }
+      if (lane == 0) topl[g * B + r] = c;
+    }
+  }
+}
 
 __global__ void __launch_bounds__(kThreads) beam_kernel(const BeamArgs A) {
   extern __shared__ __align__(16) unsigned char dsm[];
@@ -156,9 +187,10 @@ __global__ void __launch_bounds__(kThreads) beam_kernel(const BeamArgs A) {
   const int64_t f0 = A.foff[u];
   const int T = static_cast<int>(A.foff[u + 1] - f0);
   const int Vp = (V + 3) & ~3;
+  const int Vq = Vp + kMaxBeam + 4;  // a ring slot: the row, its ranked labels, its frame index
   const int W = (V + 31) >> 5;
-  float* rows = reinterpret_cast<float*>(dsm);                                      // [kRowRing][Vp]
-  uint64_t* surv = reinterpret_cast<uint64_t*>(dsm + sizeof(float) * kRowRing * Vp);  // [kSurvCap]
+  float* rows = reinterpret_cast<float*>(dsm);                                      // [kRowRing][Vq]
+  uint64_t* surv = reinterpret_cast<uint64_t*>(dsm + sizeof(float) * kRowRing * Vq);  // [kSurvCap]
   uint32_t* mbits = reinterpret_cast<uint32_t*>(surv + kSurvCap);                    // [B][W]
   const float* P = A.probs + f0 * V;
   int32_t* kept = A.kept_ws + f0;
@@ -193,139 +225,157 @@ __global__ void __launch_bounds__(kThreads) beam_kernel(const BeamArgs A) {
   __syncthreads();  // kept[] visible to every thread (global writes of this block)
 
   const bool vec = (V & 3) == 0 && (reinterpret_cast<uintptr_t>(A.probs) & 15) == 0;
-  auto issue_row = [&](int k) {
+  // Rows are staged by warp 0 alone (its own cp.async groups), so that warp 0
+  // can wait for the next row at the end of a frame without a block barrier.
+  auto issue_row = [&](int k, int t) {
     if (k < K) {
-      const float* src = P + static_cast<int64_t>(kept[k]) * V;
-      float* dst = rows + (k % kRowRing) * Vp;
+      const float* src = P + static_cast<int64_t>(t) * V;
+      float* dst = rows + (k % kRowRing) * Vq;
       if (vec) {
-        for (int q = tid; q < (V >> 2); q += kThreads) cp_async16b(dst + 4 * q, src + 4 * q);
+        for (int q = lane; q < (V >> 2); q += 32) cp_async16b(dst + 4 * q, src + 4 * q);
       } else {
-        for (int q = tid; q < V; q += kThreads) cp_async4(dst + q, src + q);
+        for (int q = lane; q < V; q += 32) cp_async4(dst + q, src + q);
       }
+      if (lane < B) cp_async4(dst + Vp + lane, A.topl + (f0 + t) * B + lane);
+      if (lane == 0) reinterpret_cast<int32_t*>(dst)[Vp + kMaxBeam] = t;
     }
     cp_commit();
   };
 
-  if (tid == 0) {
-    BeamState& b0 = S.st[0];
-    b0.pb[0] = 1.0f;
-    b0.pnb[0] = 0.0f;
-    b0.node[0] = 0;
-    b0.len[0] = 0;
-    b0.last[0] = -1;
-    b0.h[0] = kHashEmpty;
-    b0.hp[0] = 0;
-    A.nparent[nbase] = -1;
-    A.nlabel[nbase] = -1;
-    A.nframe[nbase] = -1;
-  }
-  if (tid < kMaxBeam) {
-    S.match[tid] = -1;
-    S.mword[tid] = -1;
-  }
-  int n = 1, cur = 0, E = 0;  // uniform across the block
-  for (int k = 0; k < kAhead; ++k) issue_row(k);
-  __syncthreads();
-
-  for (int k = 0; k < K; ++k) {
-    issue_row(k + kAhead);
-    cp_wait<kAhead>();
-    __syncthreads();  // row k staged by every thread
-    const float* y = rows + (k % kRowRing) * Vp;
-    const BeamState& ob = S.st[cur];
-
-    // ---- S1 (warp 0): stays, merged growths, theta ----
-    if (warp == 0) {
-      uint64_t k1 = 0, k2 = 0;  // two best non-blank labels: (y bits, ~c)
-      for (int c = lane; c < V; c += 32) {
-        if (c == blank) continue;
-        const uint64_t kc = make_key(y[c], static_cast<uint32_t>(c));
-        if (kc > k1) {
-          k2 = k1;
-          k1 = kc;
-        } else if (kc > k2) {
-          k2 = kc;
-        }
-      }
-#pragma unroll
-      for (int m = 16; m > 0; m >>= 1) {
-        const uint64_t o1 = shfl_xor_u64(k1, m), o2 = shfl_xor_u64(k2, m);
-        const uint64_t n1 = k1 > o1 ? k1 : o1;
-        const uint64_t n2 = k1 > o1 ? (k2 > o1 ? k2 : o1) : (k1 > o2 ? k1 : o2);
-        k1 = n1;
-        k2 = n2;
-      }
-      const int c1 = k1 ? static_cast<int>(key_index(k1)) : -1;
-      const int c2 = k2 ? static_cast<int>(key_index(k2)) : -1;
-      const int j = lane & 15;
-      float sj = 0.0f;
-      if (j < n) sj = ob.pb[j] + ob.pnb[j];
-      uint64_t key = 0;
-      if (lane < 16 && j < n) {  // stays
+  // S1 for kept frame k over beam buffer c with nl live hypotheses (warp 0):
+  // stays, merged growths, theta and the stays above it.
+  auto stage1 = [&](int k, int c, int nl) {
+    const float* y = rows + (k % kRowRing) * Vq;
+    const int32_t* ranked = reinterpret_cast<const int32_t*>(y + Vp);
+    const BeamState& ob = S.st[c];
+    const int j = lane & 15;
+    uint64_t key = 0;
+    if (lane < 16) {
+      if (j < nl) {  // stay of hypothesis j
+        const float sj = ob.pb[j] + ob.pnb[j];
         const float sb = sj * y[blank];
         float snb = ob.len[j] > 0 ? ob.pnb[j] * y[ob.last[j]] : 0.0f;
         const int i = S.match[j];
         if (i >= 0) {
-          const int c = ob.last[j];
+          const int cj = ob.last[j];
           const float si = ob.pb[i] + ob.pnb[i];
-          const float base = (ob.last[i] == c) ? ob.pb[i] : si;
-          snb = snb + base * y[c];
+          const float base = (ob.last[i] == cj) ? ob.pb[i] : si;
+          snb = snb + base * y[cj];
         }
         S.s[j] = sj;
         S.stay_b[j] = sb;
         S.stay_nb[j] = snb;
         key = make_key(sb + snb, static_cast<uint32_t>(j));
-      } else if (lane >= 16 && j < n) {  // hypothesis j's growth by its best label that is not merged
-        int c = -1;
-        if (c1 >= 0 && !((mbits[j * W + (c1 >> 5)] >> (c1 & 31)) & 1u)) c = c1;
-        else if (c2 >= 0 && !((mbits[j * W + (c2 >> 5)] >> (c2 & 31)) & 1u)) c = c2;
-        if (c >= 0) {
-          const float base = (ob.last[j] == c) ? ob.pb[j] : sj;
-          key = make_key(base * y[c], static_cast<uint32_t>(B + j * V + c));
-        }
       }
-      const uint64_t sorted = warp_sort_desc(key, lane);
-      const uint64_t th = __shfl_sync(kFull, static_cast<uint32_t>(sorted >> 32), B - 1);
-      const uint64_t tl = __shfl_sync(kFull, static_cast<uint32_t>(sorted), B - 1);
-      const uint64_t theta = (th << 32) | tl;  // 0 when fewer than B candidates were seen
-      const bool put = lane < 16 && j < n && key >= theta;
-      const unsigned bal = __ballot_sync(kFull, put);
-      if (put) surv[__popc(bal & ((1u << lane) - 1u))] = key;
-      if (lane == 0) {
-        S.theta = theta;
-        S.nsurv = __popc(bal);
-        S.overflow = 0;
+    } else if (j < B) {  // growth of hypothesis 0 by its j-th ranked label, when not merged
+      const int cr = ranked[j];
+      if (cr >= 0 && !((mbits[cr >> 5] >> (cr & 31)) & 1u)) {
+        const float base = (ob.last[0] == cr) ? ob.pb[0] : ob.pb[0] + ob.pnb[0];
+        key = make_key(base * y[cr], static_cast<uint32_t>(B + cr));
       }
     }
-    __syncthreads();
+    // theta: the key of rank B-1 among these actual candidates (0 when fewer than B).
+    S.kbuf[lane] = key;
+    __syncwarp();
+    int rank = 0;
+#pragma unroll
+    for (int q = 0; q < 32; ++q) rank += S.kbuf[q] > key;
+    const unsigned at = __ballot_sync(kFull, key != 0 && rank == B - 1);
+    const uint64_t theta = at ? S.kbuf[__ffs(at) - 1] : 0ull;
+    const bool put = lane < 16 && j < nl && key >= theta;
+    const unsigned bal = __ballot_sync(kFull, put);
+    if (put) surv[__popc(bal & ((1u << lane) - 1u))] = key;
+    if (lane == 0) {
+      S.theta = theta;
+      S.nsurv = __popc(bal);
+      S.overflow = 0;
+    }
+  };
+
+  int n = 1, cur = 0, E = 0;  // uniform across the block
+  int t_pref = 0;             // warp 0: frame index of the next row to stage
+  const float invV = 1.0f / static_cast<float>(V);
+  if (warp == 0) {
+    if (lane == 0) {
+      BeamState& b0 = S.st[0];
+      b0.pb[0] = 1.0f;
+      b0.pnb[0] = 0.0f;
+      b0.node[0] = 0;
+      b0.pnode[0] = -1;
+      b0.len[0] = 0;
+      b0.last[0] = -1;
+      b0.h[0] = kHashEmpty;
+      b0.hp[0] = 0;
+      S.nlive = 1;
+      A.nparent[nbase] = -1;
+      A.nlabel[nbase] = -1;
+      A.nframe[nbase] = -1;
+    }
+    if (lane < kMaxBeam) {
+      S.match[lane] = -1;
+      S.mword[lane] = -1;
+    }
+    for (int k = 0; k < kAhead; ++k) issue_row(k, k < K ? kept[k] : 0);
+    t_pref = kAhead < K ? kept[kAhead] : 0;
+    cp_wait<kAhead - 1>();
+    __syncwarp();
+    if (K > 0) stage1(0, 0, 1);
+  }
+  __syncthreads();
+
+  for (int k = 0; k < K; ++k) {
+    const float* y = rows + (k % kRowRing) * Vq;
+    const BeamState& ob = S.st[cur];
 
     // ---- S2 (all threads): growths above theta ----
     {
       const uint64_t theta = S.theta;
+      float bs[kMaxBeam], bpb[kMaxBeam];
+      int blast[kMaxBeam];
+#pragma unroll
+      for (int i = 0; i < kMaxBeam; ++i) {
+        if (i < n) {
+          bs[i] = S.s[i];
+          bpb[i] = ob.pb[i];
+          blast[i] = ob.last[i];
+        }
+      }
       for (int c = tid; c < V; c += kThreads) {
         if (c == blank) continue;
         const float yc = y[c];
-        for (int i = 0; i < n; ++i) {
+        unsigned hit = 0;  // hypotheses whose growth by c reaches theta
+#pragma unroll
+        for (int i = 0; i < kMaxBeam; ++i) {
+          const float base = (blast[i] == c) ? bpb[i] : bs[i];
+          const uint64_t key = make_key(base * yc, static_cast<uint32_t>(B + i * V + c));
+          hit |= (i < n && key >= theta) ? (1u << i) : 0u;
+        }
+        while (hit) {  // rare: recompute the key and append it unless merged
+          const int i = __ffs(hit) - 1;
+          hit &= hit - 1;
           if ((mbits[i * W + (c >> 5)] >> (c & 31)) & 1u) continue;
           const float base = (ob.last[i] == c) ? ob.pb[i] : S.s[i];
           const uint64_t key = make_key(base * yc, static_cast<uint32_t>(B + i * V + c));
-          if (key >= theta) {
-            const int slot = atomicAdd(&S.nsurv, 1);
-            if (slot < kSurvCap) surv[slot] = key;
-            else S.overflow = 1;
-          }
+          const int slot = atomicAdd(&S.nsurv, 1);
+          if (slot < kSurvCap) surv[slot] = key;
+          else S.overflow = 1;
         }
       }
     }
     __syncthreads();
 
-    // ---- S3 (warp 0): selection, new beam, rescale, merges of the next frame ----
+    // ---- S3 (warp 0): selection, new beam, rescale, merges; then S1 of the next frame ----
     if (warp == 0) {
       const int ns = min(S.nsurv, kSurvCap);
       uint64_t mine = 0;  // lane b < B: the b-th selected key (0: none)
-      if (!S.overflow && ns <= 32) {
+      if (!S.overflow && ns <= 32) {  // rank of each survivor among the others
         const uint64_t kk = lane < ns ? surv[lane] : 0ull;
-        mine = warp_sort_desc(kk, lane);
+        int rank = 0;
+#pragma unroll 8
+        for (int q = 0; q < ns; ++q) rank += surv[q] > kk;
+        if (lane < ns && rank < B) S.sel[rank] = kk;
+        __syncwarp();
+        mine = lane < min(ns, B) ? S.sel[lane] : 0ull;
       } else {
         // B rounds of warp arg-max below the previous pick: over the survivors,
         // or over every candidate when the survivor list overflowed.
@@ -360,8 +410,8 @@ __global__ void __launch_bounds__(kThreads) beam_kernel(const BeamArgs A) {
       }
       const unsigned have = __ballot_sync(kFull, lane < B && mine != 0);
       const int nb = __popc(have);  // selected keys occupy lanes 0 .. nb-1
+      const int t_k = reinterpret_cast<const int32_t*>(y + Vp)[kMaxBeam];
       BeamState& nbm = S.st[cur ^ 1];
-      float tot = 0.0f;
       if (lane < nb) {
         const uint32_t idx = key_index(mine);
         if (idx < static_cast<uint32_t>(B)) {  // a stay
@@ -369,55 +419,80 @@ __global__ void __launch_bounds__(kThreads) beam_kernel(const BeamArgs A) {
           nbm.pb[lane] = S.stay_b[i];
           nbm.pnb[lane] = S.stay_nb[i];
           nbm.node[lane] = ob.node[i];
+          nbm.pnode[lane] = ob.pnode[i];
           nbm.len[lane] = ob.len[i];
           nbm.last[lane] = ob.last[i];
           nbm.h[lane] = ob.h[i];
           nbm.hp[lane] = ob.hp[i];
         } else {  // a growth: a new node of the prefix tree
-          const uint32_t r = idx - static_cast<uint32_t>(B);
-          const int i = static_cast<int>(r / static_cast<uint32_t>(V));
-          const int c = static_cast<int>(r % static_cast<uint32_t>(V));
+          const int r = static_cast<int>(idx) - B;  // i * V + c with i < 16: exact in a float
+          int i = static_cast<int>(static_cast<float>(r) * invV);
+          if (i * V > r) --i;
+          if ((i + 1) * V <= r) ++i;
+          const int c = r - i * V;
           const int id = 1 + k * B + lane;
           A.nparent[nbase + id] = ob.node[i];
           A.nlabel[nbase + id] = c;
-          A.nframe[nbase + id] = kept[k];
+          A.nframe[nbase + id] = t_k;
           nbm.pb[lane] = 0.0f;
           nbm.pnb[lane] = key_value(mine);
           nbm.node[lane] = id;
+          nbm.pnode[lane] = ob.node[i];
           nbm.len[lane] = ob.len[i] + 1;
           nbm.last[lane] = c;
           nbm.h[lane] = grow_hash(ob.h[i], c);
           nbm.hp[lane] = ob.h[i];
         }
-        tot = nbm.pb[lane] + nbm.pnb[lane];
       }
-      // Rescale by a power of two: the largest total into [0.5, 1).
-      float m = tot;
-#pragma unroll
-      for (int s = 16; s > 0; s >>= 1) m = fmaxf(m, __shfl_xor_sync(kFull, m, s));
+      // Rescale by a power of two: the largest total into [0.5, 1). The
+      // largest total is the value of the first selected key (stays: the
+      // same sum; growths: 0 + value).
+      const float m = __uint_as_float(__shfl_sync(kFull, static_cast<unsigned>(mine >> 32), 0));
       if (m > 0.0f) {
-        int e = 0;
-        (void)frexpf(m, &e);
-        if (lane < nb) {
-          nbm.pb[lane] = ldexpf(nbm.pb[lane], -e);
-          nbm.pnb[lane] = ldexpf(nbm.pnb[lane], -e);
+        const uint32_t mb = __float_as_uint(m);
+        int e = static_cast<int>((mb >> 23) & 0xffu) - 126;  // m = f * 2^e, f in [0.5, 1), m normal
+        if (mb >= 0x00800000u && e > -126 && e < 127) {
+          const float f = __uint_as_float(static_cast<uint32_t>(127 - e) << 23);  // 2^-e, a normal float
+          if (lane < nb) {
+            nbm.pb[lane] = nbm.pb[lane] * f;
+            nbm.pnb[lane] = nbm.pnb[lane] * f;
+          }
+        } else {
+          (void)frexpf(m, &e);
+          if (lane < nb) {
+            nbm.pb[lane] = ldexpf(nbm.pb[lane], -e);
+            nbm.pnb[lane] = ldexpf(nbm.pnb[lane], -e);
+          }
         }
         E += e;
       }
-      // Clear last frame's merge bits, then find this beam's merges.
+      // Clear last frame's merge bits; then for each new hypothesis j (lane
+      // 16 + j) the hypothesis i (lane i) whose prefix is j's minus its last
+      // label: equal (hash, length) keys by a warp match, confirmed by the
+      // parent node, or by walking both prefixes when the nodes differ.
       if (lane < kMaxBeam && S.mword[lane] >= 0) {
         mbits[S.mword[lane]] = 0u;
         S.mword[lane] = -1;
       }
       __syncwarp();
+      const int e16 = lane & 15;
+      const bool as_i = lane < 16 && e16 < nb;
+      const bool as_j = lane >= 16 && e16 < nb && nbm.len[e16] > 0;
+      uint64_t mk = ~static_cast<uint64_t>(lane);  // matches nothing real in practice; confirmed below anyway
+      if (as_i) mk = nbm.h[e16] ^ (static_cast<uint64_t>(nbm.len[e16]) * 0x9e3779b97f4a7c15ull);
+      if (as_j) mk = nbm.hp[e16] ^ (static_cast<uint64_t>(nbm.len[e16] - 1) * 0x9e3779b97f4a7c15ull);
+      const unsigned imask = __ballot_sync(kFull, as_i);
+      unsigned cand = __match_any_sync(kFull, mk) & imask;
       int match = -1;
-      if (lane < nb && nbm.len[lane] > 0) {
+      if (as_j) {
         const int32_t* par = A.nparent + nbase;
         const int32_t* lab = A.nlabel + nbase;
-        for (int i = 0; i < nb && match < 0; ++i) {
-          if (nbm.len[i] != nbm.len[lane] - 1 || nbm.h[i] != nbm.hp[lane]) continue;
+        while (cand && match < 0) {
+          const int i = __ffs(cand) - 1;
+          cand &= cand - 1;
+          if (nbm.len[i] != nbm.len[e16] - 1) continue;
           int x = nbm.node[i];
-          int z = par[nbm.node[lane]];
+          int z = nbm.pnode[e16];
           bool same = true;
           for (int step = 0; step <= nbm.len[i] && x != z; ++step) {  // equal depths: both reach the root
             if (lab[x] != lab[z]) {
@@ -429,19 +504,27 @@ __global__ void __launch_bounds__(kThreads) beam_kernel(const BeamArgs A) {
           }
           if (same && x == z) match = i;
         }
+        S.match[e16] = match;
+      } else if (lane >= 16) {
+        S.match[e16] = -1;
       }
-      if (lane < kMaxBeam) S.match[lane] = lane < nb ? match : -1;
       __syncwarp();
       if (match >= 0) {
-        const int c = nbm.last[lane];
+        const int c = nbm.last[e16];
         const int w = match * W + (c >> 5);
         atomicOr(&mbits[w], 1u << (c & 31));
-        S.mword[lane] = w;
+        S.mword[e16] = w;
       }
       if (lane == 0) S.nlive = nb;
+      // Next frame: stage row k + 2, wait for row k + 1, run its S1.
+      issue_row(k + kAhead, t_pref);
+      t_pref = (k + kAhead + 1 < K) ? kept[k + kAhead + 1] : 0;  // used one frame later
+      cp_wait<kAhead - 1>();
+      __syncwarp();
+      if (k + 1 < K) stage1(k + 1, cur ^ 1, nb);
     }
     cur ^= 1;
-    __syncthreads();  // the new beam, its merges and its size are visible to every warp
+    __syncthreads();  // the new beam, its merges, theta and the next row are visible to every warp
     n = S.nlive;
   }
   cp_wait<0>();
@@ -490,7 +573,8 @@ uint64_t align_ctc_beam_workspace_bytes(int32_t n, int64_t total_frames, int32_t
   const uint64_t nodes = static_cast<uint64_t>(total_frames) * beam + n;
   const uint64_t kept = (static_cast<uint64_t>(total_frames) * 4 + 255) & ~255ull;
   const uint64_t arr = (nodes * 4 + 255) & ~255ull;
-  return kept + 3 * arr;
+  const uint64_t ranked = (static_cast<uint64_t>(total_frames) * beam * 4 + 255) & ~255ull;
+  return kept + 3 * arr + ranked;
 }
 
 int align_ctc_beam_decode(const float* probs, const int64_t* frame_offsets, int32_t n, int64_t total_frames,
@@ -522,6 +606,8 @@ int align_ctc_beam_decode(const float* probs, const int64_t* frame_offsets, int3
   a.nparent = reinterpret_cast<int32_t*>(ws + kbytes);
   a.nlabel = reinterpret_cast<int32_t*>(ws + kbytes + abytes);
   a.nframe = reinterpret_cast<int32_t*>(ws + kbytes + 2 * abytes);
+  int32_t* topl = reinterpret_cast<int32_t*>(ws + kbytes + 3 * abytes);
+  a.topl = topl;
   a.tokens = tokens;
   a.times = timesteps;
   a.lengths = lengths;
@@ -529,8 +615,8 @@ int align_ctc_beam_decode(const float* probs, const int64_t* frame_offsets, int3
   a.scale_exp = scale_exp;
   a.scores = scores;
   a.nkept = kept;
-  const int Vp = (V + 3) & ~3;
-  const size_t smem = sizeof(float) * kRowRing * Vp + sizeof(uint64_t) * kSurvCap +
+  const int Vq = ((V + 3) & ~3) + kMaxBeam + 4;
+  const size_t smem = sizeof(float) * kRowRing * Vq + sizeof(uint64_t) * kSurvCap +
                       sizeof(uint32_t) * beam * ((V + 31) / 32);
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return ALIGN_E_CUDA;
@@ -540,7 +626,15 @@ int align_ctc_beam_decode(const float* probs, const int64_t* frame_offsets, int3
   if (cudaFuncSetAttribute(beam_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) !=
       cudaSuccess)
     return ALIGN_E_CUDA;
-  beam_kernel<<<n, kThreads, smem, static_cast<cudaStream_t>(cuda_stream)>>>(a);
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (total_frames > 0) {
+    const int64_t blocks = std::min<int64_t>((total_frames + kThreads / 32 - 1) / (kThreads / 32),
+                                             static_cast<int64_t>(std::max(sms, 1)) * 8);
+    rank_kernel<<<static_cast<unsigned>(blocks), kThreads, 0, st>>>(probs, total_frames, V, blank, beam, topl);
+  }
+  beam_kernel<<<n, kThreads, smem, st>>>(a);
   return cudaGetLastError() == cudaSuccess ? ALIGN_OK : ALIGN_E_CUDA;
 }
 
