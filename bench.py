@@ -72,6 +72,8 @@ def parse():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=400)
     ap.add_argument("--profile", action="store_true", help="only warm-up + steps batches, for profilers")
+    ap.add_argument("--profile-beam", type=int, default=0, metavar="N",
+                    help="only warm-up + steps decoder calls on a batch of N utterances, for profilers")
     return ap.parse_args()
 
 
@@ -270,6 +272,17 @@ def main():
     import __graft_entry__
     __graft_entry__.build()
     from paper_2310_17864_gb300 import align, autotune, synth
+
+    if args.profile_beam:  # only decoder calls (vocabulary 500, beam 10), for profilers
+        nb = args.profile_beam
+        probs, off = synth.decoder_batch(synth.config_seed(7) + nb, nb, 500, device="cpu")
+        probs = probs.to(dev)
+        for _ in range(args.warmup + args.steps):
+            r = align.ctc_beam_decode(probs, off, beam=10, blank=0, threshold=0.95)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile": f"beam_decode_batch{nb}_V500_B10_a0.95", "calls": args.warmup + args.steps,
+                          "kept_frames": int(r.kept.sum().item()), "frames": int(off[-1])}))
+        return
 
     batch = synth.make_batch(synth.specs(wl["cfg"], C=wl["C"]), device=f"cuda:{dev}")
     n = len(batch)

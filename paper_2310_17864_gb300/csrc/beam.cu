@@ -367,15 +367,14 @@ __global__ void __launch_bounds__(kThreads) beam_kernel(const BeamArgs A) {
     // ---- S3 (warp 0): selection, new beam, rescale, merges; then S1 of the next frame ----
     if (warp == 0) {
       const int ns = min(S.nsurv, kSurvCap);
-      uint64_t mine = 0;  // lane b < B: the b-th selected key (0: none)
+      uint64_t mine = 0;  // this lane's selected key (0: none) and its place in the new beam
+      int slot = lane;
       if (!S.overflow && ns <= 32) {  // rank of each survivor among the others
-        const uint64_t kk = lane < ns ? surv[lane] : 0ull;
+        mine = lane < ns ? surv[lane] : 0ull;
         int rank = 0;
 #pragma unroll 8
-        for (int q = 0; q < ns; ++q) rank += surv[q] > kk;
-        if (lane < ns && rank < B) S.sel[rank] = kk;
-        __syncwarp();
-        mine = lane < min(ns, B) ? S.sel[lane] : 0ull;
+        for (int q = 0; q < ns; ++q) rank += surv[q] > mine;
+        slot = rank;
       } else {
         // B rounds of warp arg-max below the previous pick: over the survivors,
         // or over every candidate when the survivor list overflowed.
@@ -408,63 +407,68 @@ __global__ void __launch_bounds__(kThreads) beam_kernel(const BeamArgs A) {
           if (best == 0) break;
         }
       }
-      const unsigned have = __ballot_sync(kFull, lane < B && mine != 0);
-      const int nb = __popc(have);  // selected keys occupy lanes 0 .. nb-1
+      const bool valid = mine != 0 && slot < B;
+      const unsigned have = __ballot_sync(kFull, valid);
+      const int nb = __popc(have);  // the new beam fills slots 0 .. nb-1
+      // The largest total is the value of the slot-0 key (stays: the same
+      // sum; growths: 0 + value): the rescale by a power of two that brings
+      // it into [0.5, 1) is known before the entries are written.
+      const unsigned top = __ballot_sync(kFull, valid && slot == 0);
+      const float m = __uint_as_float(__shfl_sync(kFull, static_cast<unsigned>(mine >> 32), __ffs(top) - 1));
+      int e = 0;
+      float f = 1.0f;
+      bool pow2 = true;
+      if (m > 0.0f) {
+        const uint32_t mb = __float_as_uint(m);
+        e = static_cast<int>((mb >> 23) & 0xffu) - 126;  // m = f * 2^e, f in [0.5, 1), m normal
+        if (mb >= 0x00800000u && e > -126 && e < 127) {
+          f = __uint_as_float(static_cast<uint32_t>(127 - e) << 23);  // 2^-e, a normal float
+        } else {
+          (void)frexpf(m, &e);
+          pow2 = false;
+        }
+        E += e;
+      }
       const int t_k = reinterpret_cast<const int32_t*>(y + Vp)[kMaxBeam];
       BeamState& nbm = S.st[cur ^ 1];
-      if (lane < nb) {
+      if (valid) {
         const uint32_t idx = key_index(mine);
+        float pbv, pnbv;
         if (idx < static_cast<uint32_t>(B)) {  // a stay
           const int i = static_cast<int>(idx);
-          nbm.pb[lane] = S.stay_b[i];
-          nbm.pnb[lane] = S.stay_nb[i];
-          nbm.node[lane] = ob.node[i];
-          nbm.pnode[lane] = ob.pnode[i];
-          nbm.len[lane] = ob.len[i];
-          nbm.last[lane] = ob.last[i];
-          nbm.h[lane] = ob.h[i];
-          nbm.hp[lane] = ob.hp[i];
+          pbv = S.stay_b[i];
+          pnbv = S.stay_nb[i];
+          nbm.node[slot] = ob.node[i];
+          nbm.pnode[slot] = ob.pnode[i];
+          nbm.len[slot] = ob.len[i];
+          nbm.last[slot] = ob.last[i];
+          nbm.h[slot] = ob.h[i];
+          nbm.hp[slot] = ob.hp[i];
         } else {  // a growth: a new node of the prefix tree
           const int r = static_cast<int>(idx) - B;  // i * V + c with i < 16: exact in a float
           int i = static_cast<int>(static_cast<float>(r) * invV);
           if (i * V > r) --i;
           if ((i + 1) * V <= r) ++i;
           const int c = r - i * V;
-          const int id = 1 + k * B + lane;
+          const int id = 1 + k * B + slot;
           A.nparent[nbase + id] = ob.node[i];
           A.nlabel[nbase + id] = c;
           A.nframe[nbase + id] = t_k;
-          nbm.pb[lane] = 0.0f;
-          nbm.pnb[lane] = key_value(mine);
-          nbm.node[lane] = id;
-          nbm.pnode[lane] = ob.node[i];
-          nbm.len[lane] = ob.len[i] + 1;
-          nbm.last[lane] = c;
-          nbm.h[lane] = grow_hash(ob.h[i], c);
-          nbm.hp[lane] = ob.h[i];
+          pbv = 0.0f;
+          pnbv = key_value(mine);
+          nbm.node[slot] = id;
+          nbm.pnode[slot] = ob.node[i];
+          nbm.len[slot] = ob.len[i] + 1;
+          nbm.last[slot] = c;
+          nbm.h[slot] = grow_hash(ob.h[i], c);
+          nbm.hp[slot] = ob.h[i];
         }
-      }
-      // Rescale by a power of two: the largest total into [0.5, 1). The
-      // largest total is the value of the first selected key (stays: the
-      // same sum; growths: 0 + value).
-      const float m = __uint_as_float(__shfl_sync(kFull, static_cast<unsigned>(mine >> 32), 0));
-      if (m > 0.0f) {
-        const uint32_t mb = __float_as_uint(m);
-        int e = static_cast<int>((mb >> 23) & 0xffu) - 126;  // m = f * 2^e, f in [0.5, 1), m normal
-        if (mb >= 0x00800000u && e > -126 && e < 127) {
-          const float f = __uint_as_float(static_cast<uint32_t>(127 - e) << 23);  // 2^-e, a normal float
-          if (lane < nb) {
-            nbm.pb[lane] = nbm.pb[lane] * f;
-            nbm.pnb[lane] = nbm.pnb[lane] * f;
-          }
-        } else {
-          (void)frexpf(m, &e);
-          if (lane < nb) {
-            nbm.pb[lane] = ldexpf(nbm.pb[lane], -e);
-            nbm.pnb[lane] = ldexpf(nbm.pnb[lane], -e);
-          }
+        if (m > 0.0f) {
+          pbv = pow2 ? pbv * f : ldexpf(pbv, -e);
+          pnbv = pow2 ? pnbv * f : ldexpf(pnbv, -e);
         }
-        E += e;
+        nbm.pb[slot] = pbv;
+        nbm.pnb[slot] = pnbv;
       }
       // Clear last frame's merge bits; then for each new hypothesis j (lane
       // 16 + j) the hypothesis i (lane i) whose prefix is j's minus its last
