@@ -682,25 +682,21 @@ class Aligner:
         return int(res.status[0]), float(total.cpu()[0])
 
     def wait_packed(self, res: PackedResult) -> None:
-        """Block until every request of a packed batch is done; fills res.status."""
-        if res.request_ids.size <= 16:  # few requests: a blocking poll each
-            for i, rid in enumerate(res.request_ids.tolist()):
-                if res.status[i] == ALIGN_PENDING:
-                    rc, code = align_poll(self.ctx, rid, -1)
-                    if rc == ALIGN_OK:
-                        self._finish(rid, code)
-            if not (res.status == ALIGN_PENDING).any():
+        """Block until every request of a packed batch is done; fills res.status.
+        Blocks on the batch of its last pending request only (batches launched
+        after it keep running), then sweeps the finished statuses."""
+        ids = res.request_ids
+        while True:
+            pend = np.nonzero(res.status == ALIGN_PENDING)[0]
+            if pend.size == 0:
                 return
-        st = self._waiter()
-        self.join(st)
-        st.synchronize()
-        while (res.status == ALIGN_PENDING).any():
-            got = align_poll_done(self.ctx, max(4096, 2 * int((res.status == ALIGN_PENDING).sum())))
-            for rid, code in got:
+            rid = int(ids[pend[-1]])
+            rc, code = align_poll(self.ctx, rid, -1)
+            if rc == ALIGN_OK:
                 self._finish(rid, code)
-            if not got:
-                self.join(st)
-                st.synchronize()
+            if (res.status == ALIGN_PENDING).any():
+                for rid2, code2 in align_poll_done(self.ctx, max(4096, 2 * pend.size)):
+                    self._finish(rid2, code2)
 
     def wait(self, results) -> None:
         """Block until every result in `results` is done: one device-side join
