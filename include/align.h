@@ -48,6 +48,7 @@ extern "C" {
 #define ALIGN_E_CUDA (-8)        /* a CUDA runtime call failed (align_last_error has the text) */
 #define ALIGN_E_NOTFOUND (-9)    /* unknown request id (never submitted or already polled) */
 #define ALIGN_E_NOMEM (-10)      /* device or pinned allocation failed at create time */
+#define ALIGN_E_NONFINITE (-11)  /* NaN or +inf in the emissions (found only under ALIGN_F_DEBUG_CHECKS) */
 
 /* ---- configuration ----------------------------------------------------- */
 #define ALIGN_F_BATCHED 0x1u          /* submit only queues; align_flush (or poll) launches the
@@ -57,6 +58,11 @@ extern "C" {
 #define ALIGN_F_NO_GRID_TEAMS 0x8u    /* transcripts beyond one thread-block cluster use larger
                                          K per lane instead of a grid team (a cooperative launch of
                                          one 16-warp CTA per SM linked through global memory) */
+#define ALIGN_F_DEBUG_CHECKS 0x10u    /* every submit scans its [T, C] emissions for NaN and +inf
+                                         (-inf, log 0, stays allowed) and returns ALIGN_E_NONFINITE;
+                                         a device scan plus a synchronisation per request, or a host
+                                         scan for host inputs. Off by default: without it such inputs
+                                         give unspecified (but in-bounds) results. */
 #define ALIGN_F_TEST_STALL 0x80000000u /* testing the device watchdog only: in every request whose
                                          trellis spans more than one warp, the first warp never
                                          hands its values on, so the next warp's bounded wait runs

@@ -4,6 +4,7 @@
 // request's outputs out, instead of one cudaMemcpyAsync per buffer. Each CTA
 // takes whole chunks (at most kCopyChunk bytes); 16-byte vectors when source,
 // destination and size allow, else 4-byte words, else bytes.
+#include <cmath>
 #include <cstdint>
 
 #include <cuda_runtime.h>
@@ -38,6 +39,28 @@ __global__ void __launch_bounds__(256) copy_chunks_kernel(const CopyChunk* __res
 }
 
 }  // namespace
+
+// Any NaN or +inf among n floats: *flag becomes 1 (-inf, log 0, is allowed).
+__global__ void __launch_bounds__(256) scan_nonfinite_kernel(const float* __restrict__ p, int64_t n,
+                                                             int32_t* __restrict__ flag) {
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  bool bad = false;
+  for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const float x = p[i];
+    bad |= (x != x) || (x == INFINITY);
+  }
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) *flag = 1;
+}
+
+int launch_scan_nonfinite(const float* p, int64_t n, int32_t* d_flag, int sm_count, void* stream) {
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemsetAsync(d_flag, 0, sizeof(int32_t), st);
+  if (e != cudaSuccess || n <= 0) return e;
+  const int64_t want = (n + 255) / 256;
+  const int grid = static_cast<int>(want < 4 * sm_count ? want : 4 * sm_count);
+  scan_nonfinite_kernel<<<grid, 256, 0, st>>>(p, n, d_flag);
+  return cudaGetLastError();
+}
 
 int launch_copy_chunks(const CopyChunk* d_chunks, int n, int sm_count, void* stream) {
   if (n <= 0) return cudaSuccess;

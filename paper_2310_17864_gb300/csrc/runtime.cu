@@ -201,6 +201,8 @@ struct align_ctx {
   Arena stage_arena;
   char* h_pinned = nullptr;
   Arena pinned_arena;
+  int32_t* d_check = nullptr;  // ALIGN_F_DEBUG_CHECKS: result word of the emission scan
+  int32_t* h_check = nullptr;
 
   std::vector<GraphEntry> graphs;
   std::unordered_map<uint64_t, Request> reqs;
@@ -928,6 +930,20 @@ int submit_common(align_ctx* ctx, const float* lp, int64_t T, int64_t C, const i
   int64_t R = 0;
   int rc = validate_request(targets, L, C, blank, T, &R);
   if (rc != ALIGN_OK) return rc;
+  if (ctx->flags & ALIGN_F_DEBUG_CHECKS) {  // NaN / +inf scan of the emissions
+    const int64_t nv = T * C;
+    const float* dv = host_io ? static_cast<const float*>(device_alias(ctx, lp)) : lp;
+    if (host_io && !dv) {
+      for (int64_t i = 0; i < nv; ++i)
+        if (std::isnan(lp[i]) || lp[i] == INFINITY) return ALIGN_E_NONFINITE;
+    } else {
+      const int e = launch_scan_nonfinite(dv, nv, ctx->d_check, ctx->num_sms, ctx->main);
+      if (e != cudaSuccess) return set_error("scan_nonfinite", static_cast<cudaError_t>(e)), ALIGN_E_CUDA;
+      CU(cudaMemcpyAsync(ctx->h_check, ctx->d_check, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->main));
+      CU(cudaStreamSynchronize(ctx->main));
+      if (*ctx->h_check) return ALIGN_E_NONFINITE;
+    }
+  }
   if (static_cast<int64_t>(inflight_count(ctx)) >= ctx->max_inflight) {
     rc = pump(ctx, true);
     if (rc != ALIGN_OK) return rc;
@@ -1023,6 +1039,14 @@ int align_create(align_ctx** out, const align_config* cfg_in) {
     return ALIGN_E_NOMEM;
   }
   ctx->pinned_arena.init(pin_bytes);
+  if (cudaMalloc(&ctx->d_check, 256) != cudaSuccess || cudaMallocHost(&ctx->h_check, 256) != cudaSuccess) {
+    cudaFree(ctx->d_bp);
+    cudaFree(ctx->d_meta);
+    cudaFree(ctx->d_stage);
+    cudaFree(ctx->d_check);
+    cudaFreeHost(ctx->h_pinned);
+    return ALIGN_E_NOMEM;
+  }
   if (cfg.cuda_stream) {
     ctx->main = static_cast<cudaStream_t>(cfg.cuda_stream);
   } else {
@@ -1070,6 +1094,8 @@ int align_destroy(align_ctx* ctx) {
   cudaFree(ctx->d_meta);
   cudaFree(ctx->d_stage);
   cudaFreeHost(ctx->h_pinned);
+  cudaFree(ctx->d_check);
+  cudaFreeHost(ctx->h_check);
   delete ctx;
   return ALIGN_OK;
 }
@@ -1238,6 +1264,7 @@ const char* align_status_string(int32_t code) {
     case ALIGN_E_CUDA: return "ALIGN_E_CUDA";
     case ALIGN_E_NOTFOUND: return "ALIGN_E_NOTFOUND";
     case ALIGN_E_NOMEM: return "ALIGN_E_NOMEM";
+    case ALIGN_E_NONFINITE: return "ALIGN_E_NONFINITE";
     default: return "ALIGN_E_UNKNOWN";
   }
 }

@@ -157,5 +157,7 @@ struct alignas(16) CopyChunk {
 };
 constexpr uint64_t kCopyChunk = 256ull << 10;  // bytes per chunk at most
 int launch_copy_chunks(const CopyChunk* d_chunks, int n, int sm_count, void* stream);
+// *d_flag = 1 when one of the n floats at p is NaN or +inf, else 0 (asynchronous).
+int launch_scan_nonfinite(const float* p, int64_t n, int32_t* d_flag, int sm_count, void* stream);
 
 }  // namespace gb300_align

@@ -34,10 +34,24 @@ def test_exports_every_declared_symbol():
 
 
 def test_status_strings():
-    for code in range(-10, 2):
+    for code in range(-11, 2):
         s = align.status_string(code)
-        assert s.startswith("ALIGN_")
+        assert s.startswith("ALIGN_") and s != "ALIGN_E_UNKNOWN", code
     assert align.status_string(-6) == "ALIGN_E_NOPATH"
+    assert align.status_string(align.ALIGN_E_NONFINITE) == "ALIGN_E_NONFINITE"
+
+
+def test_header_constants_match_binding():
+    """Every ALIGN_E_* / ALIGN_F_* / ALIGN_REQ_* value in include/align.h has
+    the same value in the binding."""
+    import re
+    hdr = open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "align.h")).read()
+    found = 0
+    for name, val in re.findall(r"#define (ALIGN_(?:E|F|REQ)_[A-Z_]+) \(?(-?0x[0-9a-fA-F]+|-?\d+)u?\)?", hdr):
+        v = int(val, 16) if "0x" in val.lower() else int(val)
+        assert getattr(align, name) == v, name
+        found += 1
+    assert found >= 18
 
 
 def test_validate_agrees_with_oracle():

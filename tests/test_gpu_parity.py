@@ -116,6 +116,35 @@ def test_validation_errors(al):
         assert e.value.code == code
 
 
+def test_debug_checks_reject_nan_and_plus_inf():
+    """ALIGN_F_DEBUG_CHECKS: NaN or +inf anywhere in the emissions (device or
+    host inputs, log-probabilities or logits) fails the submit with
+    ALIGN_E_NONFINITE; -inf (log 0) still aligns, as the oracle does."""
+    build.build()
+    a = align.Aligner(device=0, debug_checks=True, bp_budget_bytes=1 << 30)
+    try:
+        u = synth.make_utterance(77, 300, 32, 60)
+        for bad in (float("nan"), float("inf")):
+            lp = u.lp.clone()
+            lp[123, 7] = bad
+            for where in ("cuda", "cpu"):
+                with pytest.raises(align.AlignError) as e:
+                    if where == "cuda":
+                        a.submit(lp.cuda(), u.targets, 0)
+                    else:
+                        a.submit_host(lp.pin_memory(), u.targets, 0)
+                assert e.value.code == align.ALIGN_E_NONFINITE, (bad, where)
+            with pytest.raises(align.AlignError) as e:
+                a.submit(lp.cuda(), u.targets, 0, logits=True)
+            assert e.value.code == align.ALIGN_E_NONFINITE
+        lp = u.lp.clone()
+        lp[200:210, 5] = float("-inf")
+        run(a, lp.numpy(), u.targets, 0, "debug -inf")
+        run(a, u.lp.numpy(), u.targets, 0, "debug clean")
+    finally:
+        a.close()
+
+
 @pytest.mark.parametrize("K,cw", [(2, 1), (2, 2), (2, 8), (2, 16), (4, 1), (4, 16), (8, 4), (16, 2)])
 def test_launch_shapes_bit_identical(K, cw):
     """Every (states per lane, warps per CTA) shape, including one-warp CTAs in
