@@ -255,7 +255,7 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
 
-    if args.impl == "reference":
+    if args.impl == "reference":  # the CPU oracle: rank 0 alone runs and prints it
         if rank == 0:
             reference_arm(args, wl)
         return
@@ -271,7 +271,7 @@ def main():
 
     import __graft_entry__
     __graft_entry__.build()
-    from paper_2310_17864_gb300 import align, autotune, synth
+    from paper_2310_17864_gb300 import align, autotune, replicas, synth
 
     if args.profile_beam:  # only decoder calls (vocabulary 500, beam 10), for profilers
         nb = args.profile_beam
@@ -356,13 +356,10 @@ def main():
     launches = (al.stats()["kernel_launches"] - l0) // max(args.steps, 1)
     tp_batches = (al.stats()["throughput_batches"] - tp0) / max(args.steps, 1)
     torch.cuda.synchronize()
-    ms = statistics.mean(times)
+    ms = replicas.slowest(statistics.mean(times), dist, dev)  # the slowest rank's step
     if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
         dist.barrier()
-    value = world * cells / (ms / 1e3)
+    value = replicas.job_rate(cells, world, ms)
 
     # Token spans (per transcript token: start, end, mean score) of this batch's
     # alignments: one packed call, timed with events on its stream.
@@ -591,18 +588,19 @@ def main():
             prev = pr
         ha.wait_packed(prev)
         assert (prev.status == 0).all()
-        e_ms = 1e3 * (time.perf_counter() - t0) / n_pipe
+        e_ms = replicas.slowest(1e3 * (time.perf_counter() - t0) / n_pipe, dist, dev)
+        sync_ms = replicas.slowest(sync_ms, dist, dev)
         ha.close()
-        e2e = {"value": world * cells / (e_ms / 1e3), "unit": "cells/s", "h2d_bytes_per_step": h2d,
+        e2e = {"value": replicas.job_rate(cells, world, e_ms), "unit": "cells/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "ms_per_step": e_ms, "steps_in_flight": 2,
-               "one_step_at_a_time": {"ms_per_step": sync_ms, "value": world * cells / (sync_ms / 1e3)}}
+               "one_step_at_a_time": {"ms_per_step": sync_ms, "value": replicas.job_rate(cells, world, sync_ms)}}
 
     serving = None
     if not args.no_serving and args.workload == "batch64":
         from paper_2310_17864_gb300 import serve
         serving = serving_run(align, serve, synth, autotune, dev, args.serving_requests)
 
-    if rank != 0:
+    if not replicas.prints(rank):
         al.close()
         if dist:
             dist.destroy_process_group()
