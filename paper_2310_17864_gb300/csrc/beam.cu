@@ -330,25 +330,15 @@ __global__ void __launch_bounds__(kThreads) beam_kernel(const BeamArgs A) {
     // ---- S2 (all threads): growths above theta ----
     {
       const uint64_t theta = S.theta;
-      float bs[kMaxBeam], bpb[kMaxBeam];
-      int blast[kMaxBeam];
-#pragma unroll
-      for (int i = 0; i < kMaxBeam; ++i) {
-        if (i < n) {
-          bs[i] = S.s[i];
-          bpb[i] = ob.pb[i];
-          blast[i] = ob.last[i];
-        }
-      }
       for (int c = tid; c < V; c += kThreads) {
         if (c == blank) continue;
         const float yc = y[c];
         unsigned hit = 0;  // hypotheses whose growth by c reaches theta
-#pragma unroll
-        for (int i = 0; i < kMaxBeam; ++i) {
-          const float base = (blast[i] == c) ? bpb[i] : bs[i];
+#pragma unroll 4
+        for (int i = 0; i < n; ++i) {
+          const float base = (ob.last[i] == c) ? ob.pb[i] : S.s[i];
           const uint64_t key = make_key(base * yc, static_cast<uint32_t>(B + i * V + c));
-          hit |= (i < n && key >= theta) ? (1u << i) : 0u;
+          hit |= (key >= theta) ? (1u << i) : 0u;
         }
         while (hit) {  // rare: recompute the key and append it unless merged
           const int i = __ffs(hit) - 1;
