@@ -471,7 +471,7 @@ def main():
                 su_times.append(e0.elapsed_time(e1))
         su_ms = statistics.mean(su_times)
         sum_line = {"ms": su_ms, "cells_per_s": cells / (su_ms / 1e3), "viterbi_ms": ms,
-                    "note": "log-add (max factored out, __expf/__logf) in place of the max; total only"}
+                    "note": "log-add in base 2 (max factored out, hardware ex2 / lg2) in place of the max; total only"}
 
     # CTC beam search with blank collapse (the paper's CUDA decoder setting:
     # vocabulary 500, beam 10, batch 4; and a batch of 2 utterances per SM),

@@ -22,6 +22,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cfloat>
 #include <cstdint>
 
 #include "trellis.cuh"
@@ -348,14 +349,30 @@ __device__ void log_softmax_shifts(const float* rows, int nf, int C, int lane, f
 // log(exp x + exp y) and log(exp x + exp y + exp z) in FP32 with the maximum
 // factored out (fast exponential and logarithm intrinsics; a sum of -inf
 // terms only is -inf).
-__device__ __forceinline__ float log_add2(float x, float y) {
-  const float m = fmaxf(x, y);
-  return (m == -INFINITY) ? -INFINITY : m + __logf(__expf(x - m) + __expf(y - m));
+// Sum-product in base 2: values are log2 of probabilities, so the log-add
+// needs only the hardware 2^x and log2(x) (PTX ex2.approx / lg2.approx, no
+// flush to zero). The largest term is factored out; clamping it to -FLT_MAX
+// turns "every term -inf" into m + log2(0) = -inf without a branch.
+__device__ __forceinline__ float ex2_approx(float x) {
+  float r;
+  asm("ex2.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
 }
-__device__ __forceinline__ float log_add3(float x, float y, float z) {
-  const float m = fmaxf(fmaxf(x, y), z);
-  return (m == -INFINITY) ? -INFINITY : m + __logf(__expf(x - m) + __expf(y - m) + __expf(z - m));
+__device__ __forceinline__ float lg2_approx(float x) {
+  float r;
+  asm("lg2.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
 }
+__device__ __forceinline__ float log2_add2(float x, float y) {
+  const float m = fmaxf(fmaxf(x, y), -FLT_MAX);
+  return m + lg2_approx(ex2_approx(x - m) + ex2_approx(y - m));
+}
+__device__ __forceinline__ float log2_add3(float x, float y, float z) {
+  const float m = fmaxf(fmaxf(fmaxf(x, y), z), -FLT_MAX);
+  return m + lg2_approx(ex2_approx(x - m) + ex2_approx(y - m) + ex2_approx(z - m));
+}
+constexpr float kLog2e = 1.4426950408889634f;  // log2(e): natural-log emissions to base 2
+constexpr float kLn2 = 0.6931471805599453f;    // ln(2): the base-2 total back to natural log
 
 // One backpointer row (NW = 3 or 6 words) stored by the lane that buffered it.
 template <int K, int NWB>
@@ -384,8 +401,8 @@ __device__ __forceinline__ void store_bp_row(uint32_t* dst, const uint32_t (&w)[
 // own code).
 //
 // kSum: the sum-product variant: log-add in place of the max (no
-// backpointers, anchors or backtrack); the job's total is the log-add of the
-// two final states.
+// backpointers, anchors or backtrack), in base 2 (log2 of probabilities);
+// the job's total is the log-add of the two final states, back in natural log.
 template <int K, bool kOcc, bool kGrid, bool kNorm, bool kSum>
 __global__ void __launch_bounds__(512, (kOcc && K <= 4) ? 2 : 1)
     trellis_kernel(const FwdJob* __restrict__ jobs, const FwdParams P) {
@@ -545,6 +562,7 @@ __global__ void __launch_bounds__(512, (kOcc && K <= 4) ? 2 : 1)
         a[j] = (s == 0) ? __ldg(row + blank) - lse0 : ((s == 1 && S > 1) ? __ldg(row + col[0]) - lse0 : -INFINITY);
       else
         a[j] = (s == 0) ? __ldg(row + blank) : ((s == 1 && S > 1) ? __ldg(row + col[0]) : -INFINITY);
+      if constexpr (kSum) a[j] *= kLog2e;  // the sum-product runs in base 2
     }
   } else {
 #pragma unroll
@@ -818,11 +836,11 @@ __global__ void __launch_bounds__(512, (kOcc && K <= 4) ? 2 : 1)
         for (int j = K - 1; j >= 0; --j) {  // descending: a[j-1], a[j-2] still hold frame t-1
           const float p1 = (j == 0) ? left : a[j - 1];
           if ((j & 1) == 0) {
-            a[j] = log_add2(a[j], p1) + eb;
+            a[j] = log2_add2(a[j], p1) + eb * kLog2e;
           } else {
             const float p2raw = (j == 1) ? left : a[j - 2];
             const float p2 = __uint_as_float((__float_as_uint(p2raw) & skeep[j >> 1]) | sfill[j >> 1]);
-            a[j] = log_add3(a[j], p1, p2) + el[j >> 1];
+            a[j] = log2_add3(a[j], p1, p2) + el[j >> 1] * kLog2e;
           }
         }
         send_one(t, a[K - 1], s_last);
@@ -935,7 +953,7 @@ __global__ void __launch_bounds__(512, (kOcc && K <= 4) ? 2 : 1)
       const float f_blank = __ldcg(J.final2 + 1);
       const float f_lab = (S > 1) ? __ldcg(J.final2 + 0) : -INFINITY;
       s_cur = (S > 1 && f_lab > f_blank) ? S - 2 : S - 1;
-      const float tot = kSum ? log_add2(f_lab, f_blank) : ((S > 1 && f_lab > f_blank) ? f_lab : f_blank);
+      const float tot = kSum ? log2_add2(f_lab, f_blank) * kLn2 : ((S > 1 && f_lab > f_blank) ? f_lab : f_blank);
       if (lane == 0) {
         if (J.total) *J.total = tot;
         atomicCAS(J.status, kStPending, tot == -INFINITY ? kStNoPath : kStOk);

@@ -1,18 +1,21 @@
 """GPU parity of the sum-product variant (ALIGN_REQ_SUM): the CTC forward
 score over the same trellis, with log-add in place of the max.
 
-Tolerance. The kernel works in FP32: every cell is m + log(1 + e^(d1) + e^(d2))
-(m the largest predecessor, d <= 0) followed by one add of the emission. With
-__expf (relative error at most 2 + 1.173|d| ulp, so at most 2 ulp weighted by
-e^d) and __logf (absolute error at most 2^-21.41 on [0.5, 2], 3 ulp above), one
-log-add term is off by at most 2^-20 in absolute terms, and the two FP32 adds
-by 2^-24 of |alpha| each. The log-sum-exp is a convex combination in its
-inputs (its partial derivatives are non-negative and sum to one), so errors
-carried from frame t-1 do not grow: after frame t the error is at most
-err_{t-1} + 2^-23 A_t + 2^-20, where A_t = sum over tau <= t of
-max_c |lp[tau, c]| bounds every finite |alpha_t(s)|. The final log-add of
-the two end states adds one more term. The test uses that bound, summed over
-the frames, against the binary64 oracle.
+Tolerance. The kernel works in FP32 and in base 2 (log2 of probabilities):
+every cell is m + log2(2^(d1) + 2^(d2) + 2^(d3)) (m the largest predecessor,
+d <= 0) followed by one add of the emission times log2(e); the total is
+multiplied by ln(2) at the end. The hardware 2^x and log2(x) (PTX ex2.approx
+and lg2.approx) are accurate to about 2^-22 (relative, resp. absolute on the
+sums in [1, 3]), so one log-add is off by at most 2^-20; the adds and the
+base changes by 2^-24 of |alpha| each. The log-sum-exp is a convex
+combination in its inputs (its partial derivatives are non-negative and sum
+to one), so errors carried from frame t-1 do not grow: after frame t the
+error is at most err_{t-1} + 2^-23 A_t + 2^-20, where A_t = sum over tau <= t
+of max_c |lp[tau, c]| bounds every finite |alpha_t(s)| (natural-log units: a
+base-2 value is 1/ln 2 times larger and its errors shrink by ln 2 when the
+total is converted back).
+The final log-add and the conversion back add one more term. The test uses
+that bound, summed over the frames, against the binary64 oracle.
 """
 import numpy as np
 import pytest
