@@ -10,13 +10,13 @@
 // equal probabilities may come in any order. This work does not depend on
 // the beam and is taken off the serial frame loop.
 //
-// beam_kernel (one CTA of 256 threads per utterance):
+// beam_kernel (one CTA of 512 threads per utterance):
 // Prologue (blank collapse): frame t is a blank frame when P[t, blank] > a;
 // a blank frame that follows a blank frame is dropped (every run of blank
 // frames shrinks to its first frame). A block-wide ballot scan writes the
 // kept frame indices to the workspace.
 // Per kept frame (the row and its ranked labels staged in shared memory with
-// cp.async, two frames ahead, a ring of four):
+// cp.async by warp 1, two frames ahead, a ring of four):
 //   S1 (warp 0): every hypothesis' stay (blank: (pb + pnb) * y[blank];
 //      repeat of its last label z: pnb * y[z]; plus the growth of the
 //      hypothesis whose prefix is this one's minus its last label), and
@@ -48,7 +48,8 @@
 namespace gb300_align {
 namespace {
 
-constexpr int kThreads = 256;
+constexpr int kThreads = 512;   // 16 warps: the growth test is latency-bound, more warps hide it
+constexpr int kRankThreads = 256;
 constexpr int kMaxBeam = 16;   // hypotheses per utterance at most (one lane per stay / growth)
 constexpr int kRowRing = 4;    // staged rows
 constexpr int kAhead = 2;      // rows in flight ahead of the one in use
@@ -116,6 +117,14 @@ __device__ __forceinline__ void cp_async16b(void* dst, const void* src) {
   const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
 }
+// Named barrier 1 between warp 0 (waits) and warp 1 (arrives after its
+// copies completed): orders the staged row before warp 0's reads.
+__device__ __forceinline__ void named_sync(int id, int nthreads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+__device__ __forceinline__ void named_arrive(int id, int nthreads) {
+  asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_wait() {
@@ -145,11 +154,11 @@ struct BeamShared {
 
 // The B largest non-blank labels of every frame (by probability; equal
 // probabilities in any order), one warp per frame.
-__global__ void __launch_bounds__(kThreads) rank_kernel(const float* __restrict__ probs, int64_t total_frames,
+__global__ void __launch_bounds__(kRankThreads) rank_kernel(const float* __restrict__ probs, int64_t total_frames,
                                                         int V, int blank, int B, int32_t* __restrict__ topl) {
   const int lane = threadIdx.x & 31;
-  const int64_t wstride = static_cast<int64_t>(gridDim.x) * (kThreads / 32);
-  for (int64_t g = static_cast<int64_t>(blockIdx.x) * (kThreads / 32) + (threadIdx.x >> 5); g < total_frames;
+  const int64_t wstride = static_cast<int64_t>(gridDim.x) * (kRankThreads / 32);
+  for (int64_t g = static_cast<int64_t>(blockIdx.x) * (kRankThreads / 32) + (threadIdx.x >> 5); g < total_frames;
        g += wstride) {
     const float* y = probs + g * V;
     // Lane head: its largest (value, ~label) key below the last one it gave.
@@ -225,8 +234,9 @@ __global__ void __launch_bounds__(kThreads) beam_kernel(const BeamArgs A) {
   __syncthreads();  // kept[] visible to every thread (global writes of this block)
 
   const bool vec = (V & 3) == 0 && (reinterpret_cast<uintptr_t>(A.probs) & 15) == 0;
-  // Rows are staged by warp 0 alone (its own cp.async groups), so that warp 0
-  // can wait for the next row at the end of a frame without a block barrier.
+  // Rows are staged by warp 1 alone (its own cp.async groups) while warp 0
+  // selects; a named barrier hands each staged row to warp 0 without a
+  // block barrier.
   auto issue_row = [&](int k, int t) {
     if (k < K) {
       const float* src = P + static_cast<int64_t>(t) * V;
@@ -293,7 +303,7 @@ __global__ void __launch_bounds__(kThreads) beam_kernel(const BeamArgs A) {
   };
 
   int n = 1, cur = 0, E = 0;  // uniform across the block
-  int t_pref = 0;             // warp 0: frame index of the next row to stage
+  int t_pref = 0;             // warp 1: frame index of the next row to stage
   const float invV = 1.0f / static_cast<float>(V);
   if (warp == 0) {
     if (lane == 0) {
@@ -315,12 +325,13 @@ __global__ void __launch_bounds__(kThreads) beam_kernel(const BeamArgs A) {
       S.match[lane] = -1;
       S.mword[lane] = -1;
     }
+  } else if (warp == 1) {  // rows are staged by warp 1 (its own cp.async groups)
     for (int k = 0; k < kAhead; ++k) issue_row(k, k < K ? kept[k] : 0);
     t_pref = kAhead < K ? kept[kAhead] : 0;
     cp_wait<kAhead - 1>();
-    __syncwarp();
-    if (K > 0) stage1(0, 0, 1);
   }
+  __syncthreads();  // row 0 staged, the initial beam written
+  if (warp == 0 && K > 0) stage1(0, 0, 1);
   __syncthreads();
 
   for (int k = 0; k < K; ++k) {
@@ -510,12 +521,15 @@ __global__ void __launch_bounds__(kThreads) beam_kernel(const BeamArgs A) {
         S.mword[e16] = w;
       }
       if (lane == 0) S.nlive = nb;
-      // Next frame: stage row k + 2, wait for row k + 1, run its S1.
+      // Next frame's S1 once warp 1 has staged its row (named barrier 1).
+      named_sync(1, 64);
+      if (k + 1 < K) stage1(k + 1, cur ^ 1, nb);
+    } else if (warp == 1) {
+      // Meanwhile: stage row k + 2, wait for row k + 1, signal warp 0.
       issue_row(k + kAhead, t_pref);
       t_pref = (k + kAhead + 1 < K) ? kept[k + kAhead + 1] : 0;  // used one frame later
       cp_wait<kAhead - 1>();
-      __syncwarp();
-      if (k + 1 < K) stage1(k + 1, cur ^ 1, nb);
+      named_arrive(1, 64);
     }
     cur ^= 1;
     __syncthreads();  // the new beam, its merges, theta and the next row are visible to every warp
@@ -624,9 +638,9 @@ int align_ctc_beam_decode(const float* probs, const int64_t* frame_offsets, int3
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (total_frames > 0) {
-    const int64_t blocks = std::min<int64_t>((total_frames + kThreads / 32 - 1) / (kThreads / 32),
+    const int64_t blocks = std::min<int64_t>((total_frames + kRankThreads / 32 - 1) / (kRankThreads / 32),
                                              static_cast<int64_t>(std::max(sms, 1)) * 8);
-    rank_kernel<<<static_cast<unsigned>(blocks), kThreads, 0, st>>>(probs, total_frames, V, blank, beam, topl);
+    rank_kernel<<<static_cast<unsigned>(blocks), kRankThreads, 0, st>>>(probs, total_frames, V, blank, beam, topl);
   }
   beam_kernel<<<n, kThreads, smem, st>>>(a);
   return cudaGetLastError() == cudaSuccess ? ALIGN_OK : ALIGN_E_CUDA;
