@@ -99,6 +99,20 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
+// Potentially blocking test: the thread may be suspended until the phase
+// completes or about `ns` nanoseconds pass (then false), so a waiting warp
+// leaves its scheduler's issue slots to the others.
+__device__ __forceinline__ bool mbar_try_wait_suspend(uint64_t* bar, uint32_t parity, uint32_t ns) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity), "r"(ns)
+      : "memory");
+  return ok != 0;
+}
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
   asm volatile(
       "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
@@ -135,7 +149,7 @@ __device__ bool wait_phase(uint64_t* bar, uint32_t parity, volatile int32_t* abo
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = gtimer();
   for (;;) {
-    if (mbar_try_wait(bar, parity)) return true;
+    if (mbar_try_wait_suspend(bar, parity, 10000u)) return true;
     if (honour_abort && *abort) return false;
     if (gtimer() - t0 > limit) {
       *abort = 1;
