@@ -377,13 +377,21 @@ __device__ __forceinline__ float lg2_approx(float x) {
   asm("lg2.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
   return r;
 }
+// The largest term contributes 2^0 = 1 (0 when every term is -inf), so only
+// the others need an exponential.
 __device__ __forceinline__ float log2_add2(float x, float y) {
-  const float m = fmaxf(fmaxf(x, y), -FLT_MAX);
-  return m + lg2_approx(ex2_approx(x - m) + ex2_approx(y - m));
+  const float mr = fmaxf(x, y);
+  const float m = fmaxf(mr, -FLT_MAX);
+  const float one = (mr == -INFINITY) ? 0.0f : 1.0f;
+  return m + lg2_approx(one + ex2_approx(fminf(x, y) - m));
 }
 __device__ __forceinline__ float log2_add3(float x, float y, float z) {
-  const float m = fmaxf(fmaxf(fmaxf(x, y), z), -FLT_MAX);
-  return m + lg2_approx(ex2_approx(x - m) + ex2_approx(y - m) + ex2_approx(z - m));
+  const float lo = fminf(x, y), hi = fmaxf(x, y);
+  const float mr = fmaxf(hi, z);
+  const float mid = fminf(hi, z);  // with lo, the two terms below the largest
+  const float m = fmaxf(mr, -FLT_MAX);
+  const float one = (mr == -INFINITY) ? 0.0f : 1.0f;
+  return m + lg2_approx(one + ex2_approx(lo - m) + ex2_approx(mid - m));
 }
 constexpr float kLog2e = 1.4426950408889634f;  // log2(e): natural-log emissions to base 2
 constexpr float kLn2 = 0.6931471805599453f;    // ln(2): the base-2 total back to natural log
