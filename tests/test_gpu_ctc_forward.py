@@ -2,8 +2,9 @@
 score over the same trellis, with log-add in place of the max.
 
 Tolerance. The kernel works in FP32 and in base 2 (log2 of probabilities):
-every cell is m + log2(2^(d1) + 2^(d2) + 2^(d3)) (m the largest predecessor,
-d <= 0) followed by one add of the emission times log2(e); the total is
+every cell is m + log2(1 + 2^(d1) + 2^(d2)) (m the largest predecessor, d <= 0
+the others' distance to it) followed by one add of the emission times
+log2(e); the total is
 multiplied by ln(2) at the end. The hardware 2^x and log2(x) (PTX ex2.approx
 and lg2.approx) are accurate to about 2^-22 (relative, resp. absolute on the
 sums in [1, 3]), so one log-add is off by at most 2^-20; the adds and the
