@@ -138,11 +138,11 @@ int align_submit_host(align_ctx *ctx, const float *log_probs, int64_t T, int64_t
                                  intrinsics, the maximum factored out of every log-add; no
                                  backpointers (no backpointer memory). Not combined with
                                  ALIGN_REQ_LOGITS (ALIGN_E_INVAL). */
-#define ALIGN_REQ_LOGITS 0x2u /* log_probs holds raw per-frame scores (logits): the kernel
-                                 applies log_softmax over each row as it stages it (one extra
-                                 warp per CTA: lse = m + logf(sum expf(x - m)), m the row
-                                 maximum, then x - lse in FP32), so no separate log_softmax
-                                 pass over [T][C] is needed; scores are then log-probabilities.
+#define ALIGN_REQ_LOGITS 0x2u /* log_probs holds raw per-frame scores (logits): a pre-pass
+                                 kernel computes each row's lse = m + logf(sum expf(x - m)), m
+                                 the row maximum, and the trellis kernel uses x - lse in FP32
+                                 as it reads the staged rows, so no log_softmax output [T][C]
+                                 is written or read again; scores are then log-probabilities.
                                  Results equal an alignment of those FP32 log-probabilities;
                                  they may differ from one of log-probabilities computed
                                  elsewhere by the rounding of expf / logf. */

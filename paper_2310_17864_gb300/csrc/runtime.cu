@@ -223,12 +223,11 @@ namespace {
 
 uint64_t inflight_count(const align_ctx* ctx) { return ctx->reqs.size(); }
 
-// Plan of a request with one tuning table. Logits requests get a normaliser
-// warp per CTA (so at most 15 compute warps) and a per-frame shift buffer.
+// Plan of a request with one tuning table. Logits requests get a per-frame
+// shift buffer (written by the lse pre-pass before their trellis launch).
 int plan_request(const align_ctx* ctx, const TuneTable& table, int64_t T, int64_t C, int64_t L, bool logits,
                  Plan* out, bool sum = false) {
   TuneTable t = table;
-  if (logits) t.max_warps = std::min(t.max_warps, 15);
   const int rc = make_plan(t, T, C, L, sum ? ~0ull : ctx->bp_arena.cap(),
                            !sum && (ctx->flags & ALIGN_F_FORCE_CHECKPOINT) != 0, out);
   if (rc != ALIGN_OK) return rc;

@@ -135,7 +135,7 @@ __device__ __forceinline__ void cp_async_mbar_arrive(uint64_t* bar) {
 struct SmemHead {
   uint64_t full[kMaxStages];   // emission stage filled
   uint64_t empty[kMaxStages];  // emission stage released by every warp
-  uint64_t normd[kMaxStages];  // logits mode: stage normalised by the normaliser warp
+  uint64_t normd[kMaxStages];  // unused (keeps the 256-byte head layout)
   int32_t abort;            // set by any thread of this CTA whose wait hit the limit
   uint32_t unused;
   uint64_t sink;            // scratch slot written by the last warp of the team
@@ -314,59 +314,11 @@ __device__ __forceinline__ void store_bp_words_if(uint32_t* dst, const uint32_t 
   }
 }
 
-// The log_softmax shift lse = m + logf(sum __expf(x - m)) of nf rows of C
-// logits (m the row maximum; the fast exponential intrinsic, whose error is
-// part of the stated tolerance), by one warp: lanes split into groups of lpr
-// lanes, one group per row (lpr = 32 / rows per pass); each lane takes every
-// lpr-th column. With one lane per row the lane starts its sweep at its own
-// column offset (rows of an even number of classes would otherwise put every
-// lane in the same shared-memory bank). Lane 0 of a group stores the row's
-// shift to lse_s[r] and, when given, lse_out[r]. The readers subtract it:
-// log-probability = x - lse, one FP32 subtraction.
-__device__ void log_softmax_shifts(const float* rows, int nf, int C, int lane, float* lse_s, float* lse_out) {
-  const int rpp = nf < 32 ? (nf < 1 ? 1 : nf) : 32;  // rows per pass
-  int lpr = 1;                                       // lanes per row: a power of two
-  while (lpr * 2 * rpp <= 32) lpr *= 2;
-  const int grp = lane / lpr, sub = lane % lpr;
-  const int groups = 32 / lpr;
-  const int rot = (lpr == 1 && (C & 1) == 0) ? lane % C : 0;  // first column of this lane's sweep
-  for (int r0 = 0; r0 < nf; r0 += groups) {
-    const int r = r0 + grp;
-    const bool live = r < nf;
-    const float* x = rows + static_cast<size_t>(live ? r : 0) * C;
-    float m = -INFINITY;
-    if (live) {
-      int c = sub + rot;
-      for (int k = sub; k < C; k += lpr, c += lpr) {
-        if (c >= C) c -= C;
-        m = fmaxf(m, x[c]);
-      }
-    }
-    for (int k = lpr >> 1; k > 0; k >>= 1) m = fmaxf(m, __shfl_xor_sync(kFull, m, k, lpr));
-    float sum = 0.0f;
-    if (live) {
-      int c = sub + rot;
-      for (int k = sub; k < C; k += lpr, c += lpr) {
-        if (c >= C) c -= C;
-        sum += __expf(x[c] - m);
-      }
-    }
-    for (int k = lpr >> 1; k > 0; k >>= 1) sum += __shfl_xor_sync(kFull, sum, k, lpr);
-    const float lse = m + logf(sum);
-    if (live && sub == 0) {
-      lse_s[r] = lse;
-      if (lse_out) lse_out[r] = lse;
-    }
-  }
-}
-
-// log(exp x + exp y) and log(exp x + exp y + exp z) in FP32 with the maximum
-// factored out (fast exponential and logarithm intrinsics; a sum of -inf
-// terms only is -inf).
 // Sum-product in base 2: values are log2 of probabilities, so the log-add
 // needs only the hardware 2^x and log2(x) (PTX ex2.approx / lg2.approx, no
 // flush to zero). The largest term is factored out; clamping it to -FLT_MAX
-// turns "every term -inf" into m + log2(0) = -inf without a branch.
+// and using 1 for the largest term (0 when every term is -inf) avoids both a
+// branch and one exponential.
 __device__ __forceinline__ float ex2_approx(float x) {
   float r;
   asm("ex2.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
@@ -418,9 +370,9 @@ __device__ __forceinline__ void store_bp_row(uint32_t* dst, const uint32_t (&w)[
 // (one per SM) instead of a thread-block cluster; the links between CTAs (the
 // boundary rings, progress words, barrier) are in global memory.
 //
-// kNorm: log_probs hold raw logits; each CTA has one more warp, the
-// normaliser (a separate instantiation so the log-probability path keeps its
-// own code).
+// kNorm: log_probs hold raw logits; the per-frame log_softmax shifts come
+// from lse_prepass_kernel and are subtracted as the emissions are used (a
+// separate instantiation so the log-probability path keeps its own code).
 //
 // kSum: the sum-product variant: log-add in place of the max (no
 // backpointers, anchors or backtrack), in base 2 (log2 of probabilities);
@@ -439,12 +391,12 @@ __global__ void __launch_bounds__(512, (kOcc && K <= 4) ? 2 : 1)
 
   const uint32_t ncta = kGrid ? static_cast<uint32_t>(max(P.grid_ctas, 1)) : cluster_nctarank();
   const uint32_t crank = kGrid ? blockIdx.x % ncta : cluster_ctarank();
-  // Logits mode (kNorm): the last warp of each CTA is a normaliser that
-  // turns each staged chunk of raw logits into log-probabilities in place
-  // before the W compute warps read it; it computes no states.
-  const int W = (blockDim.x >> 5) - (kNorm ? 1 : 0);
+  // Logits mode (kNorm): the per-frame log_softmax shifts come from the lse
+  // pre-pass (J.lse, written by lse_prepass_kernel before this launch); the
+  // warps subtract them from the staged raw logits as they use them.
+  const int W = blockDim.x >> 5;
   const int warp = threadIdx.x >> 5;
-  const bool is_norm = kNorm && warp == W;
+  constexpr bool is_norm = false;
   const int lane = threadIdx.x & 31;
   const FwdJob& J = jobs[blockIdx.x / ncta];
   const int g = static_cast<int>(crank) * W + warp;  // warp index in the team
@@ -492,7 +444,6 @@ __global__ void __launch_bounds__(512, (kOcc && K <= 4) ? 2 : 1)
     for (int st = 0; st < P.stages; ++st) {
       mbar_init(&head->full[st], bulk ? 1u : 32u);
       mbar_init(&head->empty[st], static_cast<uint32_t>(W));
-      mbar_init(&head->normd[st], 1u);
     }
     head->abort = 0;
     fence_barrier_init();
@@ -567,16 +518,7 @@ __global__ void __launch_bounds__(512, (kOcc && K <= 4) ? 2 : 1)
     // alpha_0: paths start in the blank (state 0) or the first label (state 1).
     const float* row = lp + static_cast<size_t>(t_begin) * C;
     float lse0 = 0.0f;
-    if (kNorm && g == 0) {  // logits mode: this row's log_softmax shift, by the first warp
-      float m = -INFINITY;
-      for (int c = lane; c < C; c += 32) m = fmaxf(m, __ldg(row + c));
-      for (int k = 16; k > 0; k >>= 1) m = fmaxf(m, __shfl_xor_sync(kFull, m, k));
-      float sum = 0.0f;
-      for (int c = lane; c < C; c += 32) sum += __expf(__ldg(row + c) - m);
-      for (int k = 16; k > 0; k >>= 1) sum += __shfl_xor_sync(kFull, sum, k);
-      lse0 = m + logf(sum);
-      if (lane == 0 && lse_g) lse_g[t_begin] = lse0;
-    }
+    if constexpr (kNorm) lse0 = __ldg(lse_g + t_begin);  // logits mode: this row's shift
 #pragma unroll
     for (int j = 0; j < K; ++j) {
       const int s = s0 + j;
@@ -721,8 +663,15 @@ __global__ void __launch_bounds__(512, (kOcc && K <= 4) ? 2 : 1)
   const bool write_bp = (bp != nullptr) && is_l0;
   const float* stage_f = reinterpret_cast<const float*>(stages);
   const int stage_floats = P.stage_bytes / 4;
-  float* const lse_s = reinterpret_cast<float*>(smem + P.off_lse);  // logits mode: [stages * F + 1]
-  int lidx = 0;           // logits mode: shift of frame t in lse_s
+  // Logits mode: lane i holds the shift of frame (window start + i) of the
+  // current anchor window (lse_win) and of the next one (lse_next), read from
+  // the pre-pass's J.lse one window ahead; a sub-run never crosses a window.
+  float lse_win = 0.0f, lse_next = 0.0f;
+  if constexpr (kNorm) {
+    const int fa = t_begin + 1 + lane, fb = t_begin + 1 + kAnchorD + lane;
+    lse_win = (fa < t_end) ? __ldg(lse_g + fa) : 0.0f;
+    lse_next = (fb < t_end) ? __ldg(lse_g + fb) : 0.0f;
+  }
   constexpr bool kBufBp = NW <= 6;  // K = 2, 4: a window's backpointer rows buffered in registers
   uint32_t wb[kBufBp ? NW : 1];
 #pragma unroll
@@ -734,26 +683,6 @@ __global__ void __launch_bounds__(512, (kOcc && K <= 4) ? 2 : 1)
   int roff = 0;
   int bi = 0;             // frame index within the current block
   int t = t_begin + 1;
-  if (kNorm && is_norm) {
-    // The normaliser: every chunk, once it has arrived, in stage order. The lse
-    // of each frame goes to J.lse (CTA 0 only) for the score gather.
-    int n_stage = 0;
-    uint32_t n_round = 0;
-    const float* const rows_all = reinterpret_cast<const float*>(stages);
-    for (int c = 0; c < nchunks; ++c) {
-      if (!warp_wait_phase(&head->full[n_stage], n_round & 1u, abort, limit, lane)) break;
-      const int f0 = t_begin + 1 + c * F;
-      log_softmax_shifts(rows_all + n_stage * stage_floats, min(F, t_end - f0), C, lane, lse_s + n_stage * F,
-                         (crank == 0 && lse_g) ? lse_g + f0 : nullptr);
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&head->normd[n_stage]);  // release: the shifts of this stage
-      if (++n_stage == P.stages) {
-        n_stage = 0;
-        ++n_round;
-      }
-    }
-    t = t_end;  // computes no frames
-  }
   while (t < t_end) {
     const int ft = t - t_begin - 1;  // frames computed so far
     if ((ft & (F - 1)) == 0) {       // first frame of a chunk
@@ -772,10 +701,9 @@ __global__ void __launch_bounds__(512, (kOcc && K <= 4) ? 2 : 1)
         }
       }
       if (__any_sync(kFull, *abort != 0)) break;
-      if (!warp_wait_phase(kNorm ? &head->normd[c_stage] : &head->full[c_stage], c_round & 1u, abort, limit, lane))
+      if (!warp_wait_phase(&head->full[c_stage], c_round & 1u, abort, limit, lane))
         break;
       ridx = c_stage * stage_floats;
-      if constexpr (kNorm) lidx = c_stage * F;
     }
     if ((ft & (B - 1)) == 0) {  // first frame of a receive block
       const int nb = min(B, t_end - t);
@@ -814,12 +742,6 @@ __global__ void __launch_bounds__(512, (kOcc && K <= 4) ? 2 : 1)
     float el_n[K / 2];
 #pragma unroll
     for (int q = 0; q < K / 2; ++q) el_n[q] = stage_f[ridx + col[q]];
-    if constexpr (kNorm) {  // log-probability = logit - the row's shift
-      const float sh = lse_s[lidx];
-      eb_n -= sh;
-#pragma unroll
-      for (int q = 0; q < K / 2; ++q) el_n[q] -= sh;
-    }
     // Backpointer words. NW <= 6: lane i keeps the words of the window's
     // frame i in registers and the warp stores a whole window at once (one
     // row per lane). Wider rows: lane 0 stores the words of the previous
@@ -832,22 +754,29 @@ __global__ void __launch_bounds__(512, (kOcc && K <= 4) ? 2 : 1)
     for (int j = 0; j < K / 2; ++j) pskp[j] = 0u;
     bool pend = false;
     const int fi0 = ft & (kAnchorD - 1);  // frame index of t within its window
+    if constexpr (kNorm) {
+      if (fi0 == 0 && ft != 0) {  // frame t starts a window: its shifts were read one window ago
+        lse_win = lse_next;
+        const int fn = t + kAnchorD + lane;
+        lse_next = (fn < t_end) ? __ldg(lse_g + fn) : 0.0f;
+      }
+    }
 #pragma unroll(K == 2 ? 4 : 1)
     for (int i = 0; i < n; ++i, ++t) {
-      const float eb = eb_n;
+      float eb = eb_n;
       float el[K / 2];
 #pragma unroll
       for (int q = 0; q < K / 2; ++q) el[q] = el_n[q];
+      if constexpr (kNorm) {  // log-probability = logit - the frame's shift
+        const float sh = __shfl_sync(kFull, lse_win, fi0 + i);
+        eb -= sh;
+#pragma unroll
+        for (int q = 0; q < K / 2; ++q) el[q] -= sh;
+      }
       ridx += C;
       eb_n = stage_f[ridx + blank];
 #pragma unroll
       for (int q = 0; q < K / 2; ++q) el_n[q] = stage_f[ridx + col[q]];
-      if constexpr (kNorm) {
-        const float sh = lse_s[++lidx];
-        eb_n -= sh;
-#pragma unroll
-        for (int q = 0; q < K / 2; ++q) el_n[q] -= sh;
-      }
 
       // alpha_{t-1}(s0 - 1) and its anchor: lane below by shuffle, lane 0 from the block.
       const float shf = __shfl_up_sync(kFull, a[K - 1], 1);
@@ -1119,6 +1048,26 @@ __global__ void __launch_bounds__(1024) frame_probe_kernel(int frames, uint64_t 
   }
 }
 
+// Logits mode: lse[t] = log(sum_c exp(logits[t][c])) of every frame of every
+// job, one warp per frame (the maximum factored out, fast exponential,
+// accurate logarithm), before the trellis launch reads them.
+__global__ void __launch_bounds__(256) lse_prepass_kernel(const FwdJob* __restrict__ jobs) {
+  const FwdJob& J = jobs[blockIdx.y];
+  const int lane = threadIdx.x & 31;
+  const int C = J.C;
+  const int64_t step = static_cast<int64_t>(gridDim.x) * 8;
+  for (int64_t t = J.t_begin + static_cast<int64_t>(blockIdx.x) * 8 + (threadIdx.x >> 5); t < J.t_end; t += step) {
+    const float* row = J.lp + t * C;
+    float m = -INFINITY;
+    for (int c = lane; c < C; c += 32) m = fmaxf(m, __ldg(row + c));
+    for (int k = 16; k > 0; k >>= 1) m = fmaxf(m, __shfl_xor_sync(kFull, m, k));
+    float sum = 0.0f;
+    for (int c = lane; c < C; c += 32) sum += __expf(__ldg(row + c) - m);
+    for (int k = 16; k > 0; k >>= 1) sum += __shfl_xor_sync(kFull, sum, k);
+    if (lane == 0) J.lse[t] = m + logf(sum);
+  }
+}
+
 template <int K, bool kOcc, bool kGrid, bool kNorm, bool kSum = false>
 cudaError_t launch_k(const LaunchShape& shape, const FwdParams& p, const FwdJob* d_jobs, int njobs,
                      cudaStream_t stream) {
@@ -1134,6 +1083,11 @@ cudaError_t launch_k(const LaunchShape& shape, const FwdParams& p, const FwdJob*
     if (njobs != 1) return cudaErrorInvalidValue;  // one team per cooperative launch
   }
   auto fn = trellis_kernel<K, kOcc, kGrid, kNorm, kSum>;
+  if constexpr (kNorm) {  // the per-frame shifts first, on the same stream
+    lse_prepass_kernel<<<dim3(128, static_cast<unsigned>(njobs), 1), 256, 0, stream>>>(d_jobs);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
   // The allowed maximum is always the device's opt-in limit, never the size
   // of the launch at hand: launches of one kernel captured into a graph ask
   // for different sizes, and none may see a limit lowered by another.
@@ -1142,7 +1096,7 @@ cudaError_t launch_k(const LaunchShape& shape, const FwdParams& p, const FwdJob*
   if (smem > smem_max) return cudaErrorInvalidValue;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(static_cast<unsigned>(njobs * shape.ncta), 1, 1);
-  cfg.blockDim = dim3(static_cast<unsigned>((shape.warps + (kNorm ? 1 : 0)) * 32), 1, 1);
+  cfg.blockDim = dim3(static_cast<unsigned>(shape.warps * 32), 1, 1);
   cfg.dynamicSmemBytes = static_cast<size_t>(smem);
   cfg.stream = stream;
   cudaLaunchAttribute attr[1];
@@ -1216,7 +1170,7 @@ FwdParams plan_params(const LaunchShape& shape, int C, int frames_per_stage, uin
   // One spare row after the last stage: the emission look-ahead of a chunk's
   // last frame reads (and discards) the row after it.
   p.off_lse = (p.off_stage + p.stages * p.stage_bytes + C * 4 + 15) & ~15;
-  p.off_bt = (p.off_lse + (shape.norm ? (p.stages * F + 1) * 4 : 0) + 127) & ~127;  // end of the forward region
+  p.off_bt = (p.off_lse + 127) & ~127;  // end of the forward region
   p.wait_limit_ns = wait_limit_ns;
   return p;
 }
