@@ -78,7 +78,7 @@ struct alignas(16) FwdJob {
   int32_t zstride;         // bytes per anchor row (multiple of 16, >= S)
   uint8_t* ztab;           // anchor rows: row m holds s - anchor(s) at the end of window m
   uint64_t* xlink;         // grid teams: links between consecutive CTAs (zeroed before launch)
-  float* lse;              // logits mode: per-frame log_softmax shift [T] (written by the kernel)
+  float* lse;              // logits mode: per-frame log_softmax shift [T] (written by the lse pre-pass)
 };
 
 struct FwdParams {
@@ -88,11 +88,11 @@ struct FwdParams {
   int32_t stage_bytes;     // bytes per emission stage (16-byte multiple)
   int32_t off_ring;        // shared-memory offsets
   int32_t off_stage;
-  int32_t off_lse;         // logits mode: per-stage row shifts, stages * F + 1 floats
+  int32_t off_lse;         // end of the stage ring and its spare row
   int32_t off_bt;
   int32_t stages;          // emission stages in the ring (kLead .. kMaxStages)
   int32_t grid_ctas;       // 0: a team is one thread-block cluster; > 0: CTAs per grid team
-  int32_t norm;            // 1: log_probs hold raw logits; one extra warp per CTA normalises them
+  int32_t norm;            // 1: log_probs hold raw logits (shifts from the lse pre-pass in J.lse)
   uint64_t wait_limit_ns;  // limit of every spin wait
 };
 
@@ -112,7 +112,7 @@ struct LaunchShape {
                            // resident warps, for batches that oversubscribe the GPU
   int grid = 0;            // 1: the team is ncta CTAs of one cooperative launch, one per SM,
                            // linked through global memory (transcripts beyond a cluster)
-  int norm = 0;            // 1: inputs are raw logits: CTAs get a normaliser warp (warps <= 15)
+  int norm = 0;            // 1: inputs are raw logits: an lse pre-pass runs before the launch
   int sum = 0;             // 1: sum-product forward score only (log-add in place of max)
 };
 
