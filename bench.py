@@ -77,6 +77,16 @@ def parse():
     return ap.parse_args()
 
 
+def input_digest(t, limit_bytes: int = 512 << 20) -> str:
+    """SHA-256 of a tensor's bytes (the seeded synthetic inputs of a run), or a
+    note when the tensor is too large to copy to the host for it."""
+    import hashlib
+    nbytes = t.numel() * t.element_size()
+    if nbytes > limit_bytes:
+        return f"not computed ({nbytes} bytes)"
+    return hashlib.sha256(t.detach().cpu().contiguous().numpy().tobytes()).hexdigest()
+
+
 def cores() -> int:
     try:
         return len(os.sched_getaffinity(0))
@@ -660,7 +670,8 @@ def main():
                    "tuning": ({"latency": autotune.load(mode="latency"), "throughput": autotune.load(mode="throughput"),
                               "throughput_batches_per_step": tp_batches}
                              if tuned else "built-in default (K=4, 4 warps per CTA)"),
-                   "host_enqueue_ms": round(hold["enqueue_s"] * 1e3, 3)},
+                   "host_enqueue_ms": round(hold["enqueue_s"] * 1e3, 3),
+                   "input_sha256": input_digest(batch.lp)},
         "p50_ms": float(np.percentile(times, 50)), "p99_ms": float(np.percentile(times, 99)),
         "plain": plain,
         "e2e": e2e,
