@@ -1,30 +1,35 @@
 #!/usr/bin/env python3
 """Benchmark: CTC forced alignment (Viterbi over the CTC trellis) on GB300.
 
-Default workload (batch64): 64 utterances, T uniform in 500..3000 frames
+Headline workload (batch64): 64 utterances, T uniform in 500..3000 frames
 (20 ms), C=32 classes, L=round(T/4) targets, FP32 synthetic log-probabilities
 (seeded; 3*N(0,1) logits with +4 on a planted feasible path, log_softmax).
 One step = the whole hot path (validate, expand, forward max-plus recursion,
 2-bit backpointers and anchor rows, final state, backtrack, scores) for the
-whole batch. Other workloads (--workload): plain1 (one utterance, T=200),
-longform (T=180000, L=45000), ragged32 / ragged500 (4096 utterances, lognormal
-lengths, C=32 / C=500).
+whole batch. Legs measured the same way, each with its own roofline, in
+"legs": longform (one utterance, T=180000, L=45000), ragged32 / ragged500
+(4096 utterances, lognormal lengths, C=32 / C=500). --workload picks the
+headline workload instead (plain1, batch64, longform, ragged32, ragged500).
 
 Metric: trellis cells per second, cells = sum over utterances of T * (2L+1).
-  value  : batched launch through the C ABI, inputs resident in device memory,
-           device time between CUDA events on the submitting stream (L2 flushed
-           before every timed step by writing a 256 MiB buffer).
+  value  : batched launch through the C ABI (one packed align_submit_batch),
+           inputs resident in device memory, device time between CUDA events
+           on the submitting stream (L2 flushed before every timed step by
+           writing a 256 MiB buffer).
   e2e    : same metric through the host-buffer path of align_submit_batch
            (pinned host emissions, host->device and device->host copies inside
            the timed region), host wall clock from the submit to the last poll.
   plain  : one synchronous submit+poll per utterance (reported beside).
-  serving: (batch64 only) workload 5 through the continuous-batching loop.
+  serving: (batch64 only) workload 5 through the continuous-batching loop:
+           2,000 requests per offered load after 200 warm-up requests.
 With --gpus N > 1 (torchrun), every rank aligns its own copy of the batch (no
 data-path collective; weak scaling); value is the sum of cells over ranks
 divided by the slowest rank's time.
 
 --impl reference times the CPU oracle (plain C, FP32) on this host's cores on
-the same workload and metric (a bounded sample per step for large workloads).
+the same workload, the same input bytes (generated on the GPU when there is
+one, as the GPU arm does, then copied to the host) and the same metric (a
+bounded sample per step for large workloads).
 --profile runs only warm-up + steps batches (no extras) for profilers.
 """
 from __future__ import annotations
@@ -70,7 +75,10 @@ def parse():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
-    ap.add_argument("--serving-requests", type=int, default=400)
+    ap.add_argument("--serving-requests", type=int, default=2000, help="timed requests per offered load")
+    ap.add_argument("--serving-warmup", type=int, default=200, help="warm-up requests before them")
+    ap.add_argument("--no-legs", action="store_true", help="skip the long-form and ragged legs")
+    ap.add_argument("--leg-steps", type=int, default=10, help="timed steps of each leg")
     ap.add_argument("--profile", action="store_true", help="only warm-up + steps batches, for profilers")
     ap.add_argument("--profile-beam", type=int, default=0, metavar="N",
                     help="only warm-up + steps decoder calls on a batch of N utterances, for profilers")
@@ -204,36 +212,56 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def serving_run(align, serve, synth, autotune, dev: int, n: int) -> dict:
+def serving_run(align, serve, synth, autotune, dev: int, n: int, warmup: int) -> dict:
     """Workload 5: Poisson arrivals served by the continuous-batching loop with a
     16 GiB backpointer budget. Saturation = every request arriving at time 0;
-    then offered loads of 0.5, 0.8 and 0.95 times the saturation request rate."""
-    b = synth.make_batch(synth.specs(5, n=n), device=f"cuda:{dev}")
+    then offered loads of 0.5, 0.8 and 0.95 times the saturation request rate.
+    Each run serves `warmup` + `n` requests of the stream; the first `warmup`
+    (by arrival) are excluded from its statistics."""
+    b = synth.make_batch(synth.specs(5, n=n + warmup), device=f"cuda:{dev}")
     al = align.Aligner(device=dev, batched=True, bp_budget_bytes=16 << 30)
     autotune.apply(al)
     try:
         warm = serve.poisson_requests(b, rate_per_s=1e9, seed=1)
-        serve.serve(al, warm)
+        serve.serve(al, warm, warmup=warmup)
         sat_reqs = [serve.Request(0.0, r.log_probs, r.targets) for r in warm]
-        sat = serve.serve(al, sat_reqs)
+        sat = serve.serve(al, sat_reqs, warmup=warmup)
         rate_sat = sat.n / sat.makespan_s
-        out = {"requests": n, "saturation": {**sat.as_dict(), "requests_per_s": rate_sat}, "loads": {}}
+        out = {"requests": n, "warmup_requests": warmup,
+               "saturation": {**sat.as_dict(), "requests_per_s": rate_sat}, "loads": {}}
         for frac in (0.5, 0.8, 0.95):
             reqs = serve.poisson_requests(b, rate_per_s=frac * rate_sat, seed=int(frac * 100))
-            st = serve.serve(al, reqs)
+            st = serve.serve(al, reqs, warmup=warmup)
             out["loads"][str(frac)] = {**st.as_dict(), "offered_requests_per_s": frac * rate_sat}
         return out
     finally:
         al.close()
 
 
+def make_workload_batch(wl, device: str):
+    from paper_2310_17864_gb300 import synth
+    return synth.make_batch(synth.specs(wl["cfg"], C=wl["C"]), device=device)
+
+
+def packed_targets(batch):
+    tg = np.concatenate([np.asarray(t, np.int32) for t in batch.targets] + [np.zeros(0, np.int32)])
+    tg_off = np.concatenate([[0], np.cumsum([len(t) for t in batch.targets])]).astype(np.int64)
+    return tg, tg_off
+
+
 def reference_arm(args, wl):
-    """The oracle, as it stands, on the host cores: same workload and metric."""
+    """The oracle, as it stands, on the host cores: same workload, same input
+    bytes as the GPU arm (generated with the same device generator when a GPU
+    is present, then copied to the host), same metric."""
     import concurrent.futures as cf
 
     import oracle
-    from paper_2310_17864_gb300 import synth
-    batch = synth.make_batch(synth.specs(wl["cfg"], C=wl["C"]), device="cpu")
+    import torch
+    gen_dev = "cuda:0" if torch.cuda.is_available() else "cpu"
+    batch = make_workload_batch(wl, gen_dev)
+    digest = input_digest(batch.lp)
+    if gen_dev != "cpu":
+        batch.lp = batch.lp.cpu()
     oracle.lib()
     items, cells = oracle_items(batch, 2.5e8)
     n = cores()
@@ -252,10 +280,201 @@ def reference_arm(args, wl):
         "impl": "reference", "metric": METRIC, "value": value, "unit": "cells/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": wl["name"], "utterances": len(batch), "cells_per_step": cells},
+        "config": {"workload": wl["name"], "utterances": len(batch), "cells_per_step": cells,
+                   "input_sha256": digest, "inputs_generated_on": gen_dev},
         "cpu_baseline": {"value": value, "unit": "cells/s", "cores": n, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "cells/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
+
+
+class DeviceTimer:
+    """Device time of one submitted batch between CUDA events on the
+    submitting stream. The stream is held by a device-side sleep while the
+    host enqueues, so the events time device work only; the hold is calibrated
+    to twice the slowest enqueue seen (at least 20 ms). L2 is flushed (256 MiB
+    write, above the 129 MB L2) before every step."""
+
+    def __init__(self, torch, stream, flush_buf):
+        self.torch, self.stream, self.flush_buf = torch, stream, flush_buf
+        self.cycles = 40_000_000
+        self.enqueue_max = 0.0
+        self.enqueue = []
+
+    def step(self, al, enqueue, finish) -> float:
+        torch = self.torch
+        self.flush_buf.fill_(1)
+        with torch.cuda.stream(self.stream):
+            torch.cuda._sleep(self.cycles)
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            ev0.record(self.stream)
+            h0 = time.perf_counter()
+            handle = enqueue()
+            al.join(self.stream)
+            ev1.record(self.stream)
+            h1 = time.perf_counter()
+        finish(handle)
+        ev1.synchronize()
+        self.enqueue.append(h1 - h0)
+        self.enqueue_max = max(self.enqueue_max, h1 - h0)
+        self.cycles = max(40_000_000, int(2 * self.enqueue_max * 2.0e9))
+        return ev0.elapsed_time(ev1)
+
+
+def roofline_of(batch, ms: float, t_frame_ns: float, peaks: dict, sm_count: int) -> dict:
+    """Three lower bounds on one step: HBM bytes at the measured copy
+    bandwidth, the per-frame dependency chain of the longest utterance (T_max
+    frames at the measured null-work frame time), and ALU issue (6 operations
+    per cell at the SM count and clock). The largest binds; frac = bound / time."""
+    n = len(batch)
+    T_of = [int(batch.offsets[i + 1] - batch.offsets[i]) for i in range(n)]
+    cells = batch.cells
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    peak_src = "MEASURED_PEAKS.json" if peaks else "fallback 6800 GB/s"
+    # Algorithmic bytes: emissions read once, 2 bits of backpointer per cell
+    # written and read back once, outputs (path, scores, total) written.
+    em_bytes = int(batch.lp.numel()) * 4
+    out_bytes = sum(T * 8 + 4 for T in T_of)
+    alg_bytes = em_bytes + 2 * cells * 2 / 8 + out_bytes
+    hbm_s = alg_bytes / (hbm_peak * 1e9)
+    T_max = max(T_of)
+    chain_s = T_max * t_frame_ns * 1e-9
+    sm_hz = 2.07e9
+    ops_per_cell = 6  # compare + select per candidate (2 or 3) and one add, averaged over blank/label states
+    alu_s = cells * ops_per_cell / (sm_count * 128 * sm_hz)
+    terms = {"hbm": hbm_s, "latency": chain_s, "alu": alu_s}
+    bound = max(terms, key=terms.get)
+    if bound == "latency":
+        rl = {"bound": "latency", "achieved": T_max / (ms / 1e3), "peak": 1e9 / t_frame_ns, "unit": "frames/s"}
+    elif bound == "hbm":
+        rl = {"bound": "hbm", "achieved": alg_bytes / (ms / 1e3) / 1e9, "peak": hbm_peak, "unit": "GB/s"}
+    else:
+        rl = {"bound": "alu", "achieved": cells * ops_per_cell / (ms / 1e3) / 1e12,
+              "peak": sm_count * 128 * sm_hz / 1e12, "unit": "Top/s"}
+    rl.update({"frac": terms[bound] / (ms / 1e3), "traffic": None,
+               "terms_us": {k: v * 1e6 for k, v in terms.items()}, "t_frame_ns": t_frame_ns,
+               "alg_bytes_per_step": alg_bytes, "hbm_gbs": alg_bytes / (ms / 1e3) / 1e9,
+               "hbm_peak_gbs": hbm_peak,
+               "peak_source": f"{peak_src} (HBM, of measured); null-work frame probe measured in this run (latency)"})
+    return rl
+
+
+def run_batched(torch, align, autotune, replicas, batch, dev, stream, flush_buf, steps, warmup, dist, clocks=None):
+    """Device-timed packed-batch steps of one workload. Returns the step
+    times, kernel launches per step, enqueue times and the aligner's budget."""
+    n = len(batch)
+    C = int(batch.lp.shape[1])
+    tg, tg_off = packed_targets(batch)
+    TT = int(batch.offsets[-1])
+    out = (torch.empty(TT, dtype=torch.int32, device=dev), torch.empty(TT, dtype=torch.float32, device=dev),
+           torch.empty(n, dtype=torch.float32, device=dev), None)
+    need = sum(align.align_plan(int(batch.offsets[i + 1] - batch.offsets[i]), C, len(batch.targets[i]),
+                                budget=1 << 40)["backpointer_bytes"] for i in range(n))
+    budget = max(4 << 30, int(1.2 * need) + (256 << 20))
+    al = align.Aligner(device=dev, batched=True, stream=stream, bp_budget_bytes=budget,
+                       max_inflight=max(8192, 2 * n))
+    tuned = autotune.apply(al)
+    timer = DeviceTimer(torch, stream, flush_buf)
+
+    def enqueue():
+        pr = al.submit_packed(batch.lp, batch.offsets, tg, tg_off, out)
+        al.flush()
+        return pr
+
+    def finish(pr):
+        al.wait_packed(pr)
+        assert (pr.status == 0).all(), pr.status[pr.status != 0][:4]
+
+    try:
+        for _ in range(warmup):
+            timer.step(al, enqueue, finish)
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        timer.enqueue = []
+        st0 = al.stats()
+        times = []
+        if clocks is not None:
+            with clocks:
+                for _ in range(steps):
+                    times.append(timer.step(al, enqueue, finish))
+        else:
+            for _ in range(steps):
+                times.append(timer.step(al, enqueue, finish))
+        st1 = al.stats()
+        torch.cuda.synchronize()
+    finally:
+        al.close()
+    launches = (st1["kernel_launches"] - st0["kernel_launches"]) // max(steps, 1)
+    tp = (st1["throughput_batches"] - st0["throughput_batches"]) / max(steps, 1)
+    ms = replicas.slowest(statistics.mean(times), dist, dev)
+    return {"times": times, "ms": ms, "launches": int(launches), "tp_batches": tp, "tuned": tuned,
+            "enqueue_ms_median": 1e3 * statistics.median(timer.enqueue), "budget": budget, "out": out}
+
+
+def run_e2e(torch, align, autotune, replicas, batch, dev, budget, steps, dist, world):
+    """End to end through the host-buffer path of align_submit_batch: the
+    batch as a user holds it (one packed pinned host tensor of emissions,
+    packed targets and outputs); copies in and results out inside the timed
+    region. Two steps in flight (step k+1 submitted before step k's results are
+    waited for, host outputs double-buffered), and one step at a time."""
+    n = len(batch)
+    host_lp = batch.lp.cpu().pin_memory()
+    tg_packed, tg_off = packed_targets(batch)
+    total_T = int(batch.offsets[-1])
+    mk = lambda: (torch.empty(total_T, dtype=torch.int32).pin_memory(),
+                  torch.empty(total_T, dtype=torch.float32).pin_memory(),
+                  torch.empty(n, dtype=torch.float32).pin_memory(), None)
+    host_out, host_out2 = mk(), mk()
+    h2d = host_lp.numel() * 4 + tg_packed.size * 4
+    d2h = total_T * 8 + n * 4
+    ha = align.Aligner(device=dev, batched=True, bp_budget_bytes=2 * budget, max_inflight=max(8192, 4 * n),
+                       staging_bytes=min(int(2.6 * (h2d + d2h)) + (64 << 20), 32 << 30))
+    autotune.apply(ha)
+    enq = []
+
+    def e2e_step(out):
+        h0 = time.perf_counter()
+        pr = ha.submit_packed(host_lp, batch.offsets, tg_packed, tg_off, out, host=True)
+        ha.flush()
+        enq.append(time.perf_counter() - h0)
+        return pr
+
+    try:
+        e_times = []
+        for k in range(2 + max(3, steps // 4)):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            pr = e2e_step(host_out)
+            ha.wait_packed(pr)
+            assert (pr.status == 0).all(), pr.status[pr.status != 0][:4]
+            if k >= 2:
+                e_times.append(time.perf_counter() - t0)
+        sync_ms = 1e3 * statistics.mean(e_times)
+        n_pipe = max(8, steps)
+        torch.cuda.synchronize()
+        for _ in range(2):
+            ha.wait_packed(e2e_step(host_out))
+        enq.clear()
+        t0 = time.perf_counter()
+        prev = None
+        for k in range(n_pipe):
+            pr = e2e_step(host_out if k % 2 == 0 else host_out2)
+            if prev is not None:
+                ha.wait_packed(prev)
+                assert (prev.status == 0).all()
+            prev = pr
+        ha.wait_packed(prev)
+        assert (prev.status == 0).all()
+        e_ms = replicas.slowest(1e3 * (time.perf_counter() - t0) / n_pipe, dist, dev)
+        sync_ms = replicas.slowest(sync_ms, dist, dev)
+    finally:
+        ha.close()
+    cells = batch.cells
+    return {"value": replicas.job_rate(cells, world, e_ms), "unit": "cells/s", "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h, "ms_per_step": e_ms, "steps_in_flight": 2,
+            "host_submit_ms_median": 1e3 * statistics.median(enq),
+            "one_step_at_a_time": {"ms_per_step": sync_ms, "value": replicas.job_rate(cells, world, sync_ms)}}
 
 
 def main():
@@ -294,7 +513,7 @@ def main():
                           "kept_frames": int(r.kept.sum().item()), "frames": int(off[-1])}))
         return
 
-    batch = synth.make_batch(synth.specs(wl["cfg"], C=wl["C"]), device=f"cuda:{dev}")
+    batch = make_workload_batch(wl, f"cuda:{dev}")
     n = len(batch)
     cells = batch.cells
     C = int(batch.lp.shape[1])
@@ -302,74 +521,53 @@ def main():
     L_of = [len(t) for t in batch.targets]
     T_max = max(T_of)
     utts = [batch.utt(i) for i in range(n)]
-    outs = [(torch.empty(T, dtype=torch.int32, device=dev), torch.empty(T, dtype=torch.float32, device=dev),
-             torch.empty(1, dtype=torch.float32, device=dev), None) for T in T_of]
-    need = sum(align.align_plan(T_of[i], C, L_of[i], budget=1 << 40)["backpointer_bytes"] for i in range(n))
-    budget = max(4 << 30, int(1.2 * need) + (256 << 20))
     stream = torch.cuda.Stream(dev)
-    al = align.Aligner(device=dev, batched=True, stream=stream, bp_budget_bytes=budget,
-                       max_inflight=max(8192, 2 * n))
-    tuned = autotune.apply(al)  # per-range kernel shapes measured on GB300 (tuning_gb300.json)
     flush_buf = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
-    items = [(utts[i], batch.targets[i], 0, outs[i]) for i in range(n)]
-
-    # The stream is held by a device-side sleep while the host enqueues the
-    # batch, so the events time device work only. The hold must outlast the
-    # host enqueue (submit + flush of every utterance): it is calibrated on the
-    # warm-up steps to twice the slowest enqueue seen, at least 20 ms.
-    hold = {"cycles": 40_000_000, "enqueue_s": 0.0}
-
-    def step_batched():
-        flush_buf.fill_(1)
-        with torch.cuda.stream(stream):
-            torch.cuda._sleep(hold["cycles"])
-            ev0 = torch.cuda.Event(enable_timing=True)
-            ev1 = torch.cuda.Event(enable_timing=True)
-            ev0.record(stream)
-            h0 = time.perf_counter()
-            rs = al.submit_batch(items)
-            al.flush()
-            al.join(stream)
-            ev1.record(stream)
-            h1 = time.perf_counter()
-        for r in rs:
-            al.poll(r)
-            assert r.status == 0, r.status
-        ev1.synchronize()
-        hold["enqueue_s"] = max(hold["enqueue_s"], h1 - h0)
-        hold["cycles"] = max(40_000_000, int(2 * hold["enqueue_s"] * 2.0e9))
-        return ev0.elapsed_time(ev1)
 
     if args.profile:
+        tg, tg_off = packed_targets(batch)
+        TT = int(batch.offsets[-1])
+        out = (torch.empty(TT, dtype=torch.int32, device=dev), torch.empty(TT, dtype=torch.float32, device=dev),
+               torch.empty(n, dtype=torch.float32, device=dev), None)
+        need = sum(align.align_plan(T_of[i], C, L_of[i], budget=1 << 40)["backpointer_bytes"] for i in range(n))
+        al = align.Aligner(device=dev, batched=True, stream=stream, bp_budget_bytes=max(4 << 30, int(1.2 * need)),
+                           max_inflight=max(8192, 2 * n))
+        autotune.apply(al)
         for _ in range(args.warmup + args.steps):
-            rs = al.submit_batch(items)
+            pr = al.submit_packed(batch.lp, batch.offsets, tg, tg_off, out)
             al.flush()
-            for r in rs:
-                al.poll(r)
+            al.wait_packed(pr)
         torch.cuda.synchronize()
         launches = al.stats()["kernel_launches"]
         al.close()
         print(json.dumps({"profile": wl["name"], "batches": args.warmup + args.steps, "kernel_launches": launches}))
         return
 
-    for _ in range(args.warmup):
-        step_batched()
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    l0 = al.stats()["kernel_launches"]
-    tp0 = al.stats()["throughput_batches"]
-    times = []
-    with Clocks(dev) as clk:
-        for _ in range(args.steps):
-            times.append(step_batched())
-    launches = (al.stats()["kernel_launches"] - l0) // max(args.steps, 1)
-    tp_batches = (al.stats()["throughput_batches"] - tp0) / max(args.steps, 1)
-    torch.cuda.synchronize()
-    ms = replicas.slowest(statistics.mean(times), dist, dev)  # the slowest rank's step
-    if dist:
-        dist.barrier()
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except Exception:
+        pass
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    t_frame_ns = align.align_probe_frame_latency(dev, 1, 1, 200000)
+
+    clk = Clocks(dev)
+    head = run_batched(torch, align, autotune, replicas, batch, dev, stream, flush_buf, args.steps, args.warmup,
+                       dist, clocks=clk)
+    times, ms, launches = head["times"], head["ms"], head["launches"]
     value = replicas.job_rate(cells, world, ms)
+    budget = head["budget"]
+    outs = []
+    for i in range(n):
+        f0, f1 = int(batch.offsets[i]), int(batch.offsets[i + 1])
+        outs.append((torch.empty(f1 - f0, dtype=torch.int32, device=dev),
+                     torch.empty(f1 - f0, dtype=torch.float32, device=dev),
+                     torch.empty(1, dtype=torch.float32, device=dev), None))
+    al = align.Aligner(device=dev, batched=True, stream=stream, bp_budget_bytes=budget, max_inflight=max(8192, 2 * n))
+    autotune.apply(al)
+    timer = DeviceTimer(torch, stream, flush_buf)
+    timer.cycles = max(timer.cycles, int(2 * head["enqueue_ms_median"] * 1e-3 * 2.0e9))
 
     # Token spans (per transcript token: start, end, mean score) of this batch's
     # alignments: one packed call, timed with events on its stream.
@@ -421,7 +619,7 @@ def main():
             for k in range(3 + args.steps):
                 flush_buf.fill_(1)
                 with torch.cuda.stream(stream):
-                    torch.cuda._sleep(hold["cycles"])
+                    torch.cuda._sleep(timer.cycles)
                     e0 = torch.cuda.Event(enable_timing=True)
                     e1 = torch.cuda.Event(enable_timing=True)
                     e0.record(stream)
@@ -466,7 +664,7 @@ def main():
         for k in range(3 + args.steps):
             flush_buf.fill_(1)
             with torch.cuda.stream(stream):
-                torch.cuda._sleep(hold["cycles"])
+                torch.cuda._sleep(timer.cycles)
                 e0 = torch.cuda.Event(enable_timing=True)
                 e1 = torch.cuda.Event(enable_timing=True)
                 e0.record(stream)
@@ -546,72 +744,49 @@ def main():
                  "p50_ms": float(np.percentile(lat_ms, 50)), "p99_ms": float(np.percentile(lat_ms, 99)),
                  "launch": "one synchronous launch per utterance"}
 
-    # End to end through the host-buffer path of align_submit_batch.
+
     e2e = None
     if not args.no_e2e:
-        # The batch as a user holds it: one packed pinned host tensor of emissions
-        # (utterance i = rows offsets[i]:offsets[i+1]), packed targets, packed outputs.
-        host_lp = batch.lp.cpu().pin_memory()
-        tg_packed = np.concatenate([np.asarray(t, dtype=np.int32) for t in batch.targets])
-        tg_off = np.concatenate([[0], np.cumsum([len(t) for t in batch.targets])]).astype(np.int64)
-        total_T = int(batch.offsets[-1])
-        host_out = (torch.empty(total_T, dtype=torch.int32).pin_memory(),
-                    torch.empty(total_T, dtype=torch.float32).pin_memory(),
-                    torch.empty(n, dtype=torch.float32).pin_memory(), None)
-        h2d = host_lp.numel() * 4 + tg_packed.size * 4
-        d2h = total_T * 8 + n * 4
-        host_out2 = tuple(None if x is None else torch.empty_like(x).pin_memory() for x in host_out)
-        ha = align.Aligner(device=dev, batched=True, bp_budget_bytes=2 * budget, max_inflight=max(8192, 4 * n),
-                           staging_bytes=min(int(2.6 * (h2d + d2h)) + (64 << 20), 16 << 30))
-        autotune.apply(ha)
-
-        def e2e_step(out):
-            pr = ha.submit_packed(host_lp, batch.offsets, tg_packed, tg_off, out, host=True)
-            ha.flush()
-            return pr
-
-        # One step at a time: submit, launch, wait for the step's results.
-        e_times = []
-        for k in range(2 + max(3, args.steps // 4)):
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            pr = e2e_step(host_out)
-            ha.wait_packed(pr)
-            assert (pr.status == 0).all(), pr.status[pr.status != 0][:4]
-            if k >= 2:
-                e_times.append(time.perf_counter() - t0)
-        sync_ms = 1e3 * statistics.mean(e_times)
-        # Two steps in flight (how a serving loop runs): step k+1 is submitted
-        # before step k's results are waited for; every step still copies its
-        # inputs in and its results out (double-buffered host outputs).
-        n_pipe = max(8, args.steps)
-        torch.cuda.synchronize()
-        for _ in range(2):
-            ha.wait_packed(e2e_step(host_out))
-        t0 = time.perf_counter()
-        prev = None
-        for k in range(n_pipe):
-            pr = e2e_step(host_out if k % 2 == 0 else host_out2)
-            if prev is not None:
-                ha.wait_packed(prev)
-                assert (prev.status == 0).all()
-            prev = pr
-        ha.wait_packed(prev)
-        assert (prev.status == 0).all()
-        e_ms = replicas.slowest(1e3 * (time.perf_counter() - t0) / n_pipe, dist, dev)
-        sync_ms = replicas.slowest(sync_ms, dist, dev)
-        ha.close()
-        e2e = {"value": replicas.job_rate(cells, world, e_ms), "unit": "cells/s", "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": d2h, "ms_per_step": e_ms, "steps_in_flight": 2,
-               "one_step_at_a_time": {"ms_per_step": sync_ms, "value": replicas.job_rate(cells, world, sync_ms)}}
+        e2e = run_e2e(torch, align, autotune, replicas, batch, dev, budget, args.steps, dist, world)
 
     serving = None
     if not args.no_serving and args.workload == "batch64":
         from paper_2310_17864_gb300 import serve
-        serving = serving_run(align, serve, synth, autotune, dev, args.serving_requests)
+        serving = serving_run(align, serve, synth, autotune, dev, args.serving_requests, args.serving_warmup)
+    al.close()
+
+    # The other single-GPU workloads, each with its own roofline (legs).
+    legs = None
+    if not args.no_legs:
+        legs = {}
+        for name in ("longform", "ragged32", "ragged500"):
+            if name == args.workload:
+                continue
+            lw = WORKLOADS[name]
+            lb = make_workload_batch(lw, f"cuda:{dev}")
+            lclk = Clocks(dev)
+            r = run_batched(torch, align, autotune, replicas, lb, dev, stream, flush_buf, args.leg_steps,
+                            max(3, args.warmup // 2), dist, clocks=lclk)
+            leg = {"metric": METRIC, "value": replicas.job_rate(lb.cells, world, r["ms"]), "unit": "cells/s",
+                   "ms_per_step": r["ms"], "steps": args.leg_steps,
+                   "p50_ms": float(np.percentile(r["times"], 50)), "p99_ms": float(np.percentile(r["times"], 99)),
+                   "gpu_launches": r["launches"],
+                   "config": {"workload": lw["name"], "utterances": len(lb), "cells_per_step": lb.cells,
+                              "T_max": int(np.max(np.diff(lb.offsets))),
+                              "l2": "flushed (256 MiB write) before every timed step",
+                              "host_enqueue_ms_median": round(r["enqueue_ms_median"], 3),
+                              "throughput_batches_per_step": r["tp_batches"],
+                              "input_sha256": input_digest(lb.lp)},
+                   "roofline": roofline_of(lb, r["ms"], t_frame_ns, peaks, sm_count),
+                   "clocks": lclk.summary()}
+            if name == "ragged32" and not args.no_e2e:
+                leg["e2e"] = run_e2e(torch, align, autotune, replicas, lb, dev, r["budget"], args.leg_steps, dist,
+                                     world)
+            legs[name] = leg
+            del lb, r
+            torch.cuda.empty_cache()
 
     if not replicas.prints(rank):
-        al.close()
         if dist:
             dist.destroy_process_group()
         return
@@ -620,47 +795,7 @@ def main():
     if not args.no_cpu_baseline and world == 1:
         cpu = cpu_oracle_rate(batch, args.cpu_seconds)
 
-    # Roofline of the trellis kernel (one batch per step). Three lower bounds on
-    # the step time: HBM bytes at the measured copy bandwidth, the per-frame
-    # dependency chain of the longest utterance (T_max frames at the measured
-    # null-work frame time), and ALU issue (ops per cell at the SM count and
-    # clock). The largest one binds; frac = bound time / measured time.
-    peaks = {}
-    try:
-        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            peaks = json.load(f)
-    except Exception:
-        pass
-    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
-    peak_src = "MEASURED_PEAKS.json" if peaks else "fallback 6800 GB/s"
-    # Algorithmic bytes: emissions read once, 2 bits of backpointer per cell written and
-    # read back once, outputs (path, scores) written.
-    em_bytes = int(batch.lp.numel()) * 4
-    out_bytes = sum(T * 8 + 4 for T in T_of)
-    alg_bytes = em_bytes + 2 * cells * 2 / 8 + out_bytes
-    hbm_s = alg_bytes / (hbm_peak * 1e9)
-    t_frame_ns = align.align_probe_frame_latency(dev, 1, 1, 200000)
-    chain_s = T_max * t_frame_ns * 1e-9
-    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
-    sm_hz = 2.07e9
-    ops_per_cell = 6  # compare + select per candidate (2 or 3) and one add, averaged over blank/label states
-    alu_s = cells * ops_per_cell / (sm_count * 128 * sm_hz)
-    terms = {"hbm": hbm_s, "latency": chain_s, "alu": alu_s}
-    bound = max(terms, key=terms.get)
-    bound_s = terms[bound]
-    if bound == "latency":
-        rl = {"bound": "latency", "achieved": T_max / (ms / 1e3), "peak": 1e9 / t_frame_ns, "unit": "frames/s"}
-    elif bound == "hbm":
-        rl = {"bound": "hbm", "achieved": alg_bytes / (ms / 1e3) / 1e9, "peak": hbm_peak, "unit": "GB/s"}
-    else:
-        rl = {"bound": "alu", "achieved": cells * ops_per_cell / (ms / 1e3) / 1e12,
-              "peak": sm_count * 128 * sm_hz / 1e12, "unit": "Top/s"}
-    rl.update({"frac": bound_s / (ms / 1e3), "traffic": None,
-               "terms_us": {k: v * 1e6 for k, v in terms.items()}, "t_frame_ns": t_frame_ns,
-               "alg_bytes_per_launch": alg_bytes, "hbm_gbs": alg_bytes / (ms / 1e3) / 1e9,
-               "hbm_peak_gbs": hbm_peak,
-               "peak_source": f"{peak_src} (HBM); null-work frame probe measured in this run (latency)"})
-
+    rl = roofline_of(batch, ms, t_frame_ns, peaks, sm_count)
     line = {
         "metric": METRIC, "value": value, "unit": "cells/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -668,15 +803,16 @@ def main():
         "config": {"workload": wl["name"], "utterances": n, "cells_per_step": cells, "T_max": T_max,
                    "l2": "flushed (256 MiB write) before every timed step", "parallelism": f"replicas{world}",
                    "tuning": ({"latency": autotune.load(mode="latency"), "throughput": autotune.load(mode="throughput"),
-                              "throughput_batches_per_step": tp_batches}
-                             if tuned else "built-in default (K=4, 4 warps per CTA)"),
-                   "host_enqueue_ms": round(hold["enqueue_s"] * 1e3, 3),
+                              "throughput_batches_per_step": head["tp_batches"]}
+                             if head["tuned"] else "built-in default (K=4, 4 warps per CTA)"),
+                   "host_enqueue_ms_median": round(head["enqueue_ms_median"], 3),
                    "input_sha256": input_digest(batch.lp)},
         "p50_ms": float(np.percentile(times, 50)), "p99_ms": float(np.percentile(times, 99)),
         "plain": plain,
         "e2e": e2e,
         "gpu_launches": int(launches),
         "roofline": rl,
+        "legs": legs,
         "serving": serving,
         "token_spans": spans_line,
         "logits": logits_line,
@@ -686,7 +822,6 @@ def main():
         "clocks": clk.summary(),
     }
     print(json.dumps(line))
-    al.close()
     if dist:
         dist.destroy_process_group()
 

@@ -329,8 +329,13 @@ int align_token_spans(const int32_t *states, const float *scores, const int64_t 
    anchor rows) lives in one fixed 32 MiB device array built into the library,
    held on every device where the library is loaded until the process exits.
    Requests needing more scratch than that return ALIGN_E_TOO_LARGE (message
-   in align_noalloc_last_error). The first call on a device looks up the
-   array's address; make it before any stream capture on that device. Every
+   in align_noalloc_last_error, which every non-OK return fills).
+   log_probs and the outputs must be device (or managed) memory of the current
+   device: other pointers return ALIGN_E_INVAL. The first call on a device
+   looks up the array's address and, under CUDA's lazy module loading, is where
+   the library's device code and the array are loaded onto the device (which
+   allocates and may synchronise): make it outside the allocation-sensitive
+   path and before any stream capture on that device. Every
    call shares the array and keeps the previous call's contents: calls that
    overlap on the GPU race, so never issue two at once. The call synchronises
    `cuda_stream` before it returns and writes the request's result code

@@ -71,7 +71,7 @@ def _bind(lib: ctypes.CDLL) -> ctypes.CDLL:
     lib.oracle_viterbi_total_f32.restype = ctypes.c_int
     lib.oracle_viterbi_f64.argtypes = [p, i64, i64, p, i64, i32, p, p, p, p]
     lib.oracle_viterbi_f64.restype = ctypes.c_int
-    lib.oracle_ctc_forward_f64.argtypes = [p, i64, i64, p, i64, i32, p]
+    lib.oracle_ctc_forward_f64.argtypes = [p, i64, i64, p, i64, i32, p, p]
     lib.oracle_ctc_forward_f64.restype = ctypes.c_int
     return lib
 
@@ -148,11 +148,17 @@ def viterbi_f64(lp, targets, blank: int = 0) -> dict:
     return {"status": rc, "path": path, "states": states, "scores": scores, "total": total[0]}
 
 
-def ctc_forward_f64(lp, targets, blank: int = 0) -> dict:
+def ctc_forward_f64(lp, targets, blank: int = 0, *, live_abs_max: bool = False) -> dict:
     """Sum-product over the same trellis (log-add in place of max), binary64:
-    the log of the total probability of the transcript's CTC paths."""
+    the log of the total probability of the transcript's CTC paths. With
+    live_abs_max, also "amax": per frame the largest |beta_t(s)| over the
+    finite states that can still reach a final state (for error bounds)."""
     lp, tg = _prep(lp, targets)
     T, C = lp.shape
     total = np.zeros(1, np.float64)
-    rc = lib().oracle_ctc_forward_f64(_ptr(lp), T, C, _ptr(tg), tg.size, int(blank), _ptr(total))
-    return {"status": rc, "total": float(total[0])}
+    amax = np.zeros(T, np.float64) if live_abs_max else None
+    rc = lib().oracle_ctc_forward_f64(_ptr(lp), T, C, _ptr(tg), tg.size, int(blank), _ptr(total), _ptr(amax))
+    out = {"status": rc, "total": float(total[0])}
+    if live_abs_max:
+        out["amax"] = amax
+    return out

@@ -306,6 +306,21 @@ int oracle_viterbi_f64(const float *lp, int64_t T, int64_t C, const int32_t *tar
  * In binary64 with the maximum factored out of each log-sum (log sum exp(x) =
  * m + log sum exp(x - m)); a sum of only -inf terms is -inf.
  */
+/*
+ * Largest |beta_t(s)| over the finite states that can still reach a final
+ * state (S-1 or S-2) in the frames left: a path advances at most two states
+ * per frame, so s + 2 (T-1-t) >= S-2 (a superset of the states the total
+ * depends on). Feeds error bounds only; 0 when no such state is finite.
+ */
+static double live_abs_max(const double *beta, int64_t S, int64_t T, int64_t t) {
+    double m = 0.0;
+    int64_t s, lo = S - 2 - 2 * (T - 1 - t);
+    if (lo < 0) lo = 0;
+    for (s = lo; s < S; ++s)
+        if (isfinite(beta[s]) && fabs(beta[s]) > m) m = fabs(beta[s]);
+    return m;
+}
+
 static double log_add3(double x, double y, double z) {
     double m = x;
     if (y > m) m = y;
@@ -315,7 +330,7 @@ static double log_add3(double x, double y, double z) {
 }
 
 int oracle_ctc_forward_f64(const float *lp, int64_t T, int64_t C, const int32_t *targets, int64_t L,
-                           int32_t blank, double *total) {
+                           int32_t blank, double *total, double *amax) {
     int64_t R, S = 2 * L + 1, t, s;
     int rc = oracle_validate(targets, L, C, blank, T, &R);
     double *prev, *cur, *tmp;
@@ -330,6 +345,7 @@ int oracle_ctc_forward_f64(const float *lp, int64_t T, int64_t C, const int32_t 
     for (s = 0; s < S; ++s) prev[s] = -INFINITY;
     prev[0] = (double)lp[blank];
     if (S > 1) prev[1] = (double)lp[ext_of(targets, blank, 1)];
+    if (amax) amax[0] = live_abs_max(prev, S, T, 0);
     for (t = 1; t < T; ++t) {
         const float *row = lp + t * C;
         for (s = 0; s < S; ++s) {
@@ -338,6 +354,7 @@ int oracle_ctc_forward_f64(const float *lp, int64_t T, int64_t C, const int32_t 
             cur[s] = log_add3(prev[s], a1, a2) + (double)row[ext_of(targets, blank, s)];
         }
         tmp = prev, prev = cur, cur = tmp;
+        if (amax) amax[t] = live_abs_max(prev, S, T, t);
     }
     *total = log_add3(prev[S - 1], (S > 1) ? prev[S - 2] : -INFINITY, -INFINITY);
     free(prev);

@@ -14,8 +14,11 @@
 //   * the library holds kNoAllocScratchBytes (32 MiB) of device memory on
 //     every GPU where it is loaded, until the process exits;
 //   * the first call on a device looks up the array's device address (once,
-//     with that device current); make that first call before any stream
-//     capture on the device;
+//     with that device current). Under CUDA's lazy module loading that first
+//     call is also where the library's device code and this array are loaded
+//     onto the device, which allocates and may synchronise: make the first call
+//     outside the allocation-sensitive path, and before any stream capture on
+//     the device;
 //   * every call uses the same array, which keeps the previous call's
 //     contents: calls that overlap on the GPU (different streams, or several
 //     host threads) race and must not be issued; the call synchronises its
@@ -24,6 +27,7 @@
 //     ALIGN_E_TOO_LARGE and a message in align_last_error.
 #include <cuda_runtime.h>
 
+#include <cstdarg>
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
@@ -66,11 +70,35 @@ int scratch_address(int device, void** out) {
 
 inline uint64_t up256(uint64_t v) { return (v + 255) / 256 * 256; }
 
+// Per-request metadata block (same layout as the runtime's: status, chase
+// state, alpha of the two final states).
 struct Meta {
   int32_t status;
   int32_t state_io;
   float final2[2];
 };
+static_assert(sizeof(Meta) == 16, "metadata block layout");
+
+int fail(int code, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
+int fail(int code, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  std::vsnprintf(g_msg, sizeof(g_msg), fmt, ap);
+  va_end(ap);
+  return code;
+}
+
+// A device (or managed) buffer on `device`; a host pointer given to the kernel
+// would fault on the GPU instead of returning an error.
+bool on_device(const void* p, int device) {
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return false;
+  }
+  if (a.type == cudaMemoryTypeManaged) return true;
+  return a.type == cudaMemoryTypeDevice && a.device == device;
+}
 
 }  // namespace
 }  // namespace gb300_align
@@ -82,14 +110,20 @@ extern "C" const char* align_noalloc_last_error(void) { return g_msg; }
 extern "C" int align_forced_noalloc(const float* log_probs, int64_t T, int64_t C, const int32_t* targets, int64_t L,
                                     int32_t blank, align_out out, void* cuda_stream, int32_t* request_status) {
   g_msg[0] = '\0';
-  if (!log_probs || !out.path || !out.scores || !out.total || (L > 0 && !targets)) return ALIGN_E_INVAL;
+  if (!log_probs || !out.path || !out.scores || !out.total || (L > 0 && !targets))
+    return fail(ALIGN_E_INVAL, "align_forced_noalloc: a required pointer is NULL");
   int64_t R = 0;
   int rc = validate_request(targets, L, C, blank, T, &R);
-  if (rc != ALIGN_OK) return rc;
-  if (T >= (1ll << kTagBits)) return ALIGN_E_TOO_LARGE;
+  if (rc != ALIGN_OK)
+    return fail(rc, "align_forced_noalloc: request rejected by validation (%s)", align_status_string(rc));
+  if (T >= (1ll << kTagBits))
+    return fail(ALIGN_E_TOO_LARGE, "align_forced_noalloc: T = %lld frames exceeds 2^%d - 1", static_cast<long long>(T),
+                kTagBits);
   Plan p{};
   rc = make_plan(default_tune_table(), T, C, L, ~0ull, false, &p);
-  if (rc != ALIGN_OK) return rc;
+  if (rc != ALIGN_OK)
+    return fail(rc, "align_forced_noalloc: transcript of %lld targets needs more than one thread-block cluster",
+                static_cast<long long>(L));
 
   // Scratch layout: descriptor | metadata | targets | backpointers + anchor rows.
   const uint64_t off_job = 0;
@@ -97,14 +131,16 @@ extern "C" int align_forced_noalloc(const float* log_probs, int64_t T, int64_t C
   const uint64_t off_tgt = off_meta + 256;
   const uint64_t off_bp = off_tgt + up256(static_cast<uint64_t>(L > 0 ? L : 1) * 4);
   const uint64_t need = off_bp + p.bp_bytes;
-  if (need > kNoAllocScratchBytes) {
-    std::snprintf(g_msg, sizeof(g_msg),
-                  "align_forced_noalloc: request needs %llu bytes of scratch, the fixed area holds %llu",
-                  static_cast<unsigned long long>(need), static_cast<unsigned long long>(kNoAllocScratchBytes));
-    return ALIGN_E_TOO_LARGE;
-  }
+  if (need > kNoAllocScratchBytes)
+    return fail(ALIGN_E_TOO_LARGE, "align_forced_noalloc: request needs %llu bytes of scratch, the fixed area holds %llu",
+                static_cast<unsigned long long>(need), static_cast<unsigned long long>(kNoAllocScratchBytes));
   int device = 0;
-  if (cudaGetDevice(&device) != cudaSuccess) return ALIGN_E_CUDA;
+  cudaError_t ge = cudaGetDevice(&device);
+  if (ge != cudaSuccess) return fail(ALIGN_E_CUDA, "align_forced_noalloc: %s", cudaGetErrorString(ge));
+  if (!on_device(log_probs, device) || !on_device(out.path, device) || !on_device(out.scores, device) ||
+      !on_device(out.total, device) || (out.states && !on_device(out.states, device)))
+    return fail(ALIGN_E_INVAL, "align_forced_noalloc: log_probs and outputs must be device memory of device %d",
+                device);
   void* base_v = nullptr;
   rc = scratch_address(device, &base_v);
   if (rc != ALIGN_OK) return rc;
@@ -149,10 +185,7 @@ extern "C" int align_forced_noalloc(const float* log_probs, int64_t T, int64_t C
   int32_t st = kStPending;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&st, &dmeta->status, 4, cudaMemcpyDeviceToHost, stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
-  if (e != cudaSuccess) {
-    std::snprintf(g_msg, sizeof(g_msg), "align_forced_noalloc: %s", cudaGetErrorString(e));
-    return ALIGN_E_CUDA;
-  }
+  if (e != cudaSuccess) return fail(ALIGN_E_CUDA, "align_forced_noalloc: %s", cudaGetErrorString(e));
   if (request_status) *request_status = (st == kStPending) ? ALIGN_E_TIMEOUT : st;
   return ALIGN_OK;
 }

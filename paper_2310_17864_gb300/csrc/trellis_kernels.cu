@@ -135,7 +135,7 @@ __device__ __forceinline__ void cp_async_mbar_arrive(uint64_t* bar) {
 struct SmemHead {
   uint64_t full[kMaxStages];   // emission stage filled
   uint64_t empty[kMaxStages];  // emission stage released by every warp
-  uint64_t normd[kMaxStages];  // unused (keeps the 256-byte head layout)
+  uint64_t pad[kMaxStages];    // keeps the head at 256 bytes
   int32_t abort;            // set by any thread of this CTA whose wait hit the limit
   uint32_t unused;
   uint64_t sink;            // scratch slot written by the last warp of the team
@@ -396,7 +396,6 @@ __global__ void __launch_bounds__(512, (kOcc && K <= 4) ? 2 : 1)
   // warps subtract them from the staged raw logits as they use them.
   const int W = blockDim.x >> 5;
   const int warp = threadIdx.x >> 5;
-  constexpr bool is_norm = false;
   const int lane = threadIdx.x & 31;
   const FwdJob& J = jobs[blockIdx.x / ncta];
   const int g = static_cast<int>(crank) * W + warp;  // warp index in the team
@@ -537,7 +536,6 @@ __global__ void __launch_bounds__(512, (kOcc && K <= 4) ? 2 : 1)
   }
 #pragma unroll
   for (int j = 0; j < K; ++j) A[j] = s0 + j;
-  const bool ok = true;
 
   // Ring endpoints. Each warp receives alpha(first state - 1) of frame t-1
   // from its own ring (written by the previous warp of the team, in this CTA
@@ -643,10 +641,8 @@ __global__ void __launch_bounds__(512, (kOcc && K <= 4) ? 2 : 1)
       *reinterpret_cast<uint4*>(dst) = make_uint4(packed[0], packed[1], packed[2], packed[3]);
     }
   };
-  if (ok && !is_norm) {
-    if (ckpt != nullptr && (t_begin % ck_every) == 0) store_ckpt(t_begin);
-    send_one(t_begin, a[K - 1], A[K - 1]);  // slot of t_begin is fresh: no flow check needed
-  }
+  if (ckpt != nullptr && (t_begin % ck_every) == 0) store_ckpt(t_begin);
+  send_one(t_begin, a[K - 1], A[K - 1]);  // slot of t_begin is fresh: no flow check needed
 
   // ---- frames t_begin+1 .. t_end-1 ----
   // Frames run in anchor windows of kAnchorD (an anchor row after each),
@@ -868,12 +864,12 @@ __global__ void __launch_bounds__(512, (kOcc && K <= 4) ? 2 : 1)
   }
   // Last, partial window.
   const int nwin = (t_end - 1 - t_begin + kAnchorD - 1) / kAnchorD;  // anchor rows of this pass
-  if (ok && !is_norm && *abort == 0 && t_end - 1 > t_begin && ((t_end - 1 - t_begin) % kAnchorD) != 0)
+  if (*abort == 0 && t_end - 1 > t_begin && ((t_end - 1 - t_begin) % kAnchorD) != 0)
     store_anchor_row(nwin - 1);
 
   // ---- alpha_{T-1} of the two final states ----
   const bool aborted_here = (*abort != 0);
-  if (!aborted_here && !is_norm && t_end == J.T && J.final2 != nullptr) {
+  if (!aborted_here && t_end == J.T && J.final2 != nullptr) {
 #pragma unroll
     for (int j = 0; j < K; ++j) {
       if (s0 + j == S - 1) J.final2[1] = a[j];
@@ -960,7 +956,7 @@ __global__ void __launch_bounds__(512, (kOcc && K <= 4) ? 2 : 1)
   // cache lines.
   const int G = static_cast<int>(ncta) * W;
   const int nwalk = max(nwin, 1);
-  for (int m = g * 32 + lane; !is_norm && m < nwalk; m += G * 32) {
+  for (int m = g * 32 + lane; m < nwalk; m += G * 32) {
     const int b = t_begin + m * kAnchorD;
     const int e = (nwin == 0) ? t_begin : min(b + kAnchorD, t_end - 1);
     int sc = path[e];
@@ -987,7 +983,7 @@ __global__ void __launch_bounds__(512, (kOcc && K <= 4) ? 2 : 1)
     constexpr int kT3 = 8;
     const int tid = g * 32 + lane;
     const int nthr = G * 32;
-    for (int f0 = t_begin + tid; !is_norm && f0 < t_end; f0 += kT3 * nthr) {
+    for (int f0 = t_begin + tid; f0 < t_end; f0 += kT3 * nthr) {
       int st[kT3], tok[kT3];
       float sv[kT3];
 #pragma unroll

@@ -1,46 +1,36 @@
 """GPU parity of the sum-product variant (ALIGN_REQ_SUM): the CTC forward
 score over the same trellis, with log-add in place of the max.
 
-Tolerance. The kernel works in FP32 and in base 2 (log2 of probabilities):
-every cell is m + log2(1 + 2^(d1) + 2^(d2)) (m the largest predecessor, d <= 0
-the others' distance to it) followed by one add of the emission times
-log2(e); the total is
-multiplied by ln(2) at the end. The hardware 2^x and log2(x) (PTX ex2.approx
-and lg2.approx) are accurate to about 2^-22 (relative, resp. absolute on the
-sums in [1, 3]), so one log-add is off by at most 2^-20; the adds and the
-base changes by 2^-24 of |alpha| each. The log-sum-exp is a convex
-combination in its inputs (its partial derivatives are non-negative and sum
-to one), so errors carried from frame t-1 do not grow: after frame t the
-error is at most err_{t-1} + 2^-23 A_t + 2^-20, where A_t = sum over tau <= t
-of max_c |lp[tau, c]| bounds every finite |alpha_t(s)| (natural-log units: a
-base-2 value is 1/ln 2 times larger and its errors shrink by ln 2 when the
-total is converted back).
-The final log-add and the conversion back add one more term. The test uses
-that bound, summed over the frames, against the binary64 oracle.
+Tolerance (tests/ctc_forward_bounds.py derives it): the kernel works in FP32
+and in base 2 with the hardware 2^x and log2(x); per frame the two FP32 adds
+round by at most 2^-23 |beta_t| (natural-log units), the emission's base
+change by 1.5 * 2^-23 |e|, the log-add by 2^-20, and a log-sum-exp does not
+amplify errors carried from earlier frames (a convex combination). The test
+sums these over the frames with |beta_t| bounded by the binary64 oracle's
+largest |beta_t(s)| over the states that can still reach the end. Closed
+forms at large S (per-frame emissions equal across classes, so every path's
+score is known and the paths are counted exactly) pin the cluster and grid
+team paths with a bound small enough that dropping a final state or the last
+frame's emission fails.
 """
 import numpy as np
 import pytest
 import torch
 
+import ctc_forward_bounds as cfb
 import oracle
 from paper_2310_17864_gb300 import align, build, synth
 
 pytestmark = pytest.mark.gpu
 
 
-def tolerance(lp: np.ndarray) -> float:
-    m = np.abs(np.where(np.isfinite(lp), lp, 0.0)).max(axis=1).astype(np.float64)
-    A = np.cumsum(m)
-    return float(np.sum(2.0 ** -23 * A + 2.0 ** -20) + 2.0 ** -23 * A[-1] + 2.0 ** -20)
-
-
 def check(status, total, lp, targets, blank, label=""):
-    o = oracle.ctc_forward_f64(lp, np.asarray(targets, np.int32), blank)
+    o = oracle.ctc_forward_f64(lp, np.asarray(targets, np.int32), blank, live_abs_max=True)
     assert status == o["status"], (label, status, o["status"])
     if o["status"] != 0:
         assert total == -np.inf, (label, total)
         return o
-    tol = tolerance(lp)
+    tol = cfb.tolerance(lp, o["amax"], o["total"])
     assert abs(total - o["total"]) <= tol, (label, total, o["total"], tol)
     return o
 
@@ -176,3 +166,25 @@ def test_logits_flag_rejected(al):
     with pytest.raises(align.AlignError) as e:
         align.align_submit_batch(al.ctx, reqs)
     assert e.value.code == align.ALIGN_E_INVAL
+
+
+@pytest.mark.parametrize("L,spare,team", [(2980, 20, "cluster"), (10000, 20, "grid")])
+def test_closed_form_large_S(L, spare, team):
+    """Exact totals from path counts at S = 5,961 (a thread-block cluster) and
+    S = 20,001 (a grid team over the GPU's SMs), default plans."""
+    build.build()
+    lp, tg, exact, tol = cfb.closed_form_case(L, spare)
+    T = lp.shape[0]
+    plan = align.align_plan(T, 32, L, budget=4 << 30)
+    a = align.Aligner(device=0, bp_budget_bytes=4 << 30)
+    try:
+        st, tot = a.ctc_forward(torch.from_numpy(lp).cuda(), tg, 0)
+        grid = a.stats()["grid_teams"]
+    finally:
+        a.close()
+    assert st == 0
+    if team == "grid":
+        assert grid == 1
+    else:
+        assert grid == 0 and plan["cluster_ctas"] > 1
+    assert abs(tot - exact) <= tol, (tot, exact, tol)

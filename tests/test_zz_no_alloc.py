@@ -10,6 +10,7 @@ import numpy as np
 import pytest
 import torch
 
+import oracle
 from paper_2310_17864_gb300 import align, build, synth
 
 pytestmark = pytest.mark.gpu
@@ -46,8 +47,31 @@ def test_noalloc_matches_submit_two_calls_in_a_row():
             assert torch.equal(path, r.path) and torch.equal(states, r.states)
             assert scores.cpu().numpy().tobytes() == r.scores.cpu().numpy().tobytes()
             assert total.cpu().numpy().tobytes() == r.total.cpu().numpy().tobytes()
+            # And the CPU oracle's alignment, bit for bit.
+            o = oracle.viterbi_f32(u.lp.numpy(), u.targets, 0)
+            assert o["status"] == 0
+            assert np.array_equal(path.cpu().numpy(), o["path"]) and np.array_equal(states.cpu().numpy(), o["states"])
+            assert scores.cpu().numpy().tobytes() == o["scores"].tobytes()
+            assert total.cpu().numpy().tobytes() == np.float32(o["total"]).tobytes()
     finally:
         ref.close()
+
+
+def test_noalloc_rejects_host_buffers():
+    """Emissions or outputs in host memory are refused with ALIGN_E_INVAL and a
+    message before anything runs on the GPU."""
+    build.build()
+    u = synth.make_utterance(6, 100, 32, 20)
+    path, scores, total, states = _outs(u.T)
+    o = align.AlignOut(path.data_ptr(), scores.data_ptr(), total.data_ptr(), states.data_ptr())
+    lp_host = u.lp.contiguous()
+    rc, _ = align.align_forced_noalloc(lp_host.data_ptr(), u.T, u.C, u.targets, 0, o, None)
+    assert rc == align.ALIGN_E_INVAL
+    assert "device memory" in align.align_noalloc_last_error()
+    host_path = torch.empty(u.T, dtype=torch.int32)
+    o2 = align.AlignOut(host_path.data_ptr(), scores.data_ptr(), total.data_ptr(), states.data_ptr())
+    rc, _ = align.align_forced_noalloc(u.lp.cuda().data_ptr(), u.T, u.C, u.targets, 0, o2, None)
+    assert rc == align.ALIGN_E_INVAL
 
 
 def test_noalloc_rejects_requests_beyond_its_scratch():
