@@ -63,6 +63,10 @@ extern "C" {
                                          a device scan plus a synchronisation per request, or a host
                                          scan for host inputs. Off by default: without it such inputs
                                          give unspecified (but in-bounds) results. */
+#define ALIGN_F_GENERIC_KERNEL 0x20u  /* run every Viterbi request on the generic trellis kernel
+                                         (the one that also serves the sum-product, K >= 8 and
+                                         C > 512) instead of the fast kernel for K = 2 or 4; same
+                                         results, for comparison and testing */
 #define ALIGN_F_TEST_STALL 0x80000000u /* testing the device watchdog only: in every request whose
                                          trellis spans more than one warp, the first warp never
                                          hands its values on, so the next warp's bounded wait runs

@@ -38,6 +38,7 @@ ALIGN_F_FORCE_CHECKPOINT = 0x2
 ALIGN_F_NO_GRAPHS = 0x4
 ALIGN_F_NO_GRID_TEAMS = 0x8
 ALIGN_F_DEBUG_CHECKS = 0x10
+ALIGN_F_GENERIC_KERNEL = 0x20
 ALIGN_F_TEST_STALL = 0x80000000
 
 # Every entry point declared in include/align.h.
@@ -448,7 +449,8 @@ class Aligner:
     def __init__(self, device: int = 0, batched: bool = False, bp_budget_bytes: int = 0,
                  staging_bytes: int = 0, stream=None, force_checkpoint: bool = False,
                  wait_limit_ms: int = 0, max_inflight: int = 0, graphs: bool = True,
-                 test_stall: bool = False, grid_teams: bool = True, debug_checks: bool = False):
+                 test_stall: bool = False, grid_teams: bool = True, debug_checks: bool = False,
+                 generic_kernel: bool = False):
         import torch
         self.torch = torch
         self.device = device
@@ -457,6 +459,7 @@ class Aligner:
         flags |= 0 if grid_teams else ALIGN_F_NO_GRID_TEAMS
         flags |= ALIGN_F_TEST_STALL if test_stall else 0
         flags |= ALIGN_F_DEBUG_CHECKS if debug_checks else 0
+        flags |= ALIGN_F_GENERIC_KERNEL if generic_kernel else 0
         cfg = AlignConfig(device=device, max_inflight=max_inflight, bp_budget_bytes=bp_budget_bytes,
                           staging_bytes=staging_bytes,
                           cuda_stream=(stream.cuda_stream if stream is not None else None), flags=flags,

@@ -19,7 +19,7 @@ ROOT = os.path.dirname(HERE)
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libalign.so")
 BUILD_DIR = os.path.join(HERE, "_build")
-SOURCES = ["trellis_kernels.cu", "runtime.cu", "plan.cpp", "noalloc.cu", "copy_kernels.cu", "spans.cu", "beam.cu"]
+SOURCES = ["trellis_fast.cu", "trellis_kernels.cu", "runtime.cu", "plan.cpp", "noalloc.cu", "copy_kernels.cu", "spans.cu", "beam.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-ftz=false", "-prec-div=true",
          "-prec-sqrt=true", "-fmad=false", f"-I{INCLUDE}", f"-I{CSRC}"]

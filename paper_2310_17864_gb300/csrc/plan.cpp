@@ -87,9 +87,15 @@ int make_plan(const TuneTable& tune_in, int64_t T, int64_t C, int64_t L, uint64_
     }
   }
   if (!found) return ALIGN_E_TOO_LARGE;
+  // The fast Viterbi kernel serves K = 2 or 4 with at least 4 frames per
+  // emission stage (C <= 512); its stages are 8 KB. Other shapes (and the
+  // sum-product, and logits requests that run checkpointed) use the generic
+  // kernel.
+  const bool fast = (p.shape.K == 2 || p.shape.K == 4) && C <= 512;
+  p.shape.fast = fast ? 1 : 0;
   // Emission staging: stages of 4 KB (32 frames of a 32-class row), up to 8 KB
   // for wide rows; frames per stage a power of two dividing the anchor window.
-  const int64_t stage_budget = p.shape.warps >= 2 ? 8192 : 4096;
+  const int64_t stage_budget = (fast || p.shape.warps >= 2) ? 8192 : 4096;
   const int64_t fmax = std::clamp<int64_t>(stage_budget / (4 * C), 1, kAnchorD);
   p.frames_per_stage = 1;
   while (p.frames_per_stage * 2 <= fmax) p.frames_per_stage *= 2;
@@ -98,7 +104,9 @@ int make_plan(const TuneTable& tune_in, int64_t T, int64_t C, int64_t L, uint64_
   // Anchor rows: one row of S bytes (rounded to 16) per kAnchorD frames.
   p.zstride = static_cast<int>(round_up(static_cast<uint64_t>(S), 16));
   const auto zrows = [](int64_t frames) { return static_cast<uint64_t>((frames + kAnchorD - 1) / kAnchorD); };
-  p.z_off = round_up(row_bytes * static_cast<uint64_t>(std::max<int64_t>(T - 1, 0)), 256);
+  // Backpointer words: per frame (generic layout) or per whole window of
+  // kAnchorD frames (fast layout); sized for whole windows, which covers both.
+  p.z_off = round_up(row_bytes * zrows(T - 1) * kAnchorD, 256);
   p.bp_bytes = p.z_off + round_up(zrows(T - 1) * p.zstride, 256);
   // About sqrt(T) frames per checkpoint segment, rounded up to whole anchor
   // windows so that checkpoint frames end windows.
@@ -109,7 +117,7 @@ int make_plan(const TuneTable& tune_in, int64_t T, int64_t C, int64_t L, uint64_
   p.ckpt_bytes = round_up(static_cast<uint64_t>(p.nck) * p.ck_stride * 4ull, 256);
   p.seg_z_off = round_up(row_bytes * static_cast<uint64_t>(p.ck_every), 256);
   p.seg_bp_bytes = p.seg_z_off + round_up(zrows(p.ck_every) * p.zstride, 256);
-  p.x_bytes = p.shape.grid ? xlink_bytes(p.shape.ncta) : 0;
+  p.x_bytes = p.shape.grid ? std::max({xlink_bytes(p.shape.ncta), fast_xlink_bytes(p.shape.ncta, kAnchorD), fast_xlink_bytes(p.shape.ncta, 4)}) : 0;
   p.checkpointed = force_checkpoint || p.bp_bytes + p.x_bytes > budget;
   if (p.checkpointed && p.ckpt_bytes + p.seg_bp_bytes + p.x_bytes > budget) return ALIGN_E_TOO_LARGE;
   *out = p;

@@ -231,16 +231,21 @@ int plan_request(const align_ctx* ctx, const TuneTable& table, int64_t T, int64_
   const int rc = make_plan(t, T, C, L, sum ? ~0ull : ctx->bp_arena.cap(),
                            !sum && (ctx->flags & ALIGN_F_FORCE_CHECKPOINT) != 0, out);
   if (rc != ALIGN_OK) return rc;
+  if (ctx->flags & ALIGN_F_GENERIC_KERNEL) out->shape.fast = 0;
   if (sum) {  // the forward pass only: no backpointers, anchor rows or checkpoints
     out->shape.sum = 1;
+    out->shape.fast = 0;  // the sum-product runs on the generic kernel
     out->checkpointed = false;
     out->bp_bytes = 0;
     out->z_off = 0;
     if (plan_device_bytes(*out) > ctx->bp_arena.cap()) return ALIGN_E_TOO_LARGE;
   }
   if (logits) {
+    // Per-frame shifts of the lse pre-pass (generic kernel) or per-warp partial
+    // sums of the scores (fast kernel): T or team-warps floats.
     out->shape.norm = 1;
-    out->lse_bytes = (static_cast<uint64_t>(T) * 4 + 255) & ~255ull;
+    const uint64_t team_warps = static_cast<uint64_t>(out->shape.warps) * static_cast<uint64_t>(out->shape.ncta);
+    out->lse_bytes = (std::max(static_cast<uint64_t>(T), team_warps) * 4 + 255) & ~255ull;
     if (plan_device_bytes(*out) > ctx->bp_arena.cap()) return ALIGN_E_TOO_LARGE;
   }
   return ALIGN_OK;
@@ -402,6 +407,9 @@ int launch_queued(align_ctx* ctx) {
       r.stage.bytes = sb;
       r.stage.live = true;
     }
+    // Checkpointed logits requests take the generic kernel (its score pass
+    // reads the per-frame shifts of the lse pre-pass).
+    if (r.plan.checkpointed && r.plan.shape.norm) r.plan.shape.fast = 0;
     take.push_back(&r);
   }
   for (auto it = keep.rbegin(); it != keep.rend(); ++it) ctx->queued.push_front(*it);
@@ -663,6 +671,7 @@ int launch_queued(align_ctx* ctx) {
     gl.shape = LaunchShape{std::get<0>(kv.first), std::get<1>(kv.first), std::get<2>(kv.first), std::get<5>(kv.first)};
     gl.shape.norm = std::get<6>(kv.first);
     gl.shape.sum = std::get<7>(kv.first);
+    gl.shape.fast = take[static_cast<size_t>(kv.second[0])]->plan.shape.fast;  // implied by K, C and sum
     gl.F = std::get<3>(kv.first);
     gl.first = jn;
     gl.count = kv.second.size();

@@ -39,7 +39,7 @@
 
 namespace gb300_align {
 
-constexpr int kMaxStages = 10;        // emission ring stages per CTA, at most (planned per shape)
+constexpr int kMaxStages = 16;        // emission ring stages per CTA, at most (planned per shape)
 constexpr int kLead = 4;              // stages in flight ahead of the consumer
 constexpr int kBtWindow = 32;         // frames per backtrack window
 constexpr int kAnchorD = 32;          // frames between anchor rows (== kBtWindow)
@@ -93,6 +93,12 @@ struct FwdParams {
   int32_t stages;          // emission stages in the ring (kLead .. kMaxStages)
   int32_t grid_ctas;       // 0: a team is one thread-block cluster; > 0: CTAs per grid team
   int32_t norm;            // 1: log_probs hold raw logits (shifts from the lse pre-pass in J.lse)
+  // Fast kernel (LaunchShape::fast): neighbour hand-off in packages of kb frames.
+  int32_t kb;              // frames per package (4 or 8)
+  int32_t pkgs;            // package slots per shared-memory link (power of two)
+  int32_t gpkgs;           // package slots per global link of a grid team (power of two)
+  int32_t link_off;        // shared-memory offset of the per-warp links
+  int32_t link_stride;     // bytes per warp link: 16-byte head + pkgs * kb * 8
   uint64_t wait_limit_ns;  // limit of every spin wait
 };
 
@@ -114,6 +120,7 @@ struct LaunchShape {
                            // linked through global memory (transcripts beyond a cluster)
   int norm = 0;            // 1: inputs are raw logits: an lse pre-pass runs before the launch
   int sum = 0;             // 1: sum-product forward score only (log-add in place of max)
+  int fast = 0;            // 1: the fast Viterbi kernel (K = 2 or 4, at least 4 frames per stage)
 };
 
 // Bytes of the global links of a grid team of ncta CTAs: a ring of kMaxRing
@@ -122,6 +129,19 @@ constexpr int kMaxRing = 128;  // ring slots per boundary, at least P.rb
 inline uint64_t xlink_bytes(int ncta) {
   const uint64_t b = static_cast<uint64_t>(ncta > 1 ? ncta - 1 : 0) * kMaxRing * 8ull +
                      static_cast<uint64_t>((ncta + 3) & ~3) * 4ull + 16ull;
+  return (b + 255) & ~255ull;
+}
+
+// Fast kernel: package slots per link, and the bytes of a grid team's global
+// links (one per CTA boundary: 16-byte head + slots of kb alphas and kb
+// anchors) followed by the 2-word team barrier.
+constexpr int kFastPkgs = 8;       // packages of 4 frames per shared-memory link
+constexpr int kFastGridPkgs = 16;  // packages of 4 frames per global link
+constexpr int kFastWinPkgs = 4;    // 32-frame windows per link (window mode)
+inline uint64_t fast_xlink_bytes(int ncta, int kb) {
+  const uint64_t slots = (kb == 32) ? kFastWinPkgs : kFastGridPkgs;
+  const uint64_t gstride = 16ull + slots * kb * 8ull;
+  const uint64_t b = static_cast<uint64_t>(ncta > 1 ? ncta - 1 : 0) * gstride + 16ull;
   return (b + 255) & ~255ull;
 }
 
@@ -139,6 +159,9 @@ int smem_bytes(const LaunchShape& shape, const FwdParams& p);
 // (or CTA) per job, on the given stream. Returns a cudaError_t value.
 int launch_trellis(const LaunchShape& shape, const FwdParams& p, const FwdJob* d_jobs, int njobs,
                    void* stream);
+
+// The fast Viterbi kernel (trellis_fast.cu) for shapes with fast = 1.
+int launch_trellis_fast(const LaunchShape& shape, const FwdParams& p, const FwdJob* d_jobs, int njobs, void* stream);
 
 // Null-work frame-latency probe (warp-scope chain of one frame); d_out[0] =
 // ns for `frames` frames measured by CTA 0, d_out[1] = 0.

@@ -74,8 +74,9 @@ def test_plan_shapes_and_footprints():
     # Config-1 sized: S = 81 fits one warp of K=4 lanes.
     p = align.align_plan(200, 32, 40)
     assert (p["states_per_lane"], p["warps_per_cta"], p["cluster_ctas"]) == (4, 1, 1)
-    # 199 rows of 6 words, padded to 256 B, plus 7 anchor rows of 96 B (S=81 -> 96) padded to 256 B.
-    assert p["backpointer_bytes"] == 4864 + 768
+    # 199 frames = 7 windows of 32 frames x 6 words (5376 B), plus 7 anchor rows of 96 B
+    # (S=81 -> 96) padded to 256 B.
+    assert p["backpointer_bytes"] == 5376 + 768
     assert p["checkpointed"] == 0
     # S = 1501: 12 warps of 128 states; by default 4 warps per CTA, a cluster of 3.
     p = align.align_plan(3000, 32, 750)
@@ -100,14 +101,16 @@ def test_plan_shapes_and_footprints():
     with pytest.raises(align.AlignError) as e:
         align.align_plan(180000, 32, 45000, budget=1 << 20)
     assert e.value.code == align.ALIGN_E_TOO_LARGE
-    # Stage depth: 32 rows of C=32, fewer rows of C=500.
-    assert align.align_plan(100, 32, 10)["frames_per_stage"] == 32       # one warp: 4 KB stages
+    # Stage depth: 32 rows of C=32, fewer rows of C=500 (8 KB stages for the fast
+    # kernel's shapes, K = 2 or 4 and C <= 512; else 4 KB for one-warp CTAs).
+    assert align.align_plan(100, 32, 10)["frames_per_stage"] == 32       # 4 KB of rows
     assert align.align_plan(3000, 32, 750)["frames_per_stage"] == 32     # 12 warps
     assert align.align_plan(3000, 500, 750)["frames_per_stage"] == 4     # 8 KB cap
-    assert align.align_plan(100, 500, 10)["frames_per_stage"] == 2       # 4 KB stages of 2 KB rows
+    assert align.align_plan(100, 500, 10)["frames_per_stage"] == 4       # 8 KB stages of 2 KB rows
+    assert align.align_plan(100, 600, 10)["frames_per_stage"] == 1       # generic kernel: 4 KB of 2.4 KB rows
     # Rows per stage are a power of two dividing the 32-frame anchor window.
     assert align.align_plan(3000, 96, 750)["frames_per_stage"] == 16     # 8 KB / 384 B = 21 -> 16
-    assert align.align_plan(100, 96, 10)["frames_per_stage"] == 8        # 4 KB / 384 B = 10 -> 8
+    assert align.align_plan(100, 96, 10)["frames_per_stage"] == 16       # 8 KB / 384 B = 21 -> 16
 
 
 @pytest.mark.parametrize("K", [2, 4, 8, 16])

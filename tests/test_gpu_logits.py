@@ -1,19 +1,26 @@
-"""GPU parity of logits inputs (ALIGN_REQ_LOGITS: log_softmax fused into the
-emission staging) against the FP64 log_softmax oracle.
+"""GPU parity of logits inputs (ALIGN_REQ_LOGITS) against the FP64
+log_softmax oracle.
 
-The device's __expf / logf and the host's FP64 exp / log differ, so this is
-parity with a tolerance, derived per element from the FP32 operations of the
-kernel's normalisation (d = the largest |x - m| of the row's finite logits):
-  |lp_gpu - lp64| <= (C + 6 + 2.4 d) * 2^-24 + 2^-22 * (|lse64| + |lp64|)
-  - C * 2^-24: the FP32 sum of C exponentials of non-positive numbers,
-  - (2 + 1.2 d) * 2^-23: __expf's error bound, 2 + floor(1.173 |x|) ulps,
-    relative, carried into the sum and through log,
-  - 4 * 2^-24: logf (1 ulp) on values in [1, C],
-  - 2^-22 * (|lse| + |lp|): the roundings of m + log s and of x - lse.
-Checked: the alignment is legal; every per-frame score is within that bound
-of the FP64 log-probability of its token; the total is the FP32 left fold of
-the per-frame scores; and the path is optimal for the FP64 log-probabilities
-up to twice the summed bound (plus the FP32 fold error of the recursion)."""
+log_softmax subtracts one value per frame, lse_t, from every class of frame
+t, so the best CTC path over the log-probabilities is the best path over the
+raw logits (the sum over any path differs by the same sum of lse_t). The fast
+kernel therefore runs the Viterbi recursion on the logits unchanged and, in
+its score pass, computes lse_t = m + logf(sum_c expf(x - m)) for each frame
+and scores[t] = x[t][path[t]] - lse_t; the total is the sum of the scores in a
+fixed tree order. (Checkpointed requests run the generic kernel, whose lse
+pre-pass subtracts __expf-based shifts from the emissions inside the
+recursion.) Tolerances, derived from the FP32 operations:
+  per frame |lp_gpu - lp64| <= (C + 6 + 2.4 d) * 2^-24 + 2^-22 (|lse64| + |lp64|),
+  d = the largest |x - m| of the row: C * 2^-24 for the FP32 sum of C
+  exponentials of non-positive numbers, (2 + 1.2 d) * 2^-23 for the
+  exponentials (covering __expf's 2 + floor(1.173 |x|) ulps and expf's few
+  ulps with the error of x - m), 4 * 2^-24 for logf on values in [1, C],
+  2^-22 (|lse| + |lp|) for the roundings of m + log s and of x - lse;
+  total: |total - sum(scores)| <= gamma_T * sum |scores| (any summation order);
+  path: optimal for the FP64 log-probabilities up to twice the summed
+  per-frame bound plus twice the FP32 fold error of a path sum of logits,
+  gamma_T * sum_t max_c |x[t][c]| (the recursion's adds on raw logits).
+Checked besides: the alignment is legal and collapses to the transcript."""
 import numpy as np
 import pytest
 import torch
@@ -42,11 +49,14 @@ def check(res, logits, targets, label=""):
     tol = (C + 6 + 2.4 * d) * 2.0 ** -24 + 2.0 ** -22 * (np.abs(lse64) + np.abs(ref))
     err = np.abs(sc.astype(np.float64) - ref)
     assert (err <= tol).all(), (label, float(err.max()), int(np.argmax(err - tol)))
-    assert np.float32(res.total.cpu().numpy()[0]).tobytes() == checks.fold_f32(sc).tobytes(), label
+    total = float(res.total.cpu().numpy()[0])
+    sc64 = sc.astype(np.float64)
+    assert abs(total - sc64.sum()) <= checks.gamma(T) * float(np.abs(sc64).sum()) + 1e-30, (label, total, sc64.sum())
     finite = np.where(np.isfinite(lp64), np.abs(lp64), 0.0)
     rowmax = finite.max(axis=1)
     E = float(((C + 6 + 2.4 * d) * 2.0 ** -24 + 2.0 ** -22 * (np.abs(lse64) + rowmax)).sum())
     E += checks.gamma(T) * float(rowmax.sum()) + float((2.0 ** -24 * rowmax).sum())
+    E += checks.gamma(T) * float(np.nan_to_num(np.nanmax(np.abs(xf), axis=1)).sum())
     best = oracle.viterbi_f64(lp64.astype(np.float32), targets, 0)
     assert best["status"] == 0
     assert ref.sum() >= best["total"] - 2 * E, (label, ref.sum(), best["total"], E)

@@ -539,3 +539,20 @@ def test_graph_replay_equals_direct_launch():
     finally:
         g.close()
         d.close()
+
+
+@pytest.mark.parametrize("K,cw", [(2, 2), (4, 1)])
+def test_every_last_window_length(K, cw):
+    """Frames in the last 32-frame window from 0 to 32 (so the last block of
+    hand-off packages is full, partial, or a single frame), for a team of
+    warps in one CTA and a cluster of one-warp CTAs."""
+    build.build()
+    a = align.Aligner(device=0, bp_budget_bytes=4 << 30)
+    try:
+        a.set_tuning(K, cw, 16)
+        for r in range(33):
+            T = 32 * 5 + 1 + r                 # T - 1 frames after the first: 5 windows + r
+            u = synth.make_utterance(1000 + 37 * r + K, T, 32, 70, repeat_frac=0.1)
+            run(a, u.lp.numpy(), u.targets, 0, f"K{K}cw{cw}r{r}")
+    finally:
+        a.close()
