@@ -137,9 +137,10 @@ inline uint64_t xlink_bytes(int ncta) {
 // anchors) followed by the 2-word team barrier.
 constexpr int kFastPkgs = 8;       // packages of 4 frames per shared-memory link
 constexpr int kFastGridPkgs = 16;  // packages of 4 frames per global link
-constexpr int kFastWinPkgs = 4;    // 32-frame windows per link (window mode)
+constexpr int kFastWinPkgs = 4;    // 32-frame windows per shared-memory link (window mode)
+constexpr int kFastWinGridPkgs = 8;  // 32-frame windows per global link (window mode)
 inline uint64_t fast_xlink_bytes(int ncta, int kb) {
-  const uint64_t slots = (kb == 32) ? kFastWinPkgs : kFastGridPkgs;
+  const uint64_t slots = (kb == 32) ? kFastWinGridPkgs : kFastGridPkgs;
   const uint64_t gstride = 16ull + slots * kb * 8ull;
   const uint64_t b = static_cast<uint64_t>(ncta > 1 ? ncta - 1 : 0) * gstride + 16ull;
   return (b + 255) & ~255ull;

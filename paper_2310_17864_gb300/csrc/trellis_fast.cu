@@ -443,6 +443,9 @@ __global__ void __launch_bounds__(512, 1) trellis_fast_kernel(const FwdJob* __re
 #pragma unroll
     for (int w = 0; w < NW; ++w) bits[w] = 0u;
     auto end_window = [&](const int m, const int t_last) { end_window_bits(bits, m, t_last); };
+    const int nwin_all = nwin_full + (rem > 0 ? 1 : 0);
+    uint64_t pf0 = 0ull, pf1 = 0ull;  // grid teams: window pf_m's words, loaded one window ahead
+    int pf_m = -1;
     int c_stage = 0;
     uint32_t c_round = 0;
     const float* stage_f = reinterpret_cast<const float*>(stages);
@@ -481,28 +484,57 @@ __global__ void __launch_bounds__(512, 1) trellis_fast_kernel(const FwdJob* __re
         }
       }
       if (recv_left) {
-        const int slot = m & (rslots - 1);
-        const uint32_t e = (static_cast<uint32_t>(t_begin + kWin * m + 1 + lane) << 8);
-        const uint32_t raddr = r_data + static_cast<uint32_t>(slot * kWin * 8 + lane * 8);
-        const uint64_t* rp = rg_data ? rg_data + slot * kWin + lane : nullptr;
-        const uint64_t t0 = gtimer();
-        for (;;) {
-          uint64_t w0, w1;
-          ld_words(rscope, raddr & ~15u, rp ? reinterpret_cast<const uint64_t*>(reinterpret_cast<uintptr_t>(rp) & ~static_cast<uintptr_t>(15)) : nullptr, w0, w1);
+        // Shared-memory slot of window m (the per-frame reads use it; grid
+        // teams copy their global words there), R slots.
+        const uint32_t raddr = r_data + static_cast<uint32_t>((m & (R - 1)) * kWin * 8 + lane * 8);
+        // Lane pairs read one 16-byte pair of words; lane i keeps word i.
+        // (Ring slots: rslots in global memory for grid teams, R in shared
+        // memory otherwise; rslots == R for shared-memory links.)
+        auto load_pair = [&](int mm, uint64_t& w0, uint64_t& w1) {
+          const int sl = mm & (rslots - 1);
+          const uint64_t* rp = rg_data ? rg_data + sl * kWin + (lane & ~1) : nullptr;
+          ld_words(rscope, (r_data + static_cast<uint32_t>(sl * kWin * 8 + lane * 8)) & ~15u, rp, w0, w1);
+        };
+        auto tag_ok = [&](int mm, int nfm, uint64_t w0, uint64_t w1) -> bool {
           const uint64_t w = (lane & 1) ? w1 : w0;
-          const bool ok = (lane >= nf) | (static_cast<uint32_t>(w >> 32) - e < 256u);
-          if (__all_sync(kFull, ok)) {
-            // Grid teams: the words come from global memory; keep the window's
-            // copy in this warp's own (otherwise unused) shared ring slot.
-            if (rscope == kLinkGpu) {
-              st_words(kLinkCta, (r_data + static_cast<uint32_t>(slot * kWin * 8 + lane * 8)) & ~15u, nullptr, w0, w1);
-              __syncwarp();
+          const uint32_t e = static_cast<uint32_t>(t_begin + kWin * mm + 1 + lane) << 8;
+          return (lane >= nfm) | (static_cast<uint32_t>(w >> 32) - e < 256u);
+        };
+        auto wait_slot = [&](int mm, int nfm, uint64_t& w0, uint64_t& w1) -> bool {
+          const uint64_t t0 = gtimer();
+          for (;;) {
+            load_pair(mm, w0, w1);
+            if (__all_sync(kFull, tag_ok(mm, nfm, w0, w1))) return true;
+            if (__any_sync(kFull, (*abort != 0) | (gtimer() - t0 > limit))) {
+              if (lane == 0) *abort = 1;
+              return false;
             }
-            break;
           }
-          if (__any_sync(kFull, (*abort != 0) | (gtimer() - t0 > limit))) {
-            if (lane == 0) *abort = 1;
-            return false;
+        };
+        if (rscope != kLinkGpu) {
+          uint64_t w0, w1;
+          if (!wait_slot(m, nf, w0, w1)) return false;
+        } else {
+          // Grid teams: the words come from global memory. This warp runs two
+          // windows behind its sender and loads window m+1's words at the
+          // start of window m, so the L2 round trip overlaps the window's
+          // frames; at the next window start the tags say whether the
+          // prefetched copy is complete (else it is read again). The
+          // window's words are kept in this warp's own (otherwise unused)
+          // shared ring slot for the per-frame reads.
+          uint64_t w0 = pf0, w1 = pf1;
+          if (!(pf_m == m && __all_sync(kFull, tag_ok(m, nf, w0, w1))))
+            if (!wait_slot(m, nf, w0, w1)) return false;
+          st_words(kLinkCta, raddr & ~15u, nullptr, w0, w1);
+          __syncwarp();
+          if (m + 1 < nwin_all) {
+            const int nf1 = (m + 1 < nwin_full) ? kWin : rem;
+            if (m == 0) {  // establish the lag of two windows
+              if (!wait_slot(1, nf1, pf0, pf1)) return false;
+            } else {
+              load_pair(m + 1, pf0, pf1);
+            }
+            pf_m = m + 1;
           }
         }
       }

@@ -950,7 +950,7 @@ FwdParams plan_params(const LaunchShape& shape, int C, int frames_per_stage, uin
     // (C <= 64), else packages of 4 frames.
     p.kb = (F == kAnchorD) ? kAnchorD : 4;
     p.pkgs = (p.kb == kAnchorD) ? kFastWinPkgs : kFastPkgs;
-    p.gpkgs = (p.kb == kAnchorD) ? kFastWinPkgs : kFastGridPkgs;
+    p.gpkgs = (p.kb == kAnchorD) ? kFastWinGridPkgs : kFastGridPkgs;
     p.link_off = static_cast<int>(sizeof(SmemHead));
     p.link_stride = 16 + p.pkgs * p.kb * 8;
     const int hops = std::max(0, shape.warps - 1);
