@@ -50,7 +50,12 @@ int make_plan(const TuneTable& tune_in, int64_t T, int64_t C, int64_t L, uint64_
   // Shape: one CTA of up to cta_warps warps, else a cluster of CTAs of at most
   // cta_warps warps (portable sizes first), else wider CTAs and larger K.
   const int K = tune.K;
-  const auto warp_cap = [&](int) { return std::min(16, tune.max_warps); };
+  // The fast kernel (K = 2 or 4, C <= 512) adds a producer warp to each CTA of
+  // compute warps, so it takes at most 15 of them; the generic kernel 16.
+  const auto warp_cap = [&](int k) {
+    const bool fast_k = (k == 2 || k == 4) && C <= 512;
+    return std::min(fast_k ? 15 : 16, tune.max_warps);
+  };
   const int portable = std::min(8, tune.max_cluster);
   // Transcripts beyond a cluster of the tuned K become grid teams (one CTA
   // per SM, linked through global memory) when the device has the SMs, before

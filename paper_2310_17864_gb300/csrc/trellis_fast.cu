@@ -157,6 +157,22 @@ __device__ __noinline__ bool package_wait(int scope, uint32_t addr, const uint64
   return __shfl_sync(kFull, ok, 0) != 0;
 }
 
+// Two 64-bit words stored by the lanes where `pred` holds (predicated PTX, no
+// branch): relaxed at cluster scope in shared memory, or at gpu scope through
+// a generic address.
+__device__ __forceinline__ void st_cluster_v2u64_if(uint32_t addr, uint64_t x, uint64_t y, bool pred) {
+  asm volatile(
+      "{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %3, 0;\n\t@q st.relaxed.cluster.shared::cluster.v2.u64 [%0], {%1, %2};\n\t}" ::"r"(
+          addr),
+      "l"(x), "l"(y), "r"(static_cast<uint32_t>(pred))
+      : "memory");
+}
+__device__ __forceinline__ void st_gpu_v2u64_if(uint64_t* p, uint64_t x, uint64_t y, bool pred) {
+  asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %3, 0;\n\t@q st.relaxed.gpu.v2.u64 [%0], {%1, %2};\n\t}" ::"l"(p),
+               "l"(x), "l"(y), "r"(static_cast<uint32_t>(pred))
+               : "memory");
+}
+
 // log(sum_c exp(row[c])) of one row of raw logits (max factored out; CUDA's
 // expf / logf). -inf for a row of -inf.
 __device__ float row_lse(const float* __restrict__ row, int C) {
@@ -190,8 +206,9 @@ __global__ void __launch_bounds__(512, 1) trellis_fast_kernel(const FwdJob* __re
 
   const uint32_t ncta = kGrid ? static_cast<uint32_t>(max(P.grid_ctas, 1)) : cluster_nctarank();
   const uint32_t crank = kGrid ? blockIdx.x % ncta : cluster_ctarank();
-  const int W = blockDim.x >> 5;
+  const int W = (blockDim.x >> 5) - 1;  // compute warps; warp W stages the emission rows
   const int warp = threadIdx.x >> 5;
+  const bool producer = (warp == W);
   const int lane = threadIdx.x & 31;
   const FwdJob& J = jobs[blockIdx.x / ncta];
   const int g = static_cast<int>(crank) * W + warp;  // warp index in the team
@@ -244,23 +261,7 @@ __global__ void __launch_bounds__(512, 1) trellis_fast_kernel(const FwdJob* __re
   __syncthreads();
   if (!kGrid && ncta > 1) cluster_sync();  // every CTA's links are zero before any remote store
 
-  // ---- per-lane constants: label columns and skip permissions ----
-  int col[K / 2];
-  bool skok[K / 2];
-#pragma unroll
-  for (int i = 0; i < K / 2; ++i) {
-    const int s = s0 + 2 * i + 1;
-    int lab = 0;
-    bool skip = false;
-    if (s < S) {
-      lab = tgt[(s - 1) >> 1];
-      skip = (s >= 3) && (lab != tgt[(s - 3) >> 1]);
-    }
-    col[i] = lab;
-    skok[i] = skip;
-  }
-
-  // ---- emission staging (warp 0 of each CTA is the producer) ----
+  // ---- emission staging (a dedicated producer warp) ----
   // Chunk c holds the rows of frames t_begin+1+c*F .. t_begin+(c+1)*F in
   // stage c mod stages. F divides the window, kB divides F.
   const int nfr = t_end - 1 - t_begin;  // frames computed in this pass
@@ -290,9 +291,41 @@ __global__ void __launch_bounds__(512, 1) trellis_fast_kernel(const FwdJob* __re
       ++p_round;
     }
   };
-  if (warp == 0) {
-    const int first = min(kLead, nchunks);
-    for (int c = 0; c < first; ++c) issue_next();
+  const int nwin = (nfr + kWin - 1) / kWin;  // anchor rows / backpointer windows of this pass
+  uint8_t* const ztab = J.ztab;
+  const int zstride = J.zstride;
+  // Grid teams: the team barrier follows the CTA links in global memory.
+  uint32_t* const xbar = kGrid ? reinterpret_cast<uint32_t*>(reinterpret_cast<unsigned char*>(J.xlink) +
+                                                            static_cast<size_t>(ncta - 1) * (16 + Rg * kB * 8))
+                               : nullptr;
+  if (producer) {
+    // Every chunk as soon as its stage is free (released by every compute
+    // warp); then every copy in flight lands before the shared memory is
+    // reused. The compute warps only release stages and wait for rows, so
+    // no copy is issued on the recursion's path.
+    for (int c = 0; c < nchunks; ++c) {
+      if (p_round > 0 && !warp_wait_phase(&head->empty[p_stage], (p_round - 1) & 1u, abort, limit, lane)) break;
+      issue_next();
+    }
+    if (lane == 0)
+      for (int c = max(0, issued - P.stages); c < issued; ++c)
+        (void)wait_phase(&head->full[c % P.stages], (c / P.stages) & 1, abort, limit, false);
+  } else {
+
+  // ---- per-lane constants: label columns and skip permissions ----
+  int col[K / 2];
+  bool skok[K / 2];
+#pragma unroll
+  for (int i = 0; i < K / 2; ++i) {
+    const int s = s0 + 2 * i + 1;
+    int lab = 0;
+    bool skip = false;
+    if (s < S) {
+      lab = tgt[(s - 1) >> 1];
+      skip = (s >= 3) && (lab != tgt[(s - 3) >> 1]);
+    }
+    col[i] = lab;
+    skok[i] = skip;
   }
 
   // ---- frame t_begin ----
@@ -327,7 +360,6 @@ __global__ void __launch_bounds__(512, 1) trellis_fast_kernel(const FwdJob* __re
   // last link.
   const int gstride = 16 + Rg * kB * 8;
   unsigned char* const xl = kGrid ? reinterpret_cast<unsigned char*>(J.xlink) : nullptr;
-  uint32_t* const xbar = kGrid ? reinterpret_cast<uint32_t*>(xl + static_cast<size_t>(ncta - 1) * gstride) : nullptr;
   const bool recv_left = g > 0;
   const bool send_local = warp < W - 1;
   const bool send_remote = (warp == W - 1) && (crank + 1 < ncta);
@@ -367,8 +399,6 @@ __global__ void __launch_bounds__(512, 1) trellis_fast_kernel(const FwdJob* __re
   float carry_a = a[K - 1];  // block mode: alpha of the last state at the first frame of the next package
   int carry_A = A[K - 1];
   // Window end: backpointer words, anchor row m, anchors reset, checkpoint.
-  uint8_t* const ztab = J.ztab;
-  const int zstride = J.zstride;
   auto end_window_bits = [&](uint32_t (&bits)[NW], const int m, const int t_last) {
     if (bp != nullptr) {
       uint32_t* dst = bp + (static_cast<size_t>(m) * G + g) * NW * 32 + lane;
@@ -427,17 +457,23 @@ __global__ void __launch_bounds__(512, 1) trellis_fast_kernel(const FwdJob* __re
     uint64_t* const s_gen_local = (kGrid && send_local)
                                       ? reinterpret_cast<uint64_t*>(smem + P.link_off + (warp + 1) * P.link_stride + 16)
                                       : nullptr;
-    auto send_word = [&](int m, int k, uint64_t w) {
+    // Words k, k+1 (k even) of slot m of the right neighbour's ring, in one
+    // 16-byte store by the last lane: a store per frame would sit in the
+    // shared-memory pipe ahead of the next frame's shuffles.
+    auto send_pair = [&](int m, int k, uint64_t w0, uint64_t w1) {
       if constexpr (kGrid) {
         uint64_t* base = send_remote ? slot_ptr_s(m) : s_gen_local + (m & (sslots - 1)) * kWin;
-        st_gpu_u64_if(base + k, w, s_store_pred != 0u);
+        st_gpu_v2u64_if(base + k, w0, w1, s_store_pred != 0u);
       } else {
-        st_cluster_u64_if(slot_addr_s(m) + static_cast<uint32_t>(k * 8), w, s_store_pred != 0u);
+        st_cluster_v2u64_if(slot_addr_s(m) + static_cast<uint32_t>(k * 8), w0, w1, s_store_pred != 0u);
       }
     };
+    // The word of the previous frame (at first this warp's last state at
+    // t_begin, tag t_begin + 1); stored with the next even frame's word.
+    uint64_t prev_w;
     {
       const uint32_t hb0 = (static_cast<uint32_t>(t_begin + 1) << 8) + static_cast<uint32_t>(s_last);
-      send_word(0, 0, (static_cast<uint64_t>(hb0 - static_cast<uint32_t>(A[K - 1])) << 32) | __float_as_uint(a[K - 1]));
+      prev_w = (static_cast<uint64_t>(hb0 - static_cast<uint32_t>(A[K - 1])) << 32) | __float_as_uint(a[K - 1]);
     }
     uint32_t bits[NW];
 #pragma unroll
@@ -462,17 +498,12 @@ __global__ void __launch_bounds__(512, 1) trellis_fast_kernel(const FwdJob* __re
           c_stage = 0;
           ++c_round;
         }
-        if (warp == 0 && issued < nchunks) {
-          if (p_round > 0 && !warp_wait_phase(&head->empty[p_stage], (p_round - 1) & 1u, abort, limit, lane))
-            return false;
-          issue_next();
-        }
       }
       if (!warp_wait_phase(&head->full[c_stage], c_round & 1u, abort, limit, lane)) return false;
       if (has_next && !stall) {
-        // This window writes slots m (words 1..31) and m+1 (word 0); slot
-        // m+1 last held window m+1-slots of the receiver.
-        const uint32_t need = (m + 2 > sslots) ? static_cast<uint32_t>(m + 2 - sslots) : 0u;
+        // This window writes slot m, which last held window m-slots of the
+        // receiver.
+        const uint32_t need = (m + 1 > sslots) ? static_cast<uint32_t>(m + 1 - sslots) : 0u;
         if (cons_seen < need) {
           uint32_t v = need;
           if (lane == 31) v = ld_count(sscope, s_cons, sg ? sg + 1 : nullptr);
@@ -544,6 +575,7 @@ __global__ void __launch_bounds__(512, 1) trellis_fast_kernel(const FwdJob* __re
       if (recv_left && is_l0) st_count(rscope, r_cons, rg ? rg + 1 : nullptr, static_cast<uint32_t>(m + 1));
     };
 
+    uint32_t pk_lo0 = 0u, pk_hi0 = 0u, pk_lo1 = 0u, pk_hi1 = 0u;  // the left neighbour's words of a frame pair
     // Frame i of window m (frame t_begin + 32m + 1 + i).
     auto do_frame = [&](const int m, const int i, const float* rowp, const uint32_t rslot_addr) {
       const uint32_t bit = 1u << i;
@@ -551,12 +583,14 @@ __global__ void __launch_bounds__(512, 1) trellis_fast_kernel(const FwdJob* __re
       float el[K / 2];
 #pragma unroll
       for (int q = 0; q < K / 2; ++q) el[q] = rowp[i * C + col[q]];
-      uint64_t pw;
-      {
-        uint32_t lo, hi;
-        asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(lo), "=r"(hi) : "r"(rslot_addr + static_cast<uint32_t>(i * 8)) : "memory");
-        pw = (static_cast<uint64_t>(hi) << 32) | lo;
-      }
+      // The left neighbour's word of this frame (read in pairs, at even frames).
+      if ((i & 1) == 0)
+        asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+                     : "=r"(pk_lo0), "=r"(pk_hi0), "=r"(pk_lo1), "=r"(pk_hi1)
+                     : "r"(rslot_addr + static_cast<uint32_t>(i * 8))
+                     : "memory");
+      const uint64_t pw = (i & 1) ? ((static_cast<uint64_t>(pk_hi1) << 32) | pk_lo1)
+                                  : ((static_cast<uint64_t>(pk_hi0) << 32) | pk_lo0);
       const float shf = __shfl_up_sync(kFull, a[K - 1], 1);
       const float left = is_l0 ? __uint_as_float(static_cast<uint32_t>(pw)) : shf;
       int Aleft;
@@ -591,15 +625,16 @@ __global__ void __launch_bounds__(512, 1) trellis_fast_kernel(const FwdJob* __re
           a[j] = mm + el[j >> 1];
         }
       }
-      // The word of this frame for the right neighbour: slot m word i+1, or
-      // slot m+1 word 0 for the window's last frame.
+      // The word of this frame for the right neighbour is word i+1 of slot m
+      // (word 0 of slot m+1 for the window's last frame); even frames store
+      // it with the previous frame's word.
       const uint32_t hb = (static_cast<uint32_t>(t_begin + kWin * m + 1) << 8) + static_cast<uint32_t>(s_last);
       const uint64_t w = (static_cast<uint64_t>(hb + (static_cast<uint32_t>(i + 1) << 8) - static_cast<uint32_t>(A[K - 1])) << 32) |
                          __float_as_uint(a[K - 1]);
-      if (i + 1 < kWin)
-        send_word(m, i + 1, w);
+      if ((i & 1) == 0)
+        send_pair(m, i, prev_w, w);
       else
-        send_word(m + 1, 0, w);
+        prev_w = w;
     };
 
     for (int m = 0; m < nwin_full && !dead; ++m) {
@@ -648,8 +683,8 @@ __global__ void __launch_bounds__(512, 1) trellis_fast_kernel(const FwdJob* __re
   auto run_block = [&](auto full, const int m, const int iw0, const int n) -> bool {
     constexpr bool kFullBlk = decltype(full)::value;
     const int ft0 = m * kWin + iw0;  // frames computed before this block
-    // Emission chunk of this block: release the previous stage, refill (warp
-    // 0), wait for the rows.
+    // Emission chunk of this block: release the previous stage, wait for the
+    // rows.
     if ((ft0 & (F - 1)) == 0) {
       if (chunk >= 0) {
         __syncwarp();
@@ -657,11 +692,6 @@ __global__ void __launch_bounds__(512, 1) trellis_fast_kernel(const FwdJob* __re
         if (++c_stage == P.stages) {
           c_stage = 0;
           ++c_round;
-        }
-        if (warp == 0 && issued < nchunks) {
-          if (p_round > 0 && !warp_wait_phase(&head->empty[p_stage], (p_round - 1) & 1u, abort, limit, lane))
-            return false;
-          issue_next();
         }
       }
       ++chunk;
@@ -812,8 +842,6 @@ __global__ void __launch_bounds__(512, 1) trellis_fast_kernel(const FwdJob* __re
     if (!dead) end_window(nwin_full, t_end - 1);
   }
   }
-  const int nwin = (nfr + kWin - 1) / kWin;  // anchor rows / backpointer windows of this pass
-
   // ---- alpha_{T-1} of the two final states ----
   if (!dead && *abort == 0 && t_end == J.T && J.final2 != nullptr) {
 #pragma unroll
@@ -823,11 +851,7 @@ __global__ void __launch_bounds__(512, 1) trellis_fast_kernel(const FwdJob* __re
     }
   }
 
-  // ---- drain: no copy may still target this CTA's shared memory ----
-  if (warp == 0 && lane == 0) {
-    for (int c = max(0, issued - P.stages); c < issued; ++c)
-      (void)wait_phase(&head->full[c % P.stages], (c / P.stages) & 1, abort, limit, false);
-  }
+  }  // compute warps
   // A CTA whose wait ran out marks the request timed out before the team
   // barrier; after it every CTA reads the same status and leaves together.
   auto team_sync_ok = [&]() -> bool {
@@ -904,7 +928,7 @@ __global__ void __launch_bounds__(512, 1) trellis_fast_kernel(const FwdJob* __re
   // its top state is path[e]. The words of a state hold all 32 frames of the
   // window, so a walk reloads them only when the state changes.
   const int nwalk = max(nwin, 1);
-  for (int m = g * 32 + lane; m < nwalk; m += G * 32) {
+  for (int m = g * 32 + lane; !producer && m < nwalk; m += G * 32) {
     const int b = t_begin + m * kAnchorD;
     const int e = (nwin == 0) ? t_begin : min(b + kAnchorD, t_end - 1);
     const uint32_t* wbase = bp + static_cast<size_t>(m) * G * NW * 32;
@@ -935,7 +959,7 @@ __global__ void __launch_bounds__(512, 1) trellis_fast_kernel(const FwdJob* __re
   const int tid = g * 32 + lane;
   const int nthr = G * 32;
   float part = 0.0f;  // logits: this thread's sum of scores (its frames in order)
-  for (int f0 = t_begin + tid; f0 < t_end; f0 += kT3 * nthr) {
+  for (int f0 = t_begin + tid; !producer && f0 < t_end; f0 += kT3 * nthr) {
     int st[kT3], tok[kT3];
     float sv[kT3];
 #pragma unroll
@@ -969,7 +993,7 @@ __global__ void __launch_bounds__(512, 1) trellis_fast_kernel(const FwdJob* __re
     // the warp (every lane ends with the same bits), warps in team order.
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(kFull, part, o);
-    if (lane == 0) J.lse[g] = part;
+    if (lane == 0 && !producer) J.lse[g] = part;
     if (!team_sync_ok()) return;
     if (crank == 0 && warp == 0 && lane == 0 && (J.flags & kJobWriteFinal) && J.total) {
       float tot = 0.0f;
@@ -997,7 +1021,7 @@ cudaError_t launch_fast_k(const LaunchShape& shape, const FwdParams& p, const Fw
   if (smem > smem_max) return cudaErrorInvalidValue;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(static_cast<unsigned>(njobs * shape.ncta), 1, 1);
-  cfg.blockDim = dim3(static_cast<unsigned>(shape.warps * 32), 1, 1);
+  cfg.blockDim = dim3(static_cast<unsigned>((shape.warps + 1) * 32), 1, 1);  // + the producer warp
   cfg.dynamicSmemBytes = static_cast<size_t>(smem);
   cfg.stream = stream;
   cudaLaunchAttribute attr[1];
