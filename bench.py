@@ -359,7 +359,8 @@ def roofline_of(batch, ms: float, t_frame_ns: float, peaks: dict, sm_count: int)
     return rl
 
 
-def run_batched(torch, align, autotune, replicas, batch, dev, stream, flush_buf, steps, warmup, dist, clocks=None):
+def run_batched(torch, align, autotune, replicas, batch, dev, stream, flush_buf, steps, warmup, dist, clocks=None,
+                force_checkpoint=False):
     """Device-timed packed-batch steps of one workload. Returns the step
     times, kernel launches per step, enqueue times and the aligner's budget."""
     n = len(batch)
@@ -372,7 +373,7 @@ def run_batched(torch, align, autotune, replicas, batch, dev, stream, flush_buf,
                                 budget=1 << 40)["backpointer_bytes"] for i in range(n))
     budget = max(4 << 30, int(1.2 * need) + (256 << 20))
     al = align.Aligner(device=dev, batched=True, stream=stream, bp_budget_bytes=budget,
-                       max_inflight=max(8192, 2 * n))
+                       max_inflight=max(8192, 2 * n), force_checkpoint=force_checkpoint)
     tuned = autotune.apply(al)
     timer = DeviceTimer(torch, stream, flush_buf)
 
@@ -407,9 +408,11 @@ def run_batched(torch, align, autotune, replicas, batch, dev, stream, flush_buf,
         al.close()
     launches = (st1["kernel_launches"] - st0["kernel_launches"]) // max(steps, 1)
     tp = (st1["throughput_batches"] - st0["throughput_batches"]) / max(steps, 1)
+    ck = (st1["checkpointed"] - st0["checkpointed"]) / max(steps, 1)
     ms = replicas.slowest(statistics.mean(times), dist, dev)
     return {"times": times, "ms": ms, "launches": int(launches), "tp_batches": tp, "tuned": tuned,
-            "enqueue_ms_median": 1e3 * statistics.median(timer.enqueue), "budget": budget, "out": out}
+            "enqueue_ms_median": 1e3 * statistics.median(timer.enqueue), "budget": budget, "out": out,
+            "checkpointed_per_step": ck}
 
 
 def run_e2e(torch, align, autotune, replicas, batch, dev, budget, steps, dist, world):
@@ -759,16 +762,19 @@ def main():
     legs = None
     if not args.no_legs:
         legs = {}
-        for name in ("longform", "ragged32", "ragged500"):
-            if name == args.workload:
+        # (leg, workload, forced checkpointed recompute)
+        for name, wname, ck in (("longform", "longform", False), ("longform_checkpointed", "longform", True),
+                                ("ragged32", "ragged32", False), ("ragged500", "ragged500", False)):
+            if wname == args.workload and not ck:
                 continue
-            lw = WORKLOADS[name]
+            lw = WORKLOADS[wname]
             lb = make_workload_batch(lw, f"cuda:{dev}")
             lclk = Clocks(dev)
-            r = run_batched(torch, align, autotune, replicas, lb, dev, stream, flush_buf, args.leg_steps,
-                            max(3, args.warmup // 2), dist, clocks=lclk)
+            r = run_batched(torch, align, autotune, replicas, lb, dev, stream, flush_buf,
+                            max(3, args.leg_steps // 2) if ck else args.leg_steps, max(3, args.warmup // 2), dist,
+                            clocks=lclk, force_checkpoint=ck)
             leg = {"metric": METRIC, "value": replicas.job_rate(lb.cells, world, r["ms"]), "unit": "cells/s",
-                   "ms_per_step": r["ms"], "steps": args.leg_steps,
+                   "ms_per_step": r["ms"], "steps": len(r["times"]),
                    "p50_ms": float(np.percentile(r["times"], 50)), "p99_ms": float(np.percentile(r["times"], 99)),
                    "gpu_launches": r["launches"],
                    "config": {"workload": lw["name"], "utterances": len(lb), "cells_per_step": lb.cells,
@@ -776,6 +782,7 @@ def main():
                               "l2": "flushed (256 MiB write) before every timed step",
                               "host_enqueue_ms_median": round(r["enqueue_ms_median"], 3),
                               "throughput_batches_per_step": r["tp_batches"],
+                              "checkpointed_requests_per_step": r["checkpointed_per_step"],
                               "input_sha256": input_digest(lb.lp)},
                    "roofline": roofline_of(lb, r["ms"], t_frame_ns, peaks, sm_count),
                    "clocks": lclk.summary()}

@@ -113,16 +113,33 @@ int make_plan(const TuneTable& tune_in, int64_t T, int64_t C, int64_t L, uint64_
   // kAnchorD frames (fast layout); sized for whole windows, which covers both.
   p.z_off = round_up(row_bytes * zrows(T - 1) * kAnchorD, 256);
   p.bp_bytes = p.z_off + round_up(zrows(T - 1) * p.zstride, 256);
-  // About sqrt(T) frames per checkpoint segment, rounded up to whole anchor
-  // windows so that checkpoint frames end windows.
-  p.ck_every = static_cast<int>(
-      round_up(static_cast<uint64_t>(std::max(1.0, std::ceil(std::sqrt(static_cast<double>(T))))), kAnchorD));
-  p.nck = static_cast<int>((T - 1) / p.ck_every + 1);
-  p.ck_stride = static_cast<int>(round_up(static_cast<uint64_t>(S), 4));
-  p.ckpt_bytes = round_up(static_cast<uint64_t>(p.nck) * p.ck_stride * 4ull, 256);
-  p.seg_z_off = round_up(row_bytes * static_cast<uint64_t>(p.ck_every), 256);
-  p.seg_bp_bytes = p.seg_z_off + round_up(zrows(p.ck_every) * p.zstride, 256);
   p.x_bytes = p.shape.grid ? std::max({xlink_bytes(p.shape.ncta), fast_xlink_bytes(p.shape.ncta, kAnchorD), fast_xlink_bytes(p.shape.ncta, 4)}) : 0;
+  p.ck_stride = static_cast<int>(round_up(static_cast<uint64_t>(S), 4));
+  // Checkpoint segments: every segment of the recompute pass is a new pass
+  // through the team's pipeline of warps, which fills with up to a 32-frame
+  // window of lag per warp boundary (two per CTA boundary of a grid team). So
+  // a segment spans at least about twice that fill (then the recompute pass
+  // costs about one forward pass plus the fills), and at least sqrt(T)
+  // frames; rounded up to whole anchor windows so that checkpoint frames end
+  // windows. A budget that cannot hold such a segment gets shorter ones, down
+  // to sqrt(T) frames.
+  const uint64_t team_warps = static_cast<uint64_t>(p.shape.warps) * p.shape.ncta;
+  const uint64_t fill = static_cast<uint64_t>(kAnchorD) * (team_warps - 1 + (p.shape.grid ? p.shape.ncta - 1 : 0));
+  const uint64_t ck_min =
+      round_up(static_cast<uint64_t>(std::max(1.0, std::ceil(std::sqrt(static_cast<double>(T))))), kAnchorD);
+  const auto set_segments = [&](uint64_t every) {
+    p.ck_every = static_cast<int>(every);
+    p.nck = static_cast<int>((T - 1) / p.ck_every + 1);
+    p.ckpt_bytes = round_up(static_cast<uint64_t>(p.nck) * p.ck_stride * 4ull, 256);
+    p.seg_z_off = round_up(row_bytes * every, 256);
+    p.seg_bp_bytes = p.seg_z_off + round_up(zrows(static_cast<int64_t>(every)) * p.zstride, 256);
+  };
+  uint64_t every = std::max(ck_min, round_up(std::min<uint64_t>(2 * fill, static_cast<uint64_t>(T)), kAnchorD));
+  set_segments(every);
+  while (every > ck_min && p.ckpt_bytes + p.seg_bp_bytes + p.x_bytes > budget) {
+    every = std::max(ck_min, round_up(every / 2, kAnchorD));
+    set_segments(every);
+  }
   p.checkpointed = force_checkpoint || p.bp_bytes + p.x_bytes > budget;
   if (p.checkpointed && p.ckpt_bytes + p.seg_bp_bytes + p.x_bytes > budget) return ALIGN_E_TOO_LARGE;
   *out = p;

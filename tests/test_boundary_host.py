@@ -91,12 +91,20 @@ def test_plan_shapes_and_footprints():
     # Small budget: checkpointed, footprint ~ sqrt(T) rows.
     q = align.align_plan(180000, 32, 45000, budget=1 << 30)
     assert q["checkpointed"] == 1
-    # about sqrt(T) frames per segment, rounded up to whole 32-frame anchor windows
-    assert q["checkpoint_every"] == -(-int(np.ceil(np.sqrt(180000))) // 32) * 32
+    # Segments of whole 32-frame anchor windows, at least sqrt(T) frames and about
+    # twice the team's pipeline fill (a 32-frame window per warp boundary):
+    # 11 CTAs x 16 warps -> 175 boundaries -> 2 x 5600 frames.
+    warps = q["warps_per_cta"] * q["cluster_ctas"]
+    assert q["checkpoint_every"] % 32 == 0 and q["checkpoint_every"] >= np.sqrt(180000)
+    assert q["checkpoint_every"] == 2 * 32 * (warps - 1)
     assert q["checkpoints"] == (180000 - 1) // q["checkpoint_every"] + 1
     assert q["checkpoint_bytes"] < (1 << 30) < q["backpointer_bytes"]
     # Forced checkpointing.
     assert align.align_plan(500, 32, 100, flags=align.ALIGN_F_FORCE_CHECKPOINT)["checkpointed"] == 1
+    # A budget too small for such segments gets shorter ones (down to sqrt(T)).
+    small = align.align_plan(180000, 32, 45000, budget=q["checkpoint_bytes"] // 2)
+    assert small["checkpointed"] == 1 and small["checkpoint_every"] < q["checkpoint_every"]
+    assert small["checkpoint_every"] >= np.sqrt(180000)
     # Nothing fits.
     with pytest.raises(align.AlignError) as e:
         align.align_plan(180000, 32, 45000, budget=1 << 20)
