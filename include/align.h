@@ -67,6 +67,13 @@ extern "C" {
                                          (the one that also serves the sum-product, K >= 8 and
                                          C > 512) instead of the fast kernel for K = 2 or 4; same
                                          results, for comparison and testing */
+#define ALIGN_F_PERSISTENT 0x40u      /* batches whose requests all qualify (log-probabilities on the
+                                         device, one vocabulary with 16-byte rows, full backpointers
+                                         within the budget, every team within the resident CTAs)
+                                         run as ONE persistent launch: resident CTAs take the
+                                         requests' seats from a device counter, longest first, with
+                                         one kernel shape (the tuning table's for the batch's median
+                                         S, K = 2 or 4); other batches launch per shape group */
 #define ALIGN_F_TEST_STALL 0x80000000u /* testing the device watchdog only: in every request whose
                                          trellis spans more than one warp, the first warp never
                                          hands its values on, so the next warp's bounded wait runs
@@ -205,6 +212,7 @@ typedef struct {
     uint64_t throughput_batches; /* batches planned with the throughput tuning table */
     uint64_t grid_teams;        /* finished requests that ran as a grid team */
     uint64_t sum_requests;      /* finished sum-product (ALIGN_REQ_SUM) requests */
+    uint64_t persistent_batches; /* batches launched as one persistent launch (ALIGN_F_PERSISTENT) */
 } align_stats;
 
 int align_get_stats(align_ctx *ctx, align_stats *out, int32_t reset);

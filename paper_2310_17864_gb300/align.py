@@ -39,6 +39,7 @@ ALIGN_F_NO_GRAPHS = 0x4
 ALIGN_F_NO_GRID_TEAMS = 0x8
 ALIGN_F_DEBUG_CHECKS = 0x10
 ALIGN_F_GENERIC_KERNEL = 0x20
+ALIGN_F_PERSISTENT = 0x40
 ALIGN_F_TEST_STALL = 0x80000000
 
 # Every entry point declared in include/align.h.
@@ -77,7 +78,7 @@ class AlignStats(ctypes.Structure):
                 ("requests_done", ctypes.c_uint64), ("cells", ctypes.c_uint64),
                 ("checkpointed", ctypes.c_uint64), ("bp_bytes_peak", ctypes.c_uint64),
                 ("throughput_batches", ctypes.c_uint64), ("grid_teams", ctypes.c_uint64),
-                ("sum_requests", ctypes.c_uint64)]
+                ("sum_requests", ctypes.c_uint64), ("persistent_batches", ctypes.c_uint64)]
 
 
 class AlignPlanInfo(ctypes.Structure):
@@ -450,7 +451,7 @@ class Aligner:
                  staging_bytes: int = 0, stream=None, force_checkpoint: bool = False,
                  wait_limit_ms: int = 0, max_inflight: int = 0, graphs: bool = True,
                  test_stall: bool = False, grid_teams: bool = True, debug_checks: bool = False,
-                 generic_kernel: bool = False):
+                 generic_kernel: bool = False, persistent: bool = False):
         import torch
         self.torch = torch
         self.device = device
@@ -460,6 +461,7 @@ class Aligner:
         flags |= ALIGN_F_TEST_STALL if test_stall else 0
         flags |= ALIGN_F_DEBUG_CHECKS if debug_checks else 0
         flags |= ALIGN_F_GENERIC_KERNEL if generic_kernel else 0
+        flags |= ALIGN_F_PERSISTENT if persistent else 0
         cfg = AlignConfig(device=device, max_inflight=max_inflight, bp_budget_bytes=bp_budget_bytes,
                           staging_bytes=staging_bytes,
                           cuda_stream=(stream.cuda_stream if stream is not None else None), flags=flags,

@@ -55,6 +55,13 @@ int validate_request(const int32_t* targets, int64_t L, int64_t C, int32_t blank
 // Shape and footprint of a request; ALIGN_E_TOO_LARGE if it cannot run within budget.
 int make_plan(const TuneTable& tune, int64_t T, int64_t C, int64_t L, uint64_t budget, bool force_checkpoint,
               Plan* out);
+// Footprint and staging of a request whose shape is already set in *shape_plan.
+int plan_footprint(int64_t T, int64_t C, int64_t L, uint64_t budget, bool force_checkpoint, Plan* shape_plan,
+                   Plan* out);
+// Plan of a request in a persistent launch: the fixed shape (K states per
+// lane, `warps` compute warps per CTA), ceil(S / (32 K warps)) CTAs per team,
+// full backpointers (ALIGN_E_TOO_LARGE otherwise; no CTA links of its own).
+int make_persist_plan(int K, int warps, int64_t T, int64_t C, int64_t L, uint64_t budget, Plan* out);
 
 // Device staging of a host-I/O request: emissions, then outputs.
 struct HostStage {

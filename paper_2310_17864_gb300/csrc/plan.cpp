@@ -92,6 +92,29 @@ int make_plan(const TuneTable& tune_in, int64_t T, int64_t C, int64_t L, uint64_
     }
   }
   if (!found) return ALIGN_E_TOO_LARGE;
+  return plan_footprint(T, C, L, budget, force_checkpoint, &p, out);
+}
+
+int make_persist_plan(int K, int warps, int64_t T, int64_t C, int64_t L, uint64_t budget, Plan* out) {
+  if ((K != 2 && K != 4) || warps < 1 || warps > 15 || C > 512) return ALIGN_E_INVAL;
+  Plan p{};
+  const uint64_t S = static_cast<uint64_t>(2 * L + 1);
+  const uint64_t ncta = ceil_div(S, 32ull * K * static_cast<uint64_t>(warps));
+  p.shape = LaunchShape{K, warps, static_cast<int>(ncta)};
+  p.shape.grid = 1;  // CTAs of a team link through global memory
+  const int rc = plan_footprint(T, C, L, budget, false, &p, out);
+  if (rc != ALIGN_OK) return rc;
+  if (out->checkpointed) return ALIGN_E_TOO_LARGE;  // persistent launches keep full backpointers
+  out->shape.persist = 1;
+  out->x_bytes = 0;  // the links of a persistent batch are one region of the batch
+  return ALIGN_OK;
+}
+
+// Footprint and staging of a request whose kernel shape (K, warps, CTAs,
+// grid) is set in *p.
+int plan_footprint(int64_t T, int64_t C, int64_t L, uint64_t budget, bool force_checkpoint, Plan* pp, Plan* out) {
+  Plan& p = *pp;
+  const int64_t S = 2 * L + 1;
   // The fast Viterbi kernel serves K = 2 or 4 with at least 4 frames per
   // emission stage (C <= 512); its stages are 8 KB. Other shapes (and the
   // sum-product, and logits requests that run checkpointed) use the generic

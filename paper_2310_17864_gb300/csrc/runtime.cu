@@ -175,6 +175,7 @@ struct Batch {
   MetaBlock* h_meta = nullptr;  // pinned copy of the requests' metadata blocks
   bool finished = false;
   std::vector<cudaEvent_t> events;     // pooled events used by this batch
+  Alloc xlink;     // persistent launches: the teams' CTA links (backpointer arena)
 };
 
 }  // namespace
@@ -216,6 +217,7 @@ struct align_ctx {
   TuneTable tune_tp;  // throughput shapes (nbuckets == 0: not set)
   int num_sms = 0;
   int smem_optin = 0;
+  std::map<std::tuple<int, int, int>, int> persist_ctas;  // (K, warps, C) -> resident CTAs of that shape
   align_stats stats{};
 };
 
@@ -291,11 +293,12 @@ int finish_batch(align_ctx* ctx, Batch& b) {
     ctx->stats.requests_done++;
     ctx->stats.cells += static_cast<uint64_t>(r.T) * static_cast<uint64_t>(2 * r.L + 1);
     if (r.plan.checkpointed) ctx->stats.checkpointed++;
-    if (r.plan.shape.grid) ctx->stats.grid_teams++;
+    if (r.plan.shape.grid && !r.plan.shape.persist) ctx->stats.grid_teams++;
     if (r.sum) ctx->stats.sum_requests++;
   }
   if (b.meta.live) ctx->meta_arena.release(b.meta.off, b.meta.bytes), b.meta.live = false;
   if (b.pinned.live) ctx->pinned_arena.release(b.pinned.off, b.pinned.bytes), b.pinned.live = false;
+  if (b.xlink.live) ctx->bp_arena.release(b.xlink.off, b.xlink.bytes), b.xlink.live = false;
   if (b.graph >= 0) ctx->graphs[static_cast<size_t>(b.graph)].busy = false;
   b.finished = true;
   return ALIGN_OK;
@@ -330,7 +333,7 @@ uint64_t request_bp_bytes(const Plan& p) { return plan_device_bytes(p); }
 // table. Plans are only
 // remade for requests whose table changes; a request keeps its plan if the
 // other table cannot place it.
-bool choose_tables(align_ctx* ctx) {
+bool want_throughput(const align_ctx* ctx) {
   if (ctx->tune_tp.nbuckets == 0) return false;
   uint64_t work = 0;
   int64_t tmax = 0;
@@ -340,8 +343,12 @@ bool choose_tables(align_ctx* ctx) {
     tmax = std::max(tmax, r.T);
   }
   // One request alone is a latency problem whatever its size.
-  const bool tp = ctx->queued.size() >= 2 &&
-                  work > static_cast<uint64_t>(tmax) * 8ull * static_cast<uint64_t>(std::max(1, ctx->num_sms));
+  return ctx->queued.size() >= 2 &&
+         work > static_cast<uint64_t>(tmax) * 8ull * static_cast<uint64_t>(std::max(1, ctx->num_sms));
+}
+
+bool choose_tables(align_ctx* ctx) {
+  const bool tp = want_throughput(ctx);
   const int want = tp ? ALIGN_TUNE_THROUGHPUT : ALIGN_TUNE_LATENCY;
   for (uint64_t id : ctx->queued) {
     Request& r = ctx->reqs.at(id);
@@ -356,9 +363,79 @@ bool choose_tables(align_ctx* ctx) {
   return tp;
 }
 
+constexpr int kPersistTable = 2;  // plan_table of a request planned for a persistent launch
+
+// Resident CTAs of a persistent launch of shape (K, warps) over rows of C
+// classes (cached per context), or 0.
+int persist_ctas(align_ctx* ctx, const LaunchShape& shape, int C, int F) {
+  const auto key = std::make_tuple(shape.K, shape.warps, C);
+  auto it = ctx->persist_ctas.find(key);
+  if (it != ctx->persist_ctas.end()) return it->second;
+  const FwdParams P = plan_params(shape, C, F, ctx->wait_limit_ns);
+  int n = 0;
+  if (persist_max_ctas(shape, P, ctx->device, &n) != 0) {
+    (void)cudaGetLastError();
+    n = 0;
+  }
+  ctx->persist_ctas[key] = n;
+  return n;
+}
+
+// Whether the queued requests run as one persistent launch; if so, every
+// queued request is planned with the batch's one shape: K states per lane and
+// W compute warps from the tuning table's entry for the median S (K = 2 or 4,
+// W <= 15), ceil(S / (32 K W)) CTAs per team. Every request must align
+// log-probabilities in device memory with 16-byte rows of one vocabulary
+// C <= 512, keep full backpointers within the budget, and have a team of at
+// most the resident CTAs of that shape. Otherwise plans made for a persistent
+// launch are remade by choose_tables.
+bool choose_persist(align_ctx* ctx, bool tp) {
+  if (!(ctx->flags & ALIGN_F_PERSISTENT) || (ctx->flags & (ALIGN_F_GENERIC_KERNEL | ALIGN_F_FORCE_CHECKPOINT)) ||
+      ctx->queued.size() < 2)
+    return false;
+  const int64_t C = ctx->reqs.at(ctx->queued.front()).C;
+  std::vector<int64_t> S;
+  S.reserve(ctx->queued.size());
+  for (uint64_t id : ctx->queued) {
+    const Request& r = ctx->reqs.at(id);
+    if (r.sum || r.logits || r.host_io || r.C != C || C > 512 || !rows_bulk_ok(r.lp, r.C)) return false;
+    S.push_back(2 * r.L + 1);
+  }
+  std::nth_element(S.begin(), S.begin() + static_cast<std::ptrdiff_t>(S.size() / 2), S.end());
+  const TuneTable t = resolve_tuning(tp ? ctx->tune_tp : ctx->tune, S[S.size() / 2]);
+  const int K = (t.K == 2) ? 2 : 4;
+  const int W = std::max(1, std::min({t.cta_warps, t.max_warps, 15}));
+  std::vector<std::pair<Request*, Plan>> plans;
+  plans.reserve(ctx->queued.size());
+  for (uint64_t id : ctx->queued) {
+    Request& r = ctx->reqs.at(id);
+    Plan p{};
+    if (r.plan_table == kPersistTable && r.plan.shape.K == K && r.plan.shape.warps == W) {
+      p = r.plan;
+    } else if (make_persist_plan(K, W, r.T, r.C, r.L, ctx->bp_arena.cap(), &p) != ALIGN_OK) {
+      return false;
+    }
+    plans.emplace_back(&r, p);
+  }
+  LaunchShape one = plans.front().second.shape;
+  one.ncta = 1;
+  const int ctas = persist_ctas(ctx, one, static_cast<int>(C), plans.front().second.frames_per_stage);
+  for (const auto& rp : plans)
+    if (rp.second.shape.ncta > ctas) return false;
+  for (auto& rp : plans) {
+    rp.first->plan = rp.second;
+    rp.first->plan_table = kPersistTable;
+  }
+  return true;
+}
+
+int launch_persistent(align_ctx* ctx, std::vector<Request*>& take);
+
 int launch_queued(align_ctx* ctx) {
   if (ctx->queued.empty()) return ALIGN_OK;
-  const bool tp_batch = choose_tables(ctx);
+  const bool tp_want = want_throughput(ctx);
+  const bool persist = choose_persist(ctx, tp_want);
+  const bool tp_batch = persist ? tp_want : choose_tables(ctx);
   std::vector<Request*> take;
   std::deque<uint64_t> keep;
   uint64_t meta_est = 0;  // descriptor + metadata + targets bytes of the batch
@@ -368,7 +445,7 @@ int launch_queued(align_ctx* ctx) {
     const uint64_t id = ctx->queued.front();
     Request& r = ctx->reqs.at(id);
     uint64_t m = (1 + static_cast<uint64_t>(r.plan.nck)) * sizeof(FwdJob) + 64 +
-                 static_cast<uint64_t>(r.L) * 4 + 16;
+                 static_cast<uint64_t>(r.L) * 4 + 16 + static_cast<uint64_t>(r.plan.shape.ncta) * 4;
     if (r.host_io && r.lp_alias) {  // batched-copy chunks of this request
       const uint64_t T = static_cast<uint64_t>(r.T);
       m += (T * static_cast<uint64_t>(r.C) * 4 / kCopyChunk + 3 * (T * 4 / kCopyChunk) + 5) * sizeof(CopyChunk);
@@ -379,6 +456,10 @@ int launch_queued(align_ctx* ctx) {
     Plan& p = r.plan;
     uint64_t need = request_bp_bytes(p);
     if (!p.checkpointed && !ctx->bp_arena.alloc(need, &r.bp.off)) {
+      if (p.shape.persist) {  // persistent launches keep full backpointers: wait for memory
+        keep.push_back(id);
+        continue;
+      }
       // Full backpointers do not fit now: fall back to checkpointed recompute
       // if that fits, otherwise wait for memory to be released.
       const uint64_t ck_need = p.ckpt_bytes + p.seg_bp_bytes + p.x_bytes;
@@ -420,6 +501,10 @@ int launch_queued(align_ctx* ctx) {
   std::stable_sort(take.begin(), take.end(), [](const Request* a, const Request* b) {
     return a->T * (2 * a->L + 1) > b->T * (2 * b->L + 1);
   });
+  if (persist) {
+    if (tp_batch) ctx->stats.throughput_batches++;
+    return launch_persistent(ctx, take);
+  }
 
   // Descriptor image: full-mode jobs grouped by shape; checkpointed requests
   // get 1 + nck descriptors each.
@@ -909,6 +994,157 @@ int launch_queued(align_ctx* ctx) {
     if (rc != ALIGN_OK) return rc;
     ctx->stats.kernel_launches += nkernels;
   }
+  b.done = take_event(ctx);
+  b.events.push_back(b.done);
+  CU(cudaEventRecord(b.done, s0));
+  ctx->batches.emplace(b.id, b);
+  return ALIGN_OK;
+}
+
+// One persistent launch over the admitted requests (all planned by
+// choose_persist with one shape): descriptors in seat order (longest chain
+// first), the seat table and the seat counter in one upload; the teams' CTA
+// links in one zeroed region of the backpointer arena.
+int launch_persistent(align_ctx* ctx, std::vector<Request*>& take) {
+  std::stable_sort(take.begin(), take.end(), [](const Request* a, const Request* b) { return a->T > b->T; });
+  const size_t n = take.size();
+  const LaunchShape shape = [&] {
+    LaunchShape sh = take[0]->plan.shape;
+    sh.ncta = 1;
+    return sh;
+  }();
+  const int C = static_cast<int>(take[0]->C);
+  const int F = take[0]->plan.frames_per_stage;
+  const FwdParams P = plan_params(shape, C, F, ctx->wait_limit_ns);
+  int64_t total_seats = 0;
+  uint64_t x_bytes = 0, tgt_words = 0;
+  std::vector<uint64_t> x_off(n, 0);
+  for (size_t i = 0; i < n; ++i) {
+    const int ncta = take[i]->plan.shape.ncta;
+    total_seats += ncta;
+    if (ncta > 1) {
+      x_off[i] = x_bytes;
+      x_bytes += fast_xlink_bytes(ncta, P.kb);
+    }
+    tgt_words += round_up(static_cast<uint64_t>(std::max<int64_t>(take[i]->L, 1)), 4);
+  }
+  const uint64_t off_jobs = 0;
+  const uint64_t off_metas = round_up(n * sizeof(FwdJob), kAlign);
+  const uint64_t off_tgts = round_up(off_metas + n * sizeof(MetaBlock), kAlign);
+  const uint64_t off_seats = round_up(off_tgts + tgt_words * 4, kAlign);
+  const uint64_t off_counter = round_up(off_seats + static_cast<uint64_t>(total_seats) * 4, kAlign);
+  const uint64_t up_bytes = round_up(off_counter + 16, kAlign);
+  const uint64_t pin_bytes = up_bytes + round_up(n * sizeof(MetaBlock), kAlign);
+
+  Batch b;
+  b.id = ctx->next_batch++;
+  auto unwind = [&]() {
+    if (b.meta.live) ctx->meta_arena.release(b.meta.off, b.meta.bytes), b.meta.live = false;
+    if (b.pinned.live) ctx->pinned_arena.release(b.pinned.off, b.pinned.bytes), b.pinned.live = false;
+    if (b.xlink.live) ctx->bp_arena.release(b.xlink.off, b.xlink.bytes), b.xlink.live = false;
+    for (auto it = take.rbegin(); it != take.rend(); ++it) {
+      Request* r = *it;
+      if (r->bp.live) ctx->bp_arena.release(r->bp.off, r->bp.bytes), r->bp.live = false;
+      ctx->queued.push_front(r->id);
+    }
+    return ALIGN_OK;  // retried after other batches release memory
+  };
+  if (!ctx->meta_arena.alloc(up_bytes, &b.meta.off)) return unwind();
+  b.meta.bytes = up_bytes;
+  b.meta.live = true;
+  if (!ctx->pinned_arena.alloc(pin_bytes, &b.pinned.off)) return unwind();
+  b.pinned.bytes = pin_bytes;
+  b.pinned.live = true;
+  if (x_bytes) {
+    if (!ctx->bp_arena.alloc(x_bytes, &b.xlink.off)) return unwind();
+    b.xlink.bytes = x_bytes;
+    b.xlink.live = true;
+  }
+  char* h = ctx->h_pinned + b.pinned.off;
+  char* d = ctx->d_meta + b.meta.off;
+  FwdJob* hjobs = reinterpret_cast<FwdJob*>(h + off_jobs);
+  MetaBlock* hmeta = reinterpret_cast<MetaBlock*>(h + off_metas);
+  int32_t* htgt = reinterpret_cast<int32_t*>(h + off_tgts);
+  int32_t* hseat = reinterpret_cast<int32_t*>(h + off_seats);
+  MetaBlock* dmeta = reinterpret_cast<MetaBlock*>(d + off_metas);
+  const int32_t* dtgt = reinterpret_cast<const int32_t*>(d + off_tgts);
+  b.h_meta = reinterpret_cast<MetaBlock*>(h + up_bytes);
+  std::memset(h + off_counter, 0, 16);
+  char* d_x = x_bytes ? ctx->d_bp + b.xlink.off : nullptr;
+  uint64_t tw = 0;
+  int32_t seat = 0;
+  for (size_t i = 0; i < n; ++i) {
+    Request& r = *take[i];
+    const Plan& p = r.plan;
+    r.state = ReqState::Launched;
+    r.batch = b.id;
+    r.meta_index = static_cast<int>(i);
+    b.reqs.push_back(r.id);
+    hmeta[i].status = ALIGN_PENDING;
+    hmeta[i].state_io = 0;
+    hmeta[i].final2[0] = hmeta[i].final2[1] = -INFINITY;
+    b.h_meta[i].status = ALIGN_PENDING;
+    if (r.L) std::memcpy(htgt + tw, r.targets.data(), static_cast<size_t>(r.L) * 4);
+    FwdJob j{};
+    j.lp = r.lp;
+    j.tgt = dtgt + tw;
+    tw += round_up(static_cast<uint64_t>(std::max<int64_t>(r.L, 1)), 4);
+    j.status = &dmeta[i].status;
+    j.state_io = &dmeta[i].state_io;
+    j.final2 = dmeta[i].final2;
+    j.path = r.out.path;
+    j.scores = r.out.scores;
+    j.total = r.out.total;
+    j.states = r.out.states;
+    j.T = static_cast<int32_t>(r.T);
+    j.C = static_cast<int32_t>(r.C);
+    j.blank = r.blank;
+    j.L = static_cast<int32_t>(r.L);
+    j.S = static_cast<int32_t>(2 * r.L + 1);
+    j.flags = kJobBulkRows | kJobWriteFinal | kJobChase | ((ctx->flags & ALIGN_F_TEST_STALL) ? kJobTestStall : 0u);
+    j.bp = reinterpret_cast<uint32_t*>(ctx->d_bp + r.bp.off);
+    j.ztab = reinterpret_cast<uint8_t*>(ctx->d_bp + r.bp.off + p.z_off);
+    j.zstride = p.zstride;
+    j.t_begin = 0;
+    j.t_end = j.T;
+    j.bp_rows = std::max(j.T - 1, 0);
+    j.xlink = p.shape.ncta > 1 ? reinterpret_cast<uint64_t*>(d_x + x_off[i]) : nullptr;
+    j.team_ctas = p.shape.ncta;
+    j.first_seat = seat;
+    for (int c = 0; c < p.shape.ncta; ++c) hseat[seat++] = static_cast<int32_t>(i);
+    hjobs[i] = j;
+  }
+
+  // One idle worker stream (the batch forks from the main stream).
+  cudaStream_t s0 = nullptr;
+  for (size_t k = 0; k < ctx->workers.size() && !s0; ++k) {
+    cudaStream_t s = ctx->workers[(static_cast<size_t>(ctx->next_worker) + k) % ctx->workers.size()];
+    if (cudaStreamQuery(s) == cudaSuccess) s0 = s;
+  }
+  ctx->next_worker = static_cast<int>((static_cast<size_t>(ctx->next_worker) + 1) % ctx->workers.size());
+  if (!s0 && ctx->workers.size() < kMaxStreams) {
+    CU(cudaStreamCreateWithFlags(&s0, cudaStreamNonBlocking));
+    ctx->workers.push_back(s0);
+  }
+  if (!s0) s0 = ctx->workers[static_cast<size_t>(ctx->next_worker) % ctx->workers.size()];
+  cudaEvent_t fork = ctx->fork_events[static_cast<size_t>(b.id) % ctx->fork_events.size()];
+  CU(cudaEventRecord(fork, ctx->main));
+  CU(cudaStreamWaitEvent(s0, fork, 0));
+  CU(cudaMemcpyAsync(d, h, up_bytes, cudaMemcpyHostToDevice, s0));
+  if (x_bytes) CU(cudaMemsetAsync(d_x, 0, x_bytes, s0));
+  const int ctas = persist_ctas(ctx, shape, C, F);
+  const cudaError_t e = static_cast<cudaError_t>(
+      launch_trellis_persist(shape, P, reinterpret_cast<const FwdJob*>(d + off_jobs),
+                             reinterpret_cast<const int32_t*>(d + off_seats), static_cast<int32_t>(total_seats),
+                             reinterpret_cast<int32_t*>(d + off_counter), ctas, s0));
+  if (e != cudaSuccess) {
+    set_error("launch_trellis_persist", e);
+    return ALIGN_E_CUDA;
+  }
+  CU(cudaMemcpyAsync(b.h_meta, dmeta, n * sizeof(MetaBlock), cudaMemcpyDeviceToHost, s0));
+  ctx->stats.kernel_launches += 1;
+  ctx->stats.persistent_batches++;
+  ctx->stats.bp_bytes_peak = std::max(ctx->stats.bp_bytes_peak, ctx->bp_arena.peak());
   b.done = take_event(ctx);
   b.events.push_back(b.done);
   CU(cudaEventRecord(b.done, s0));

@@ -79,6 +79,8 @@ struct alignas(16) FwdJob {
   uint8_t* ztab;           // anchor rows: row m holds s - anchor(s) at the end of window m
   uint64_t* xlink;         // grid teams: links between consecutive CTAs (zeroed before launch)
   float* lse;              // logits mode: per-frame log_softmax shift [T] (written by the lse pre-pass)
+  int32_t team_ctas;       // persistent launches: CTAs of this job's team
+  int32_t first_seat;      // persistent launches: the team's first seat (rank 0)
 };
 
 struct FwdParams {
@@ -121,6 +123,7 @@ struct LaunchShape {
   int norm = 0;            // 1: inputs are raw logits: an lse pre-pass runs before the launch
   int sum = 0;             // 1: sum-product forward score only (log-add in place of max)
   int fast = 0;            // 1: the fast Viterbi kernel (K = 2 or 4, at least 4 frames per stage)
+  int persist = 0;         // 1: a job of a persistent launch (teams of any CTAs, global links)
 };
 
 // Bytes of the global links of a grid team of ncta CTAs: a ring of kMaxRing
@@ -163,6 +166,16 @@ int launch_trellis(const LaunchShape& shape, const FwdParams& p, const FwdJob* d
 
 // The fast Viterbi kernel (trellis_fast.cu) for shapes with fast = 1.
 int launch_trellis_fast(const LaunchShape& shape, const FwdParams& p, const FwdJob* d_jobs, int njobs, void* stream);
+
+// One persistent launch over the jobs of a batch planned with one shape
+// (trellis_fast.cu): `ctas` resident CTAs take the `total_seats` seats in
+// order from *d_counter (zero before the launch); seat x is job
+// d_seat_job[x]. Every job's rows must be 16-byte aligned.
+int launch_trellis_persist(const LaunchShape& shape, const FwdParams& p, const FwdJob* d_jobs,
+                           const int32_t* d_seat_job, int32_t total_seats, int32_t* d_counter, int ctas,
+                           void* stream);
+// The most CTAs of that shape that are resident at once on the device.
+int persist_max_ctas(const LaunchShape& shape, const FwdParams& p, int device, int* ctas);
 
 // Null-work frame-latency probe (warp-scope chain of one frame); d_out[0] =
 // ns for `frames` frames measured by CTA 0, d_out[1] = 0.

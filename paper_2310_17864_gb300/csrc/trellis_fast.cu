@@ -220,25 +220,41 @@ __device__ float row_lse(const float* __restrict__ row, int C, bool vec4) {
 // from every state of that frame, so the Viterbi choices over the logits
 // equal those over the log-probabilities: the frame loop runs on the logits
 // unchanged, and the score pass subtracts each chosen frame's log-sum-exp.
+// The dynamic shared memory of the fast kernels.
+__device__ __forceinline__ unsigned char* fast_smem() {
+  extern __shared__ __align__(128) unsigned char smem_dyn[];
+  return smem_dyn;
+}
+
+// Positions in the ring of emission stages, kept across the jobs a
+// persistent CTA runs: the producer's next stage and round, and the compute
+// warps' current ones (the mbarrier phases follow the rounds).
+struct StageRing {
+  int p_stage = 0;
+  uint32_t p_round = 0;
+  int c_stage = 0;
+  uint32_t c_round = 0;
+};
+
+// The whole hot path of one job for one CTA of its team: this CTA is rank
+// `crank` of `ncta` CTAs. The stage barriers are initialised by the caller.
 template <int K, int kB, bool kGrid, bool kNorm>
-__global__ void __launch_bounds__(512, 1) trellis_fast_kernel(const FwdJob* __restrict__ jobs, const FwdParams P) {
+__device__ __forceinline__ void team_job(const FwdJob& J, const FwdParams& P, const uint32_t ncta, const uint32_t crank,
+                                         StageRing& ring) {
   static_assert(K == 2 || K == 4, "fast kernel: K = 2 or 4");
   static_assert(kB == 4 || kB == 8 || kB == kAnchorD, "fast kernel: blocks of 4 or 8 frames, or whole windows");
   constexpr int NW = bp_words(K);
   constexpr int GS = 32 * K;
   constexpr int kWin = kAnchorD;
-  extern __shared__ __align__(128) unsigned char smem[];
+  unsigned char* const smem = fast_smem();
   SmemHead* head = reinterpret_cast<SmemHead*>(smem);
   unsigned char* stages = smem + P.off_stage;
   volatile int32_t* abort = &head->abort;
 
-  const uint32_t ncta = kGrid ? static_cast<uint32_t>(max(P.grid_ctas, 1)) : cluster_nctarank();
-  const uint32_t crank = kGrid ? blockIdx.x % ncta : cluster_ctarank();
   const int W = (blockDim.x >> 5) - 1;  // compute warps; warp W stages the emission rows
   const int warp = threadIdx.x >> 5;
   const bool producer = (warp == W);
   const int lane = threadIdx.x & 31;
-  const FwdJob& J = jobs[blockIdx.x / ncta];
   const int g = static_cast<int>(crank) * W + warp;  // warp index in the team
   const int G = static_cast<int>(ncta) * W;
   const int S = J.S, C = J.C, blank = J.blank;
@@ -265,7 +281,7 @@ __global__ void __launch_bounds__(512, 1) trellis_fast_kernel(const FwdJob* __re
   if (F * C * 4 > P.stage_bytes || static_cast<int64_t>(ncta) * W * 32 * K < S || P.stages < kLead ||
       P.stages > kMaxStages || F < kB || F > kAnchorD || (F & (F - 1)) != 0 || P.kb != kB || R < 2 ||
       (R & (R - 1)) != 0 || P.link_stride < 16 + R * kB * 8 || !ck_ok ||
-      (kGrid && (P.grid_ctas < 1 || J.xlink == nullptr || Rg < 2 || (Rg & (Rg - 1)) != 0))) {
+      (kGrid && ncta > 1 && (J.xlink == nullptr || Rg < 2 || (Rg & (Rg - 1)) != 0))) {
     if (threadIdx.x == 0 && crank == 0) atomicExch(J.status, kStBadLaunch);
     return;
   }
@@ -278,14 +294,7 @@ __global__ void __launch_bounds__(512, 1) trellis_fast_kernel(const FwdJob* __re
     for (int i = threadIdx.x; i < n16; i += blockDim.x) lk[i] = make_uint4(0u, 0u, 0u, 0u);
   }
   const bool bulk = (J.flags & kJobBulkRows) != 0;
-  if (threadIdx.x == 0) {
-    for (int st = 0; st < P.stages; ++st) {
-      mbar_init(&head->full[st], bulk ? 1u : 32u);
-      mbar_init(&head->empty[st], static_cast<uint32_t>(W));
-    }
-    head->abort = 0;
-    fence_barrier_init();
-  }
+  if (threadIdx.x == 0) head->abort = 0;
   __syncthreads();
   if (!kGrid && ncta > 1) cluster_sync();  // every CTA's links are zero before any remote store
 
@@ -295,8 +304,8 @@ __global__ void __launch_bounds__(512, 1) trellis_fast_kernel(const FwdJob* __re
   const int nfr = t_end - 1 - t_begin;  // frames computed in this pass
   const int nchunks = (nfr + F - 1) / F;
   int issued = 0;
-  int p_stage = 0;
-  uint32_t p_round = 0;
+  int& p_stage = ring.p_stage;
+  uint32_t& p_round = ring.p_round;
   auto issue_next = [&]() {
     const int f0 = t_begin + 1 + issued * F;
     const int nf = min(F, t_end - f0);
@@ -335,9 +344,13 @@ __global__ void __launch_bounds__(512, 1) trellis_fast_kernel(const FwdJob* __re
       if (p_round > 0 && !warp_wait_phase(&head->empty[p_stage], (p_round - 1) & 1u, abort, limit, lane)) break;
       issue_next();
     }
-    if (lane == 0)
-      for (int c = max(0, issued - P.stages); c < issued; ++c)
-        (void)wait_phase(&head->full[c % P.stages], (c / P.stages) & 1, abort, limit, false);
+    if (lane == 0) {
+      // Chunk x of the ring (counted over every job of this CTA) used stage
+      // x mod stages in round x / stages.
+      const int64_t next = static_cast<int64_t>(p_round) * P.stages + p_stage;
+      for (int64_t x = next - min(issued, P.stages); x < next; ++x)
+        (void)wait_phase(&head->full[x % P.stages], static_cast<uint32_t>(x / P.stages) & 1u, abort, limit, false);
+    }
   } else {
 
   // ---- per-lane constants: label columns and skip permissions ----
@@ -510,8 +523,8 @@ __global__ void __launch_bounds__(512, 1) trellis_fast_kernel(const FwdJob* __re
     const int nwin_all = nwin_full + (rem > 0 ? 1 : 0);
     uint64_t pf0 = 0ull, pf1 = 0ull;  // grid teams: window pf_m's words, loaded one window ahead
     int pf_m = -1;
-    int c_stage = 0;
-    uint32_t c_round = 0;
+    int& c_stage = ring.c_stage;
+    uint32_t& c_round = ring.c_round;
     const float* stage_f = reinterpret_cast<const float*>(stages);
     const int stage_floats = P.stage_bytes / 4;
 
@@ -691,6 +704,16 @@ __global__ void __launch_bounds__(512, 1) trellis_fast_kernel(const FwdJob* __re
         end_window(m, t_end - 1);
       }
     }
+    // Release the stage of the last window (a persistent CTA's next job
+    // continues the ring).
+    if (!dead && nwin_all > 0) {
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&head->empty[c_stage]);
+      if (++c_stage == P.stages) {
+        c_stage = 0;
+        ++c_round;
+      }
+    }
   } else {
   float carry_a = a[K - 1];  // alpha of the last state at the first frame of the next package
   int carry_A = A[K - 1];
@@ -698,9 +721,9 @@ __global__ void __launch_bounds__(512, 1) trellis_fast_kernel(const FwdJob* __re
 #pragma unroll
   for (int w = 0; w < NW; ++w) bits[w] = 0u;
   auto end_window = [&](const int m, const int t_last) { end_window_bits(bits, m, t_last); };
-  int c_stage = 0;
-  uint32_t c_round = 0;
-  int chunk = -1;  // chunk whose stage is in use
+  int& c_stage = ring.c_stage;
+  uint32_t& c_round = ring.c_round;
+  int chunk = -1;  // chunk of this job whose stage is in use
   const float* stage_f = reinterpret_cast<const float*>(stages);
   const int stage_floats = P.stage_bytes / 4;
 
@@ -869,6 +892,14 @@ __global__ void __launch_bounds__(512, 1) trellis_fast_kernel(const FwdJob* __re
     if (!dead && iw0 < rem) dead = !run_block(kPartBlock, nwin_full, iw0, rem - iw0);
     if (!dead) end_window(nwin_full, t_end - 1);
   }
+  if (!dead && chunk >= 0) {  // release the last chunk's stage
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&head->empty[c_stage]);
+    if (++c_stage == P.stages) {
+      c_stage = 0;
+      ++c_round;
+    }
+  }
   }
   // ---- alpha_{T-1} of the two final states ----
   if (!dead && *abort == 0 && t_end == J.T && J.final2 != nullptr) {
@@ -886,18 +917,20 @@ __global__ void __launch_bounds__(512, 1) trellis_fast_kernel(const FwdJob* __re
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0 && *abort != 0) atomicExch(J.status, kStTimeout);
-    if constexpr (kGrid) {
-      team_barrier(xbar, ncta, abort, limit);
-      if (*abort != 0) {
-        if (threadIdx.x == 0) atomicExch(J.status, kStTimeout);
-        return false;
+    if (ncta > 1) {
+      if constexpr (kGrid) {
+        team_barrier(xbar, ncta, abort, limit);
+        if (*abort != 0) {
+          if (threadIdx.x == 0) atomicExch(J.status, kStTimeout);
+          return false;
+        }
+      } else {
+        cluster_sync();
       }
-    } else if (ncta > 1) {
-      cluster_sync();
-    } else {
-      __syncthreads();
     }
-    return *reinterpret_cast<const volatile int32_t*>(J.status) != kStTimeout;
+    // One decision for the whole CTA (another CTA of the team may mark the
+    // request timed out while this one reads the status).
+    return __syncthreads_or(*reinterpret_cast<const volatile int32_t*>(J.status) == kStTimeout) == 0;
   };
   if (!team_sync_ok()) return;
 
@@ -1031,6 +1064,63 @@ __global__ void __launch_bounds__(512, 1) trellis_fast_kernel(const FwdJob* __re
   }
 }
 
+// Stage barriers of the emission ring: `full` completes when a stage's rows
+// have landed (one arrival with the byte count for bulk copies, 32 for the
+// per-float fallback), `empty` when every compute warp released it.
+__device__ __forceinline__ void init_stage_barriers(const FwdParams& P, bool bulk) {
+  SmemHead* head = reinterpret_cast<SmemHead*>(fast_smem());
+  if (threadIdx.x == 0) {
+    for (int st = 0; st < P.stages; ++st) {
+      mbar_init(&head->full[st], bulk ? 1u : 32u);
+      mbar_init(&head->empty[st], static_cast<uint32_t>((blockDim.x >> 5) - 1));
+    }
+    fence_barrier_init();
+  }
+  __syncthreads();
+}
+
+// One team per job: a thread-block cluster (or one CTA), or a grid team of
+// P.grid_ctas consecutive CTAs of a cooperative launch.
+template <int K, int kB, bool kGrid, bool kNorm>
+__global__ void __launch_bounds__(512, 1) trellis_fast_kernel(const FwdJob* __restrict__ jobs, const FwdParams P) {
+  const uint32_t ncta = kGrid ? static_cast<uint32_t>(max(P.grid_ctas, 1)) : cluster_nctarank();
+  const uint32_t crank = kGrid ? blockIdx.x % ncta : cluster_ctarank();
+  const FwdJob& J = jobs[blockIdx.x / ncta];
+  init_stage_barriers(P, (J.flags & kJobBulkRows) != 0);
+  StageRing ring;
+  team_job<K, kB, kGrid, kNorm>(J, P, ncta, crank, ring);
+}
+
+// Persistent launch: every CTA of a cooperative launch (all resident) takes
+// seats from a counter in order. Seat x belongs to job seat_job[x] (jobs
+// ordered longest first, each with team_ctas consecutive seats from
+// first_seat); a job of several CTAs links them through global memory as a
+// grid team does. Seats are handed out in order and every CTA is resident,
+// so each team fills: the CTAs of earlier jobs finish and take later seats.
+template <int K, int kB, bool kNorm>
+__global__ void __launch_bounds__(512, 1) trellis_persist_kernel(const FwdJob* __restrict__ jobs, const FwdParams P,
+                                                                 const int32_t* __restrict__ seat_job,
+                                                                 int32_t total_seats, int32_t* counter) {
+  SmemHead* head = reinterpret_cast<SmemHead*>(fast_smem());
+  init_stage_barriers(P, true);  // every job of a persistent launch has 16-byte rows
+  StageRing ring;
+  for (;;) {
+    if (threadIdx.x == 0) head->unused = static_cast<uint32_t>(atomicAdd(counter, 1));
+    __syncthreads();
+    const int seat = static_cast<int>(head->unused);
+    __syncthreads();
+    if (seat >= total_seats) break;
+    const FwdJob& J = jobs[seat_job[seat]];
+    team_job<K, kB, true, kNorm>(J, P, static_cast<uint32_t>(J.team_ctas), static_cast<uint32_t>(seat - J.first_seat),
+                                 ring);
+    // The backtrack used the links and stages as scratch: the next job's
+    // bulk copies write there.
+    fence_proxy_async_smem();
+    __syncthreads();
+    if (*reinterpret_cast<volatile int32_t*>(&head->abort) != 0) break;  // the ring's phases are not trusted after a wait ran out
+  }
+}
+
 template <int K, int kB, bool kGrid, bool kNorm>
 cudaError_t launch_fast_k(const LaunchShape& shape, const FwdParams& p, const FwdJob* d_jobs, int njobs,
                           cudaStream_t stream) {
@@ -1084,7 +1174,68 @@ cudaError_t launch_fast_kb(const LaunchShape& shape, const FwdParams& p, const F
   return launch_fast_k<K, kB, false, false>(shape, p, d_jobs, njobs, s);
 }
 
+template <int K, int kB>
+cudaError_t persist_fn(void (**fn)(const FwdJob*, FwdParams, const int32_t*, int32_t, int32_t*)) {
+  *fn = trellis_persist_kernel<K, kB, false>;
+  return cudaSuccess;
+}
+
+cudaError_t persist_kernel_of(const LaunchShape& shape, const FwdParams& p,
+                              void (**fn)(const FwdJob*, FwdParams, const int32_t*, int32_t, int32_t*)) {
+  if (shape.norm || shape.sum) return cudaErrorInvalidValue;  // persistent launches align log-probabilities
+  if (shape.K == 2 && p.kb == kAnchorD) return persist_fn<2, kAnchorD>(fn);
+  if (shape.K == 2 && p.kb == 4) return persist_fn<2, 4>(fn);
+  if (shape.K == 4 && p.kb == kAnchorD) return persist_fn<4, kAnchorD>(fn);
+  if (shape.K == 4 && p.kb == 4) return persist_fn<4, 4>(fn);
+  return cudaErrorInvalidValue;
+}
+
 }  // namespace
+
+int persist_max_ctas(const LaunchShape& shape, const FwdParams& p, int device, int* ctas) {
+  void (*fn)(const FwdJob*, FwdParams, const int32_t*, int32_t, int32_t*) = nullptr;
+  cudaError_t e = persist_kernel_of(shape, p, &fn);
+  if (e != cudaSuccess) return e;
+  const int smem_max = max_smem_optin(device);
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0, sms = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, (shape.warps + 1) * 32,
+                                                    static_cast<size_t>(smem_bytes(shape, p)));
+  if (e != cudaSuccess) return e;
+  e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+  if (e != cudaSuccess) return e;
+  *ctas = per_sm * sms;
+  return cudaSuccess;
+}
+
+int launch_trellis_persist(const LaunchShape& shape, const FwdParams& p, const FwdJob* d_jobs,
+                           const int32_t* d_seat_job, int32_t total_seats, int32_t* d_counter, int ctas,
+                           void* stream) {
+  if (total_seats <= 0) return cudaSuccess;
+  void (*fn)(const FwdJob*, FwdParams, const int32_t*, int32_t, int32_t*) = nullptr;
+  cudaError_t e = persist_kernel_of(shape, p, &fn);
+  if (e != cudaSuccess) return e;
+  int dev = 0;
+  e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const int smem_max = max_smem_optin(dev);
+  const int smem = smem_bytes(shape, p);
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max);
+  if (e != cudaSuccess) return e;
+  if (smem > smem_max || ctas < 1) return cudaErrorInvalidValue;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(static_cast<unsigned>(std::min(ctas, static_cast<int>(total_seats))), 1, 1);
+  cfg.blockDim = dim3(static_cast<unsigned>((shape.warps + 1) * 32), 1, 1);  // + the producer warp
+  cfg.dynamicSmemBytes = static_cast<size_t>(smem);
+  cfg.stream = static_cast<cudaStream_t>(stream);
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;  // every CTA resident: teams fill (see the kernel)
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, fn, d_jobs, p, d_seat_job, total_seats, d_counter);
+}
 
 int launch_trellis_fast(const LaunchShape& shape, const FwdParams& p, const FwdJob* d_jobs, int njobs,
                         void* stream) {
