@@ -212,14 +212,14 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def serving_run(align, serve, synth, autotune, dev: int, n: int, warmup: int) -> dict:
+def serving_run(align, serve, synth, autotune, dev: int, n: int, warmup: int, persistent: bool = False) -> dict:
     """Workload 5: Poisson arrivals served by the continuous-batching loop with a
     16 GiB backpointer budget. Saturation = every request arriving at time 0;
     then offered loads of 0.5, 0.8 and 0.95 times the saturation request rate.
     Each run serves `warmup` + `n` requests of the stream; the first `warmup`
     (by arrival) are excluded from its statistics."""
     b = synth.make_batch(synth.specs(5, n=n + warmup), device=f"cuda:{dev}")
-    al = align.Aligner(device=dev, batched=True, bp_budget_bytes=16 << 30)
+    al = align.Aligner(device=dev, batched=True, bp_budget_bytes=16 << 30, persistent=persistent)
     autotune.apply(al)
     try:
         warm = serve.poisson_requests(b, rate_per_s=1e9, seed=1)
@@ -233,6 +233,7 @@ def serving_run(align, serve, synth, autotune, dev: int, n: int, warmup: int) ->
             reqs = serve.poisson_requests(b, rate_per_s=frac * rate_sat, seed=int(frac * 100))
             st = serve.serve(al, reqs, warmup=warmup)
             out["loads"][str(frac)] = {**st.as_dict(), "offered_requests_per_s": frac * rate_sat}
+        out["persistent_batches"] = al.stats()["persistent_batches"]
         return out
     finally:
         al.close()
@@ -360,7 +361,7 @@ def roofline_of(batch, ms: float, t_frame_ns: float, peaks: dict, sm_count: int)
 
 
 def run_batched(torch, align, autotune, replicas, batch, dev, stream, flush_buf, steps, warmup, dist, clocks=None,
-                force_checkpoint=False):
+                force_checkpoint=False, persistent=False):
     """Device-timed packed-batch steps of one workload. Returns the step
     times, kernel launches per step, enqueue times and the aligner's budget."""
     n = len(batch)
@@ -373,7 +374,7 @@ def run_batched(torch, align, autotune, replicas, batch, dev, stream, flush_buf,
                                 budget=1 << 40)["backpointer_bytes"] for i in range(n))
     budget = max(4 << 30, int(1.2 * need) + (256 << 20))
     al = align.Aligner(device=dev, batched=True, stream=stream, bp_budget_bytes=budget,
-                       max_inflight=max(8192, 2 * n), force_checkpoint=force_checkpoint)
+                       max_inflight=max(8192, 2 * n), force_checkpoint=force_checkpoint, persistent=persistent)
     tuned = autotune.apply(al)
     timer = DeviceTimer(torch, stream, flush_buf)
 
@@ -409,10 +410,11 @@ def run_batched(torch, align, autotune, replicas, batch, dev, stream, flush_buf,
     launches = (st1["kernel_launches"] - st0["kernel_launches"]) // max(steps, 1)
     tp = (st1["throughput_batches"] - st0["throughput_batches"]) / max(steps, 1)
     ck = (st1["checkpointed"] - st0["checkpointed"]) / max(steps, 1)
+    pb = (st1["persistent_batches"] - st0["persistent_batches"]) / max(steps, 1)
     ms = replicas.slowest(statistics.mean(times), dist, dev)
     return {"times": times, "ms": ms, "launches": int(launches), "tp_batches": tp, "tuned": tuned,
             "enqueue_ms_median": 1e3 * statistics.median(timer.enqueue), "budget": budget, "out": out,
-            "checkpointed_per_step": ck}
+            "checkpointed_per_step": ck, "persistent_batches_per_step": pb}
 
 
 def run_e2e(torch, align, autotune, replicas, batch, dev, budget, steps, dist, world):
@@ -756,23 +758,31 @@ def main():
     if not args.no_serving and args.workload == "batch64":
         from paper_2310_17864_gb300 import serve
         serving = serving_run(align, serve, synth, autotune, dev, args.serving_requests, args.serving_warmup)
+        # The same streams with ALIGN_F_PERSISTENT: every tick's batch as one
+        # persistent launch.
+        serving["with_persistent_launch"] = serving_run(align, serve, synth, autotune, dev, args.serving_requests,
+                                                        args.serving_warmup, persistent=True)
     al.close()
 
     # The other single-GPU workloads, each with its own roofline (legs).
     legs = None
     if not args.no_legs:
         legs = {}
-        # (leg, workload, forced checkpointed recompute)
-        for name, wname, ck in (("longform", "longform", False), ("longform_checkpointed", "longform", True),
-                                ("ragged32", "ragged32", False), ("ragged500", "ragged500", False)):
-            if wname == args.workload and not ck:
+        # (leg, workload, forced checkpointed recompute, persistent launch)
+        for name, wname, ck, ps in (("longform", "longform", False, False),
+                                    ("longform_checkpointed", "longform", True, False),
+                                    ("ragged32", "ragged32", False, False),
+                                    ("ragged32_persistent", "ragged32", False, True),
+                                    ("ragged500", "ragged500", False, False),
+                                    ("batch64_persistent", "batch64", False, True)):
+            if wname == args.workload and not ck and not ps:
                 continue
             lw = WORKLOADS[wname]
             lb = make_workload_batch(lw, f"cuda:{dev}")
             lclk = Clocks(dev)
             r = run_batched(torch, align, autotune, replicas, lb, dev, stream, flush_buf,
                             max(3, args.leg_steps // 2) if ck else args.leg_steps, max(3, args.warmup // 2), dist,
-                            clocks=lclk, force_checkpoint=ck)
+                            clocks=lclk, force_checkpoint=ck, persistent=ps)
             leg = {"metric": METRIC, "value": replicas.job_rate(lb.cells, world, r["ms"]), "unit": "cells/s",
                    "ms_per_step": r["ms"], "steps": len(r["times"]),
                    "p50_ms": float(np.percentile(r["times"], 50)), "p99_ms": float(np.percentile(r["times"], 99)),
@@ -783,6 +793,7 @@ def main():
                               "host_enqueue_ms_median": round(r["enqueue_ms_median"], 3),
                               "throughput_batches_per_step": r["tp_batches"],
                               "checkpointed_requests_per_step": r["checkpointed_per_step"],
+                              "persistent_batches_per_step": r["persistent_batches_per_step"],
                               "input_sha256": input_digest(lb.lp)},
                    "roofline": roofline_of(lb, r["ms"], t_frame_ns, peaks, sm_count),
                    "clocks": lclk.summary()}

@@ -14,6 +14,7 @@ All alignment work runs in the CUDA library; this module only schedules calls.
 from __future__ import annotations
 
 import dataclasses
+import gc
 import time
 
 import numpy as np
@@ -47,11 +48,12 @@ class ServeStats:
     p50_ms: float
     p99_ms: float
     max_inflight: int
+    max_tick_ms: float = 0.0   # longest iteration of the loop (a host stall shows here)
 
     def as_dict(self) -> dict:
         return {"requests": self.n, "makespan_s": self.makespan_s, "cells": self.cells,
                 "cells_per_s": self.cells_per_s, "p50_ms": self.p50_ms, "p99_ms": self.p99_ms,
-                "max_inflight": self.max_inflight}
+                "max_inflight": self.max_inflight, "max_tick_ms": self.max_tick_ms}
 
 
 def _alloc_out(torch, T: int, device):
@@ -60,12 +62,28 @@ def _alloc_out(torch, T: int, device):
 
 
 def serve(aligner: align.Aligner, requests: list[Request], *, tick_s: float = 0.0, clock=time.perf_counter,
-          warmup: int = 0) -> ServeStats:
+          warmup: int = 0, freeze_gc: bool = True) -> ServeStats:
     """Run the arrival schedule to completion. ``aligner`` must be in batched mode.
     Arrival times are relative to the start of the run. The first ``warmup``
-    requests are served but excluded from the statistics."""
+    requests are served but excluded from the statistics.
+
+    freeze_gc: move every object that exists when the loop starts to the
+    collector's permanent generation for the duration of the run, so that a
+    full collection (which otherwise scans every object of the process, e.g.
+    all of torch's, for tens of milliseconds) does not stall the loop."""
     import torch
 
+    if freeze_gc:
+        gc.freeze()
+    try:
+        return _serve(aligner, requests, tick_s, clock, warmup, torch)
+    finally:
+        if freeze_gc:
+            gc.unfreeze()
+
+
+def _serve(aligner, requests, tick_s, clock, warmup, torch) -> ServeStats:
+    """The loop of serve()."""
     order = sorted(range(len(requests)), key=lambda i: requests[i].arrival_s)
     for r in requests:
         if r.out is None:
@@ -74,8 +92,12 @@ def serve(aligner: align.Aligner, requests: list[Request], *, tick_s: float = 0.
     nxt = 0
     t0 = clock()
     max_inflight = 0
+    max_tick = 0.0
+    prev = 0.0
     while nxt < len(order) or pending:
         now = clock() - t0
+        max_tick = max(max_tick, now - prev)
+        prev = now
         arrived = []
         while nxt < len(order) and requests[order[nxt]].arrival_s <= now:
             arrived.append(requests[order[nxt]])
@@ -116,7 +138,7 @@ def serve(aligner: align.Aligner, requests: list[Request], *, tick_s: float = 0.
     span = max(t_last - t_first, 1e-9)
     return ServeStats(n=len(kept), makespan_s=span, cells=cells, cells_per_s=cells / span, latency_ms=lat,
                       p50_ms=float(np.percentile(lat, 50)), p99_ms=float(np.percentile(lat, 99)),
-                      max_inflight=max_inflight)
+                      max_inflight=max_inflight, max_tick_ms=1e3 * max_tick)
 
 
 def poisson_requests(batch, rate_per_s: float, seed: int) -> list[Request]:
