@@ -80,6 +80,8 @@ def parse():
     ap.add_argument("--no-legs", action="store_true", help="skip the long-form and ragged legs")
     ap.add_argument("--leg-steps", type=int, default=10, help="timed steps of each leg")
     ap.add_argument("--profile", action="store_true", help="only warm-up + steps batches, for profilers")
+    ap.add_argument("--profile-utts", type=int, default=0, metavar="N",
+                    help="with --profile: only the workload's first N utterances (a small capture)")
     ap.add_argument("--profile-beam", type=int, default=0, metavar="N",
                     help="only warm-up + steps decoder calls on a batch of N utterances, for profilers")
     return ap.parse_args()
@@ -239,9 +241,10 @@ def serving_run(align, serve, synth, autotune, dev: int, n: int, warmup: int, pe
         al.close()
 
 
-def make_workload_batch(wl, device: str):
+def make_workload_batch(wl, device: str, n: int | None = None):
+    """The workload's synthetic batch (its first n utterances if n is given)."""
     from paper_2310_17864_gb300 import synth
-    return synth.make_batch(synth.specs(wl["cfg"], C=wl["C"]), device=device)
+    return synth.make_batch(synth.specs(wl["cfg"], C=wl["C"], n=n), device=device)
 
 
 def packed_targets(batch):
@@ -518,7 +521,7 @@ def main():
                           "kept_frames": int(r.kept.sum().item()), "frames": int(off[-1])}))
         return
 
-    batch = make_workload_batch(wl, f"cuda:{dev}")
+    batch = make_workload_batch(wl, f"cuda:{dev}", n=(args.profile_utts or None) if args.profile else None)
     n = len(batch)
     cells = batch.cells
     C = int(batch.lp.shape[1])
