@@ -74,6 +74,13 @@ extern "C" {
                                          requests' seats from a device counter, longest first, with
                                          one kernel shape (the tuning table's for the batch's median
                                          S, K = 2 or 4); other batches launch per shape group */
+#define ALIGN_F_UPLOAD_DESCRIPTORS 0x80u /* always copy a batch's descriptors and targets to device
+                                         memory and its result codes back, as for batches that
+                                         use other kernels; by default a batch that runs only the
+                                         fast kernel (device inputs and outputs, full or grid-team
+                                         backpointers) has its kernels read them from the pinned
+                                         host image and write the result codes there, which saves
+                                         two copies per batch (needs native host atomics) */
 #define ALIGN_F_TEST_STALL 0x80000000u /* testing the device watchdog only: in every request whose
                                          trellis spans more than one warp, the first warp never
                                          hands its values on, so the next warp's bounded wait runs

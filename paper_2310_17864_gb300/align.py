@@ -40,6 +40,7 @@ ALIGN_F_NO_GRID_TEAMS = 0x8
 ALIGN_F_DEBUG_CHECKS = 0x10
 ALIGN_F_GENERIC_KERNEL = 0x20
 ALIGN_F_PERSISTENT = 0x40
+ALIGN_F_UPLOAD_DESCRIPTORS = 0x80
 ALIGN_F_TEST_STALL = 0x80000000
 
 # Every entry point declared in include/align.h.
@@ -451,7 +452,7 @@ class Aligner:
                  staging_bytes: int = 0, stream=None, force_checkpoint: bool = False,
                  wait_limit_ms: int = 0, max_inflight: int = 0, graphs: bool = True,
                  test_stall: bool = False, grid_teams: bool = True, debug_checks: bool = False,
-                 generic_kernel: bool = False, persistent: bool = False):
+                 generic_kernel: bool = False, persistent: bool = False, upload_descriptors: bool = False):
         import torch
         self.torch = torch
         self.device = device
@@ -462,6 +463,7 @@ class Aligner:
         flags |= ALIGN_F_DEBUG_CHECKS if debug_checks else 0
         flags |= ALIGN_F_GENERIC_KERNEL if generic_kernel else 0
         flags |= ALIGN_F_PERSISTENT if persistent else 0
+        flags |= ALIGN_F_UPLOAD_DESCRIPTORS if upload_descriptors else 0
         cfg = AlignConfig(device=device, max_inflight=max_inflight, bp_budget_bytes=bp_budget_bytes,
                           staging_bytes=staging_bytes,
                           cuda_stream=(stream.cuda_stream if stream is not None else None), flags=flags,

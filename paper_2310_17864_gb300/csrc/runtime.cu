@@ -201,6 +201,7 @@ struct align_ctx {
   char* d_stage = nullptr;
   Arena stage_arena;
   char* h_pinned = nullptr;
+  char* d_pinned = nullptr;  // device address of h_pinned (direct images), or nullptr
   Arena pinned_arena;
   int32_t* d_check = nullptr;  // ALIGN_F_DEBUG_CHECKS: result word of the emission scan
   int32_t* h_check = nullptr;
@@ -547,11 +548,17 @@ int launch_queued(align_ctx* ctx) {
   // copies have per-batch host addresses).
   bool any_host = false;
   for (auto* r : take) any_host = any_host || r->host_io;
+  // Direct image: when every launch is the fast kernel on device buffers,
+  // the kernels read the descriptors and targets from the pinned image (each
+  // CTA copies its descriptor to shared memory once) and update the result
+  // codes there: no upload or download copy, no graph.
+  bool direct = ctx->d_pinned != nullptr && !any_host;
+  for (auto* r : take) direct = direct && r->plan.shape.fast != 0;
   int gi = -1;
   bool need_capture = false;
   uint64_t up_copy = up_bytes;
   uint64_t off_meta_dl = off_status;
-  if (!(ctx->flags & ALIGN_F_NO_GRAPHS) && !any_host) {
+  if (!(ctx->flags & ALIGN_F_NO_GRAPHS) && !any_host && !direct) {
     uint64_t up_bucket = 64 << 10;
     while (up_bucket < up_bytes) up_bucket <<= 1;
     std::vector<int64_t> key{static_cast<int64_t>(take.size()), static_cast<int64_t>(up_bucket)};
@@ -624,6 +631,16 @@ int launch_queued(align_ctx* ctx) {
     b.graph = gi;
     h = ctx->h_pinned + ge.pinned.off;
     d = ctx->d_meta + ge.meta.off;
+  } else if (direct) {
+    if (!ctx->pinned_arena.alloc(up_bytes, &b.pinned.off)) {
+      unwind();
+      return ALIGN_OK;  // retried after other batches release their images
+    }
+    b.pinned.bytes = up_bytes;
+    b.pinned.live = true;
+    h = ctx->h_pinned + b.pinned.off;
+    d = ctx->d_pinned + b.pinned.off;
+    off_meta_dl = off_metas;  // the result codes are read where the kernels write them
   } else {
     if (!ctx->meta_arena.alloc(up_bytes, &b.meta.off)) {
       unwind();
@@ -869,7 +886,7 @@ int launch_queued(align_ctx* ctx) {
   // Everything from the descriptor upload to the status download; issued
   // directly, or captured once into the batch graph.
   auto body = [&]() -> int {
-  CU(cudaMemcpyAsync(d, h, up_copy, cudaMemcpyHostToDevice, s0));
+  if (!direct) CU(cudaMemcpyAsync(d, h, up_copy, cudaMemcpyHostToDevice, s0));
   for (size_t i = 0; i < take.size(); ++i) {
     Request& r = *take[i];
     if (r.host_io && !r.lp_alias) {
@@ -941,7 +958,7 @@ int launch_queued(align_ctx* ctx) {
     CU(cudaStreamWaitEvent(s0, j, 0));
   }
   if (!split_copies && copy_range(dd2h, 0, id2h, s0) != ALIGN_OK) return ALIGN_E_CUDA;
-  CU(cudaMemcpyAsync(b.h_meta, dmeta, take.size() * sizeof(MetaBlock), cudaMemcpyDeviceToHost, s0));
+  if (!direct) CU(cudaMemcpyAsync(b.h_meta, dmeta, take.size() * sizeof(MetaBlock), cudaMemcpyDeviceToHost, s0));
 
   for (size_t i = 0; i < take.size(); ++i) {
     Request& r = *take[i];
@@ -1032,9 +1049,15 @@ int launch_persistent(align_ctx* ctx, std::vector<Request*>& take) {
   const uint64_t off_metas = round_up(n * sizeof(FwdJob), kAlign);
   const uint64_t off_tgts = round_up(off_metas + n * sizeof(MetaBlock), kAlign);
   const uint64_t off_seats = round_up(off_tgts + tgt_words * 4, kAlign);
-  const uint64_t off_counter = round_up(off_seats + static_cast<uint64_t>(total_seats) * 4, kAlign);
-  const uint64_t up_bytes = round_up(off_counter + 16, kAlign);
-  const uint64_t pin_bytes = up_bytes + round_up(n * sizeof(MetaBlock), kAlign);
+  const uint64_t up_bytes = round_up(off_seats + static_cast<uint64_t>(total_seats) * 4, kAlign);
+  // Direct image (as for shape-group batches): the kernel reads the
+  // descriptors, targets and seat table from the pinned image and writes the
+  // result codes there. Otherwise the image is uploaded and the codes copied back.
+  const bool direct = ctx->d_pinned != nullptr;
+  const uint64_t pin_bytes = direct ? up_bytes : up_bytes + round_up(n * sizeof(MetaBlock), kAlign);
+  // Device region zeroed before the launch: the teams' CTA links, then the seat counter.
+  const uint64_t off_counter = round_up(x_bytes, kAlign);
+  const uint64_t dev_bytes = off_counter + kAlign;
 
   Batch b;
   b.id = ctx->next_batch++;
@@ -1049,28 +1072,27 @@ int launch_persistent(align_ctx* ctx, std::vector<Request*>& take) {
     }
     return ALIGN_OK;  // retried after other batches release memory
   };
-  if (!ctx->meta_arena.alloc(up_bytes, &b.meta.off)) return unwind();
-  b.meta.bytes = up_bytes;
-  b.meta.live = true;
+  if (!direct) {
+    if (!ctx->meta_arena.alloc(up_bytes, &b.meta.off)) return unwind();
+    b.meta.bytes = up_bytes;
+    b.meta.live = true;
+  }
   if (!ctx->pinned_arena.alloc(pin_bytes, &b.pinned.off)) return unwind();
   b.pinned.bytes = pin_bytes;
   b.pinned.live = true;
-  if (x_bytes) {
-    if (!ctx->bp_arena.alloc(x_bytes, &b.xlink.off)) return unwind();
-    b.xlink.bytes = x_bytes;
-    b.xlink.live = true;
-  }
+  if (!ctx->bp_arena.alloc(dev_bytes, &b.xlink.off)) return unwind();
+  b.xlink.bytes = dev_bytes;
+  b.xlink.live = true;
   char* h = ctx->h_pinned + b.pinned.off;
-  char* d = ctx->d_meta + b.meta.off;
+  char* d = direct ? ctx->d_pinned + b.pinned.off : ctx->d_meta + b.meta.off;
   FwdJob* hjobs = reinterpret_cast<FwdJob*>(h + off_jobs);
   MetaBlock* hmeta = reinterpret_cast<MetaBlock*>(h + off_metas);
   int32_t* htgt = reinterpret_cast<int32_t*>(h + off_tgts);
   int32_t* hseat = reinterpret_cast<int32_t*>(h + off_seats);
   MetaBlock* dmeta = reinterpret_cast<MetaBlock*>(d + off_metas);
   const int32_t* dtgt = reinterpret_cast<const int32_t*>(d + off_tgts);
-  b.h_meta = reinterpret_cast<MetaBlock*>(h + up_bytes);
-  std::memset(h + off_counter, 0, 16);
-  char* d_x = x_bytes ? ctx->d_bp + b.xlink.off : nullptr;
+  b.h_meta = reinterpret_cast<MetaBlock*>(direct ? h + off_metas : h + up_bytes);
+  char* d_x = ctx->d_bp + b.xlink.off;
   uint64_t tw = 0;
   int32_t seat = 0;
   for (size_t i = 0; i < n; ++i) {
@@ -1130,18 +1152,18 @@ int launch_persistent(align_ctx* ctx, std::vector<Request*>& take) {
   cudaEvent_t fork = ctx->fork_events[static_cast<size_t>(b.id) % ctx->fork_events.size()];
   CU(cudaEventRecord(fork, ctx->main));
   CU(cudaStreamWaitEvent(s0, fork, 0));
-  CU(cudaMemcpyAsync(d, h, up_bytes, cudaMemcpyHostToDevice, s0));
-  if (x_bytes) CU(cudaMemsetAsync(d_x, 0, x_bytes, s0));
+  if (!direct) CU(cudaMemcpyAsync(d, h, up_bytes, cudaMemcpyHostToDevice, s0));
+  CU(cudaMemsetAsync(d_x, 0, dev_bytes, s0));
   const int ctas = persist_ctas(ctx, shape, C, F);
   const cudaError_t e = static_cast<cudaError_t>(
       launch_trellis_persist(shape, P, reinterpret_cast<const FwdJob*>(d + off_jobs),
                              reinterpret_cast<const int32_t*>(d + off_seats), static_cast<int32_t>(total_seats),
-                             reinterpret_cast<int32_t*>(d + off_counter), ctas, s0));
+                             reinterpret_cast<int32_t*>(d_x + off_counter), ctas, s0));
   if (e != cudaSuccess) {
     set_error("launch_trellis_persist", e);
     return ALIGN_E_CUDA;
   }
-  CU(cudaMemcpyAsync(b.h_meta, dmeta, n * sizeof(MetaBlock), cudaMemcpyDeviceToHost, s0));
+  if (!direct) CU(cudaMemcpyAsync(b.h_meta, dmeta, n * sizeof(MetaBlock), cudaMemcpyDeviceToHost, s0));
   ctx->stats.kernel_launches += 1;
   ctx->stats.persistent_batches++;
   ctx->stats.bp_bytes_peak = std::max(ctx->stats.bp_bytes_peak, ctx->bp_arena.peak());
@@ -1283,6 +1305,17 @@ int align_create(align_ctx** out, const align_config* cfg_in) {
     return ALIGN_E_NOMEM;
   }
   ctx->pinned_arena.init(pin_bytes);
+  {
+    // Direct images: kernels read a batch's descriptors from the pinned
+    // arena and update its result codes there (atomics on host memory).
+    void* alias = nullptr;
+    int host_atomics = 0;
+    if (!(cfg.flags & ALIGN_F_UPLOAD_DESCRIPTORS) &&
+        cudaDeviceGetAttribute(&host_atomics, cudaDevAttrHostNativeAtomicSupported, cfg.device) == cudaSuccess &&
+        host_atomics && cudaHostGetDevicePointer(&alias, ctx->h_pinned, 0) == cudaSuccess)
+      ctx->d_pinned = static_cast<char*>(alias);
+    (void)cudaGetLastError();
+  }
   if (cudaMalloc(&ctx->d_check, 256) != cudaSuccess || cudaMallocHost(&ctx->h_check, 256) != cudaSuccess) {
     cudaFree(ctx->d_bp);
     cudaFree(ctx->d_meta);

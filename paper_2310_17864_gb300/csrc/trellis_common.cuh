@@ -126,6 +126,7 @@ struct SmemHead {
   int32_t abort;            // set by any thread of this CTA whose wait hit the limit
   uint32_t unused;
   uint64_t sink;            // scratch slot written by the last warp of the team
+  FwdJob job;               // fast kernel: this CTA's copy of its job descriptor
 };
 static_assert(sizeof(SmemHead) % 16 == 0, "head size: what follows it is 16-byte aligned");
 

@@ -1085,10 +1085,19 @@ template <int K, int kB, bool kGrid, bool kNorm>
 __global__ void __launch_bounds__(512, 1) trellis_fast_kernel(const FwdJob* __restrict__ jobs, const FwdParams P) {
   const uint32_t ncta = kGrid ? static_cast<uint32_t>(max(P.grid_ctas, 1)) : cluster_nctarank();
   const uint32_t crank = kGrid ? blockIdx.x % ncta : cluster_ctarank();
-  const FwdJob& J = jobs[blockIdx.x / ncta];
-  init_stage_barriers(P, (J.flags & kJobBulkRows) != 0);
+  // The descriptor is read once into shared memory (it may live in pinned
+  // host memory, where every field access would cross the chip link).
+  FwdJob& sjob = reinterpret_cast<SmemHead*>(fast_smem())->job;
+  static_assert(sizeof(FwdJob) % 16 == 0, "descriptor copied in 16-byte words");
+  {
+    const uint4* src = reinterpret_cast<const uint4*>(jobs + blockIdx.x / ncta);
+    uint4* dst = reinterpret_cast<uint4*>(&sjob);
+    for (int i = threadIdx.x; i < static_cast<int>(sizeof(FwdJob) / 16); i += blockDim.x) dst[i] = src[i];
+  }
+  __syncthreads();
+  init_stage_barriers(P, (sjob.flags & kJobBulkRows) != 0);
   StageRing ring;
-  team_job<K, kB, kGrid, kNorm>(J, P, ncta, crank, ring);
+  team_job<K, kB, kGrid, kNorm>(sjob, P, ncta, crank, ring);
 }
 
 // Persistent launch: every CTA of a cooperative launch (all resident) takes
@@ -1108,9 +1117,16 @@ __global__ void __launch_bounds__(512, 1) trellis_persist_kernel(const FwdJob* _
     if (threadIdx.x == 0) head->unused = static_cast<uint32_t>(atomicAdd(counter, 1));
     __syncthreads();
     const int seat = static_cast<int>(head->unused);
+    if (seat >= total_seats) break;  // the same seat in every thread
+    // The seat's descriptor into shared memory (the table and descriptors may
+    // live in pinned host memory).
+    {
+      const uint4* src = reinterpret_cast<const uint4*>(jobs + seat_job[seat]);
+      uint4* dst = reinterpret_cast<uint4*>(&head->job);
+      for (int i = threadIdx.x; i < static_cast<int>(sizeof(FwdJob) / 16); i += blockDim.x) dst[i] = src[i];
+    }
     __syncthreads();
-    if (seat >= total_seats) break;
-    const FwdJob& J = jobs[seat_job[seat]];
+    const FwdJob& J = head->job;
     team_job<K, kB, true, kNorm>(J, P, static_cast<uint32_t>(J.team_ctas), static_cast<uint32_t>(seat - J.first_seat),
                                  ring);
     // The backtrack used the links and stages as scratch: the next job's

@@ -512,14 +512,15 @@ def test_grid_team_watchdog():
 
 
 def test_graph_replay_equals_direct_launch():
-    """A batch with the same launch structure is captured once and replayed;
-    results equal direct launches bit for bit."""
+    """A batch with the same launch structure (descriptors uploaded to the
+    device) is captured once and replayed; results equal direct launches of
+    a batch whose kernels read the pinned descriptor image, bit for bit."""
     build.build()
     specs = synth.specs(2)[:20]
     b = synth.make_batch(specs, device="cuda")
     outs = lambda: [(torch.empty(s.T, dtype=torch.int32, device="cuda"), torch.empty(s.T, device="cuda"),
                      torch.empty(1, device="cuda"), torch.empty(s.T, dtype=torch.int32, device="cuda")) for s in specs]
-    g = align.Aligner(device=0, batched=True)
+    g = align.Aligner(device=0, batched=True, upload_descriptors=True)
     d = align.Aligner(device=0, batched=True, graphs=False)
     try:
         ref = d.submit_batch([(b.utt(i), b.targets[i], 0, o) for i, o in enumerate(outs())])
