@@ -43,8 +43,8 @@ constexpr int kMaxStages = 16;        // emission ring stages per CTA, at most (
 constexpr int kLead = 4;              // stages in flight ahead of the consumer
 constexpr int kBtWindow = 32;         // frames per backtrack window
 constexpr int kAnchorD = 32;          // frames between anchor rows (== kBtWindow)
-constexpr int kHopBatch = 16;         // anchor rows fetched per batch while hopping back
-constexpr int kHopSpan = 320;         // states below the current one staged per anchor row
+constexpr int kHopBatch = 32;         // anchor rows fetched per batch while hopping back
+constexpr int kHopSpan = 640;         // states below the current one staged per anchor row
 constexpr int kHopRowBytes = (kHopSpan + 32 + 15) / 16 * 16;  // staged bytes per row (16-aligned range)
 constexpr int kTagBits = 24;          // frame tag bits in a ring word
 

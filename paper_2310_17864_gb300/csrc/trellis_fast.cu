@@ -244,7 +244,6 @@ __device__ __forceinline__ void team_job(const FwdJob& J, const FwdParams& P, co
   static_assert(K == 2 || K == 4, "fast kernel: K = 2 or 4");
   static_assert(kB == 4 || kB == 8 || kB == kAnchorD, "fast kernel: blocks of 4 or 8 frames, or whole windows");
   constexpr int NW = bp_words(K);
-  constexpr int GS = 32 * K;
   constexpr int kWin = kAnchorD;
   unsigned char* const smem = fast_smem();
   SmemHead* head = reinterpret_cast<SmemHead*>(smem);
@@ -960,9 +959,9 @@ __device__ __forceinline__ void team_job(const FwdJob& J, const FwdParams& P, co
         const int lo = max(0, s_cur - kHopSpan) & ~15;
         const int hi = min(zstride, (s_cur + 16) & ~15);
         const int nchunk = (hi - lo) / 16;
-        if (lane < nchunk) {
+        for (int c = lane; c < nchunk; c += 32) {  // lane c copies bytes [lo + 16c, lo + 16c + 16) of each row
           for (int r = 0; r < nb; ++r)
-            cp_async16(zb + r * kHopRowBytes + lane * 16, ztab + static_cast<size_t>(m - r) * zstride + lo + lane * 16);
+            cp_async16(zb + r * kHopRowBytes + c * 16, ztab + static_cast<size_t>(m - r) * zstride + lo + c * 16);
         }
         cp_async_wait_all();
         __syncwarp();
@@ -987,27 +986,35 @@ __device__ __forceinline__ void team_job(const FwdJob& J, const FwdParams& P, co
   // ---- tail 2 (every lane of the team): walk the windows in parallel ----
   // Window m covers frames (b, e], b = t_begin + 32m, e = min(b + 32, t_end - 1);
   // its top state is path[e]. The words of a state hold all 32 frames of the
-  // window, so a walk reloads them only when the state changes.
+  // window, and the NW words of a lane hold its K states, so a walk loads a
+  // lane's words together (independent loads, one round trip) and reloads
+  // only when the path leaves that lane's states.
   const int nwalk = max(nwin, 1);
   for (int m = g * 32 + lane; !producer && m < nwalk; m += G * 32) {
     const int b = t_begin + m * kAnchorD;
     const int e = (nwin == 0) ? t_begin : min(b + kAnchorD, t_end - 1);
     const uint32_t* wbase = bp + static_cast<size_t>(m) * G * NW * 32;
     int sc = path[e];
-    int cur = -1;
-    uint32_t aw = 0u, sw = 0u;
+    int cur = -1;  // lane (over the team) whose words are in wv
+    uint32_t wv[NW];
+#pragma unroll
+    for (int q = 0; q < NW; ++q) wv[q] = 0u;
     for (int f = e; f > b; --f) {
       path[f] = sc;
-      if (sc != cur) {
-        cur = sc;
-        const int gs = sc / GS;
-        const int r = sc - gs * GS;
-        const int ln = r / K;
-        const int j = r - ln * K;
-        const uint32_t* w = wbase + static_cast<size_t>(gs) * NW * 32 + ln;
-        aw = w[j * 32];
-        sw = (j & 1) ? w[(K + (j >> 1)) * 32] : 0u;
+      const int lg = sc / K;
+      if (lg != cur) {
+        cur = lg;
+        const int gs = lg / 32;
+        const uint32_t* w = wbase + static_cast<size_t>(gs) * NW * 32 + (lg - gs * 32);
+#pragma unroll
+        for (int q = 0; q < NW; ++q) wv[q] = w[q * 32];
       }
+      const int j = sc - lg * K;
+      uint32_t aw = wv[0], sw = 0u;
+#pragma unroll
+      for (int q = 1; q < K; ++q) aw = (j == q) ? wv[q] : aw;
+#pragma unroll
+      for (int q = 0; q < K / 2; ++q) sw = (j == 2 * q + 1) ? wv[K + q] : sw;
       const int i = f - b - 1;
       sc -= ((sw >> i) & 1u) ? 2 : static_cast<int>((aw >> i) & 1u);
     }

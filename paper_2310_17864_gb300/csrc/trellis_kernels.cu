@@ -708,8 +708,8 @@ __global__ void __launch_bounds__(512, (kOcc && K <= 4) ? 2 : 1)
     }
     if (chase) {
       if (lane == 0) path[t_end - 1] = s_cur;
-      // Batches of kHopBatch rows: lane q copies bytes [lo + 16q, lo + 16q + 16)
-      // of every row into shared memory (asynchronous copies, one wait), the
+      // Batches of kHopBatch rows: lane q copies bytes [lo + 16c, lo + 16c + 16)
+      // for c = q, q + 32, ... of every row into shared memory (asynchronous copies, one wait), the
       // range [s - kHopSpan, s] around the current state; then lane 0 hops.
       // A path moves at most 64 states per window but far fewer in practice;
       // a hop below the staged range reads its byte from global memory.
@@ -719,9 +719,9 @@ __global__ void __launch_bounds__(512, (kOcc && K <= 4) ? 2 : 1)
         const int lo = max(0, s_cur - kHopSpan) & ~15;
         const int hi = min(zstride, (s_cur + 16) & ~15);  // exclusive, 16-aligned
         const int nchunk = (hi - lo) / 16;                // <= kHopRowBytes / 16
-        if (lane < nchunk) {
+        for (int c = lane; c < nchunk; c += 32) {  // lane c copies bytes [lo + 16c, lo + 16c + 16) of each row
           for (int r = 0; r < nb; ++r)
-            cp_async16(zb + r * kHopRowBytes + lane * 16, ztab + static_cast<size_t>(m - r) * zstride + lo + lane * 16);
+            cp_async16(zb + r * kHopRowBytes + c * 16, ztab + static_cast<size_t>(m - r) * zstride + lo + c * 16);
         }
         cp_async_wait_all();
         __syncwarp();
