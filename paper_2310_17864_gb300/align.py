@@ -470,6 +470,7 @@ class Aligner:
                           wait_limit_ms=wait_limit_ms)
         self.ctx = align_create(cfg)
         self._live: dict[int, tuple] = {}
+        self._ranges: list[list] = []  # packed batches: [first id, count, PackedResult, pending]
 
     def close(self) -> None:
         if self.ctx is not None:
@@ -624,9 +625,18 @@ class Aligner:
         if bad.any():
             raise AlignError(int(st[bad][0]), "align_submit_batch")
         res = PackedResult(ids, np.full(n, ALIGN_PENDING, dtype=np.int32), (log_probs, tg, out))
-        for i, rid in enumerate(ids.tolist()):
-            self._live[rid] = (None, (res, i))
+        self._register_packed(res, ids)
         return res
+
+    def _register_packed(self, res, ids) -> None:
+        """The requests of a packed batch, live until finished: one range entry
+        when their ids are consecutive (the usual case), else one per id."""
+        n = ids.size
+        if n and int(ids[-1]) - int(ids[0]) == n - 1:
+            self._ranges.append([int(ids[0]), n, res, n])
+        else:
+            for i, rid in enumerate(ids.tolist()):
+                self._live[rid] = (None, (res, i))
 
     def _waiter(self):
         """A stream of this context's device used only to wait for batches."""
@@ -638,6 +648,15 @@ class Aligner:
         """Record a finished request; returns its Result (None for a packed one)."""
         entry = self._live.pop(rid, None)
         if entry is None:
+            for k, rg in enumerate(self._ranges):
+                i = rid - rg[0]
+                if 0 <= i < rg[1]:
+                    if rg[2].status[i] == ALIGN_PENDING:
+                        rg[2].status[i] = code
+                        rg[3] -= 1
+                        if rg[3] == 0:
+                            del self._ranges[k]
+                    break
             return None
         target = entry[1]
         if isinstance(target, tuple):
@@ -674,8 +693,7 @@ class Aligner:
         if (st < 0).any():
             raise AlignError(int(st[st < 0][0]), "align_submit_batch")
         res = PackedResult(ids, np.full(n, ALIGN_PENDING, dtype=np.int32), (log_probs, tg, total))
-        for i, rid in enumerate(ids.tolist()):
-            self._live[rid] = (None, (res, i))
+        self._register_packed(res, ids)
         return res
 
     def ctc_forward(self, log_probs, targets, blank: int = 0) -> tuple[int, float]:

@@ -1184,9 +1184,12 @@ int pump(align_ctx* ctx, bool launch) {
   return ALIGN_OK;
 }
 
+// Queues one request; then (unless `pump_after` is false, as for the
+// requests of one batch call, which pump once at its end) retires finished
+// batches and, outside batched mode, launches.
 int submit_common(align_ctx* ctx, const float* lp, int64_t T, int64_t C, const int32_t* targets, int64_t L,
                   int32_t blank, align_out out, uint64_t* request_id, bool host_io, bool logits = false,
-                  bool sum = false) {
+                  bool sum = false, bool pump_after = true) {
   if (!ctx || !lp || !request_id || !out.total || (!sum && (!out.path || !out.scores))) return ALIGN_E_INVAL;
   if (sum && logits) return ALIGN_E_INVAL;  // the sum-product path takes log-probabilities
   if (sum) out.path = nullptr, out.scores = nullptr, out.states = nullptr;
@@ -1247,6 +1250,7 @@ int submit_common(align_ctx* ctx, const float* lp, int64_t T, int64_t C, const i
   *request_id = r.id;
   ctx->reqs.emplace(r.id, std::move(r));
   ctx->queued.push_back(*request_id);
+  if (!pump_after) return ALIGN_OK;
   const bool launch_now = !(ctx->flags & ALIGN_F_BATCHED);
   return pump(ctx, launch_now);
 }
@@ -1403,16 +1407,15 @@ int align_submit_batch(align_ctx* ctx, int32_t n, const align_request* reqs, uin
                  ? ALIGN_E_INVAL
                  : submit_common(ctx, q.log_probs, q.T, q.C, q.targets, q.L, q.blank, q.out, &request_ids[i],
                                  (q.flags & ALIGN_REQ_HOST) != 0, (q.flags & ALIGN_REQ_LOGITS) != 0,
-                                 (q.flags & ALIGN_REQ_SUM) != 0);
+                                 (q.flags & ALIGN_REQ_SUM) != 0, /*pump_after=*/false);
     if (rc != ALIGN_OK) request_ids[i] = 0;
     if (submit_status) submit_status[i] = rc;
     if (rc != ALIGN_OK && first_err == ALIGN_OK) first_err = rc;
   }
   ctx->flags = saved;
-  if (!(saved & ALIGN_F_BATCHED)) {
-    const int rc = pump(ctx, true);
-    if (rc != ALIGN_OK) return rc;
-  }
+  // One retire pass for the whole call (and the launch, outside batched mode).
+  const int rc = pump(ctx, !(saved & ALIGN_F_BATCHED));
+  if (rc != ALIGN_OK) return rc;
   return first_err;
 }
 
