@@ -548,12 +548,13 @@ int launch_queued(align_ctx* ctx) {
   // copies have per-batch host addresses).
   bool any_host = false;
   for (auto* r : take) any_host = any_host || r->host_io;
-  // Direct image: when every launch is the fast kernel on device buffers,
-  // the kernels read the descriptors and targets from the pinned image (each
-  // CTA copies its descriptor to shared memory once) and update the result
-  // codes there: no upload or download copy, no graph.
-  bool direct = ctx->d_pinned != nullptr && !any_host;
-  for (auto* r : take) direct = direct && r->plan.shape.fast != 0;
+  // Direct image: when every launch is the fast kernel (device buffers, or
+  // host buffers the copy kernels reach), the kernels read the descriptors,
+  // targets and copy lists from the pinned image (each CTA copies its
+  // descriptor to shared memory once) and update the result codes there: no
+  // upload or download copy, no graph.
+  bool direct = ctx->d_pinned != nullptr;
+  for (auto* r : take) direct = direct && r->plan.shape.fast != 0 && (!r->host_io || r->lp_alias != nullptr);
   int gi = -1;
   bool need_capture = false;
   uint64_t up_copy = up_bytes;
@@ -1187,9 +1188,11 @@ int pump(align_ctx* ctx, bool launch) {
 // Queues one request; then (unless `pump_after` is false, as for the
 // requests of one batch call, which pump once at its end) retires finished
 // batches and, outside batched mode, launches.
+// `tp_plan`: plan with the throughput table (the table the batch will be
+// launched with), so that the launch need not plan the request again.
 int submit_common(align_ctx* ctx, const float* lp, int64_t T, int64_t C, const int32_t* targets, int64_t L,
                   int32_t blank, align_out out, uint64_t* request_id, bool host_io, bool logits = false,
-                  bool sum = false, bool pump_after = true) {
+                  bool sum = false, bool pump_after = true, bool tp_plan = false) {
   if (!ctx || !lp || !request_id || !out.total || (!sum && (!out.path || !out.scores))) return ALIGN_E_INVAL;
   if (sum && logits) return ALIGN_E_INVAL;  // the sum-product path takes log-probabilities
   if (sum) out.path = nullptr, out.scores = nullptr, out.states = nullptr;
@@ -1219,8 +1222,14 @@ int submit_common(align_ctx* ctx, const float* lp, int64_t T, int64_t C, const i
     if (static_cast<int64_t>(inflight_count(ctx)) >= ctx->max_inflight) return ALIGN_E_AGAIN;
   }
   Plan p{};
-  rc = plan_request(ctx, ctx->tune, T, C, L, logits, &p, sum);
+  tp_plan = tp_plan && ctx->tune_tp.nbuckets != 0;
+  rc = plan_request(ctx, tp_plan ? ctx->tune_tp : ctx->tune, T, C, L, logits, &p, sum);
+  if (rc != ALIGN_OK && tp_plan) {  // the throughput table cannot place it: the latency table's plan
+    tp_plan = false;
+    rc = plan_request(ctx, ctx->tune, T, C, L, logits, &p, sum);
+  }
   if (rc != ALIGN_OK) return rc;
+  if (tp_plan) p.shape.occ = 1;
   Request r;
   r.logits = logits;
   r.sum = sum;
@@ -1247,6 +1256,7 @@ int submit_common(align_ctx* ctx, const float* lp, int64_t T, int64_t C, const i
   r.blank = blank;
   r.targets.assign(targets, targets + L);
   r.plan = p;
+  r.plan_table = tp_plan ? ALIGN_TUNE_THROUGHPUT : ALIGN_TUNE_LATENCY;
   *request_id = r.id;
   ctx->reqs.emplace(r.id, std::move(r));
   ctx->queued.push_back(*request_id);
@@ -1398,6 +1408,24 @@ int align_submit_batch(align_ctx* ctx, int32_t n, const align_request* reqs, uin
   if (!ctx || n < 0 || (n > 0 && (!reqs || !request_ids))) return ALIGN_E_INVAL;
   cudaSetDevice(ctx->device);
   // Queue every request without launching, then launch once: one batch.
+  // The table the batch will most likely be launched with (the rule of
+  // want_throughput over the queued requests and these) plans them at once.
+  bool tp_plan = false;
+  if (ctx->tune_tp.nbuckets != 0 && ctx->queued.size() + static_cast<size_t>(n) >= 2) {
+    uint64_t work = 0;
+    int64_t tmax = 0;
+    for (uint64_t id : ctx->queued) {
+      const Request& r = ctx->reqs.at(id);
+      work += static_cast<uint64_t>(r.T) * static_cast<uint64_t>((2 * r.L + 1 + 63) / 64);
+      tmax = std::max(tmax, r.T);
+    }
+    for (int32_t i = 0; i < n; ++i) {
+      if (reqs[i].T < 1 || reqs[i].L < 0) continue;
+      work += static_cast<uint64_t>(reqs[i].T) * static_cast<uint64_t>((2 * reqs[i].L + 1 + 63) / 64);
+      tmax = std::max<int64_t>(tmax, reqs[i].T);
+    }
+    tp_plan = work > static_cast<uint64_t>(tmax) * 8ull * static_cast<uint64_t>(std::max(1, ctx->num_sms));
+  }
   const uint32_t saved = ctx->flags;
   ctx->flags |= ALIGN_F_BATCHED;
   int first_err = ALIGN_OK;
@@ -1407,7 +1435,7 @@ int align_submit_batch(align_ctx* ctx, int32_t n, const align_request* reqs, uin
                  ? ALIGN_E_INVAL
                  : submit_common(ctx, q.log_probs, q.T, q.C, q.targets, q.L, q.blank, q.out, &request_ids[i],
                                  (q.flags & ALIGN_REQ_HOST) != 0, (q.flags & ALIGN_REQ_LOGITS) != 0,
-                                 (q.flags & ALIGN_REQ_SUM) != 0, /*pump_after=*/false);
+                                 (q.flags & ALIGN_REQ_SUM) != 0, /*pump_after=*/false, tp_plan);
     if (rc != ALIGN_OK) request_ids[i] = 0;
     if (submit_status) submit_status[i] = rc;
     if (rc != ALIGN_OK && first_err == ALIGN_OK) first_err = rc;
