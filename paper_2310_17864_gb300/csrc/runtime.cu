@@ -231,6 +231,10 @@ uint64_t inflight_count(const align_ctx* ctx) { return ctx->reqs.size(); }
 int plan_request(const align_ctx* ctx, const TuneTable& table, int64_t T, int64_t C, int64_t L, bool logits,
                  Plan* out, bool sum = false) {
   TuneTable t = table;
+  // Throughput batches with wide rows (C > 64: stages of 8 KB per few frames):
+  // CTAs of at most four warps, so that several share an SM (a wider CTA
+  // needs a stage ring that leaves room for one).
+  if (&table == &ctx->tune_tp && C > 64) t.max_warps = std::min(t.max_warps, 4);
   const int rc = make_plan(t, T, C, L, sum ? ~0ull : ctx->bp_arena.cap(),
                            !sum && (ctx->flags & ALIGN_F_FORCE_CHECKPOINT) != 0, out);
   if (rc != ALIGN_OK) return rc;

@@ -954,7 +954,11 @@ FwdParams plan_params(const LaunchShape& shape, int C, int frames_per_stage, uin
     p.link_off = static_cast<int>(sizeof(SmemHead));
     p.link_stride = 16 + p.pkgs * p.kb * 8;
     const int hops = std::max(0, shape.warps - 1);
-    p.stages = std::min(kMaxStages, kLead + (hops * 2 * p.kb + F - 1) / F);
+    // Throughput-planned batches with wide rows (packages of 4 frames, stages
+    // of 8 KB) keep two stages ahead of the first warp instead of kLead, so
+    // that three CTAs of four warps share an SM instead of two.
+    const int lead = (p.kb == 4 && shape.occ) ? 2 : kLead;
+    p.stages = std::min(kMaxStages, std::max(kLead, lead + (hops * 2 * p.kb + F - 1) / F));
     p.block = p.kb;
     p.rb = 0;
     p.off_ring = p.link_off;  // the backtrack's hop buffer reuses links and stages
