@@ -112,6 +112,16 @@ extern "C" int align_forced_noalloc(const float* log_probs, int64_t T, int64_t C
   g_msg[0] = '\0';
   if (!log_probs || !out.path || !out.scores || !out.total || (L > 0 && !targets))
     return fail(ALIGN_E_INVAL, "align_forced_noalloc: a required pointer is NULL");
+  {
+    // The call copies from host memory and synchronises its stream, which a
+    // stream capture cannot record: refused before any other CUDA call.
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(static_cast<cudaStream_t>(cuda_stream), &cs) != cudaSuccess) {
+      (void)cudaGetLastError();
+    } else if (cs != cudaStreamCaptureStatusNone) {
+      return fail(ALIGN_E_INVAL, "align_forced_noalloc: the stream is being captured (the call cannot be captured)");
+    }
+  }
   int64_t R = 0;
   int rc = validate_request(targets, L, C, blank, T, &R);
   if (rc != ALIGN_OK)

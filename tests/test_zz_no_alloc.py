@@ -83,3 +83,21 @@ def test_noalloc_rejects_requests_beyond_its_scratch():
     rc, _ = align.align_forced_noalloc(lp.data_ptr(), u.T, u.C, u.targets, 0, o, None)
     assert rc == align.ALIGN_E_TOO_LARGE
     assert "scratch" in align.align_noalloc_last_error()
+
+
+def test_noalloc_refuses_a_capturing_stream():
+    """The call copies from host memory and synchronises its stream, so it can
+    never be captured: on a stream under capture it returns ALIGN_E_INVAL with
+    a message and records nothing."""
+    build.build()
+    u = synth.make_utterance(7, 100, 32, 20)
+    path, scores, total, states = _outs(u.T)
+    lp = u.lp.cuda()
+    o = align.AlignOut(path.data_ptr(), scores.data_ptr(), total.data_ptr(), states.data_ptr())
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    torch.cuda.synchronize()
+    with torch.cuda.graph(g, stream=s):
+        rc, _ = align.align_forced_noalloc(lp.data_ptr(), u.T, u.C, u.targets, 0, o, s.cuda_stream)
+    assert rc == align.ALIGN_E_INVAL
+    assert "captured" in align.align_noalloc_last_error()
