@@ -101,6 +101,8 @@ struct FwdParams {
   int32_t gpkgs;           // package slots per global link of a grid team (power of two)
   int32_t link_off;        // shared-memory offset of the per-warp links
   int32_t link_stride;     // bytes per warp link: 16-byte head + pkgs * kb * 8
+  int32_t row_c;           // 32: every job of the launch has 32 classes and whole-window
+                           // hand-offs (rows at compile-time offsets); else 0
   uint64_t wait_limit_ns;  // limit of every spin wait
 };
 

@@ -27,9 +27,16 @@
 //
 // Backpointer layout (per pass): window m (frames t_begin+1+32m ..
 // t_begin+32m+32, bit i = frame t_begin+1+32m+i), warp g, word w, lane l at
-//   bp[((m * G + g) * NW + w) * 32 + l],   NW = 3K/2:
-//   word j < K      : "advance won" bits of state 32Kg + Kl + j,
-//   word K + i      : "skip won" bits of label state 32Kg + Kl + 2i + 1.
+//   bp[((m * G + g) * NW + w) * 32 + l],   NW = 3K/2 (words K+1.. unused):
+//   word j < K, j even : "advance won" bits of blank state 32Kg + Kl + j,
+//   word j < K, j odd  : "stay lost" bits of label state 32Kg + Kl + j,
+//   word K             : the lane's skip permissions (bit i: label state
+//                        32Kg + Kl + 2i + 1 may skip), the same every window.
+// A label state's advance and skip candidates are also the two candidates of
+// the blank state below it, so one comparison serves both: when the label
+// state does not stay, it skips exactly when skipping is allowed and the
+// blank state below advanced at the same frame (strict '>' keeps the order
+// stay, advance, skip), and the backtrack reads that bit back.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -238,10 +245,13 @@ struct StageRing {
 
 // The whole hot path of one job for one CTA of its team: this CTA is rank
 // `crank` of `ncta` CTAs. The stage barriers are initialised by the caller.
-template <int K, int kB, bool kGrid, bool kNorm>
+// kC: 0, or the vocabulary of every job of the launch when it is 32 (window
+// mode): emission rows then sit at compile-time offsets in a stage.
+template <int K, int kB, bool kGrid, bool kNorm, int kC>
 __device__ __forceinline__ void team_job(const FwdJob& J, const FwdParams& P, const uint32_t ncta, const uint32_t crank,
                                          StageRing& ring) {
   static_assert(K == 2 || K == 4, "fast kernel: K = 2 or 4");
+  static_assert(kC == 0 || (kC == 32 && kB == kAnchorD), "fixed rows of 32 classes in window mode only");
   static_assert(kB == 4 || kB == 8 || kB == kAnchorD, "fast kernel: blocks of 4 or 8 frames, or whole windows");
   constexpr int NW = bp_words(K);
   constexpr int kWin = kAnchorD;
@@ -277,7 +287,7 @@ __device__ __forceinline__ void team_job(const FwdJob& J, const FwdParams& P, co
   // any barrier): stages hold F >= kB rows, the team holds every state,
   // package rings are powers of two, checkpoint frames end windows.
   const bool ck_ok = ckpt == nullptr || (ck_every > 0 && ck_every % kAnchorD == 0 && t_begin % ck_every == 0);
-  if (F * C * 4 > P.stage_bytes || static_cast<int64_t>(ncta) * W * 32 * K < S || P.stages < kLead ||
+  if (F * C * 4 > P.stage_bytes || (kC != 0 && C != kC) || static_cast<int64_t>(ncta) * W * 32 * K < S || P.stages < kLead ||
       P.stages > kMaxStages || F < kB || F > kAnchorD || (F & (F - 1)) != 0 || P.kb != kB || R < 2 ||
       (R & (R - 1)) != 0 || P.link_stride < 16 + R * kB * 8 || !ck_ok ||
       (kGrid && ncta > 1 && (J.xlink == nullptr || Rg < 2 || (Rg & (Rg - 1)) != 0))) {
@@ -368,6 +378,10 @@ __device__ __forceinline__ void team_job(const FwdJob& J, const FwdParams& P, co
     skok[i] = skip;
   }
 
+  uint32_t skmask = 0u;  // bit i: label state s0 + 2i + 1 may skip
+#pragma unroll
+  for (int i = 0; i < K / 2; ++i) skmask |= skok[i] ? (1u << i) : 0u;
+
   // ---- frame t_begin ----
   float a[K];
   int A[K];  // anchor: state at the last window end on the best path to each state
@@ -435,6 +449,35 @@ __device__ __forceinline__ void team_job(const FwdJob& J, const FwdParams& P, co
   const bool stall = (J.flags & kJobTestStall) && g == 0;  // test hook: the first warp never publishes
   bool dead = false;                                       // a bounded wait ran out (or another warp aborted)
 
+  // One frame of this lane's states, as (blank j-1, label j) pairs in
+  // descending order (a[j-1], a[j-2] still hold frame t-1). The blank state
+  // advances when its left neighbour is strictly greater; the label state's
+  // best move other than staying is then that same candidate when it may
+  // skip, else the blank state below, and it leaves its state only when that
+  // candidate is strictly greater (stay > advance > skip on ties). Selects
+  // for the values; a chosen move's bit is set by a predicated OR.
+  auto step_pairs = [&](const float left, const int Aleft, const float eb, const float (&el)[K / 2],
+                        uint32_t (&bw)[NW], const uint32_t bit) {
+#pragma unroll
+    for (int j = K - 1; j >= 1; j -= 2) {
+      const float p = (j == 1) ? left : a[j - 2];
+      const int qp = (j == 1) ? Aleft : A[j - 2];
+      const bool adv = p > a[j - 1];
+      const float mb = adv ? p : a[j - 1];
+      const int Ab = adv ? qp : A[j - 1];
+      const bool sk = skok[j >> 1];
+      const float mv = sk ? mb : a[j - 1];
+      const int Am = sk ? Ab : A[j - 1];
+      const bool moved = mv > a[j];
+      a[j] = (moved ? mv : a[j]) + el[j >> 1];
+      A[j] = moved ? Am : A[j];
+      if (moved) bw[j] |= bit;
+      a[j - 1] = mb + eb;
+      A[j - 1] = Ab;
+      if (adv) bw[j - 1] |= bit;
+    }
+  };
+
   // ---- frames t_begin+1 .. t_end-1 ----
   float carry_a = a[K - 1];  // block mode: alpha of the last state at the first frame of the next package
   int carry_A = A[K - 1];
@@ -443,7 +486,8 @@ __device__ __forceinline__ void team_job(const FwdJob& J, const FwdParams& P, co
     if (bp != nullptr) {
       uint32_t* dst = bp + (static_cast<size_t>(m) * G + g) * NW * 32 + lane;
 #pragma unroll
-      for (int w = 0; w < NW; ++w) dst[w * 32] = bits[w];
+      for (int w = 0; w < K; ++w) dst[w * 32] = bits[w];
+      dst[K * 32] = skmask;
     }
     if (ztab != nullptr && s0 < zstride) {
       uint8_t* dst = ztab + static_cast<size_t>(m) * zstride + s0;
@@ -572,6 +616,8 @@ __device__ __forceinline__ void team_job(const FwdJob& J, const FwdParams& P, co
           return (lane >= nfm) | (static_cast<uint32_t>(w >> 32) - e < 256u);
         };
         auto wait_slot = [&](int mm, int nfm, uint64_t& w0, uint64_t& w1) -> bool {
+          load_pair(mm, w0, w1);  // usually there already: no timer read
+          if (__all_sync(kFull, tag_ok(mm, nfm, w0, w1))) return true;
           const uint64_t t0 = gtimer();
           for (;;) {
             load_pair(mm, w0, w1);
@@ -617,12 +663,13 @@ __device__ __forceinline__ void team_job(const FwdJob& J, const FwdParams& P, co
 
     uint32_t pk_lo0 = 0u, pk_hi0 = 0u, pk_lo1 = 0u, pk_hi1 = 0u;  // the left neighbour's words of a frame pair
     // Frame i of window m (frame t_begin + 32m + 1 + i).
+    const int Cr = kC != 0 ? kC : C;  // row stride of a stage (a compile-time 32 when kC is)
     auto do_frame = [&](const int m, const int i, const float* rowp, const uint32_t rslot_addr) {
       const uint32_t bit = 1u << i;
-      const float eb = rowp[i * C + blank];
+      const float eb = rowp[i * Cr + blank];
       float el[K / 2];
 #pragma unroll
-      for (int q = 0; q < K / 2; ++q) el[q] = rowp[i * C + col[q]];
+      for (int q = 0; q < K / 2; ++q) el[q] = rowp[i * Cr + col[q]];
       // The left neighbour's word of this frame (read in pairs, at even frames).
       if ((i & 1) == 0)
         asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
@@ -641,30 +688,7 @@ __device__ __forceinline__ void team_job(const FwdJob& J, const FwdParams& P, co
         const uint32_t e = (static_cast<uint32_t>(t_begin + kWin * m + 1 + i) << 8);
         Aleft = is_l0 ? (s0 - 1 - static_cast<int>(static_cast<uint32_t>(pw >> 32) - e)) : shA;
       }
-#pragma unroll
-      for (int j = K - 1; j >= 0; --j) {  // descending: a[j-1], a[j-2] still hold frame t-1
-        const float p1 = (j == 0) ? left : a[j - 1];
-        const int q1 = (j == 0) ? Aleft : A[j - 1];
-        if ((j & 1) == 0) {  // blank state: stay or advance
-          const bool b1 = p1 > a[j];
-          const float mm = b1 ? p1 : a[j];
-          A[j] = b1 ? q1 : A[j];
-          if (b1) bits[j] |= bit;
-          a[j] = mm + eb;
-        } else {  // label state: stay, advance, or skip when allowed
-          const float p2 = (j == 1) ? left : a[j - 2];
-          const int q2 = (j == 1) ? Aleft : A[j - 2];
-          const bool b1 = p1 > a[j];
-          float mm = b1 ? p1 : a[j];
-          const int an = b1 ? q1 : A[j];
-          const bool b2 = skok[j >> 1] & (p2 > mm);
-          mm = b2 ? p2 : mm;
-          A[j] = b2 ? q2 : an;
-          if (b1) bits[j] |= bit;
-          if (b2) bits[K + (j >> 1)] |= bit;
-          a[j] = mm + el[j >> 1];
-        }
-      }
+      step_pairs(left, Aleft, eb, el, bits, bit);
       // The word of this frame for the right neighbour is word i+1 of slot m
       // (word 0 of slot m+1 for the window's last frame); even frames store
       // it with the previous frame's word.
@@ -803,32 +827,7 @@ __device__ __forceinline__ void team_job(const FwdJob& J, const FwdParams& P, co
         // (anchors are reset at window ends).
         if (i == 0 && iw0 == 0) Aleft = s0 - 1;
         const uint32_t bit = 1u << i;
-#pragma unroll
-        for (int j = K - 1; j >= 0; --j) {  // descending: a[j-1], a[j-2] still hold frame t-1
-          const float p1 = (j == 0) ? left : a[j - 1];
-          const int q1 = (j == 0) ? Aleft : A[j - 1];
-          // Selects for the values (no data-dependent branch); the bit of a
-          // chosen move is set by a one-statement conditional (predicated).
-          if ((j & 1) == 0) {  // blank state: stay or advance
-            const bool b1 = p1 > a[j];
-            const float mm = b1 ? p1 : a[j];
-            A[j] = b1 ? q1 : A[j];
-            if (b1) bb[j] |= bit;
-            a[j] = mm + eb[i];
-          } else {  // label state: stay, advance, or skip when allowed
-            const float p2 = (j == 1) ? left : a[j - 2];
-            const int q2 = (j == 1) ? Aleft : A[j - 2];
-            const bool b1 = p1 > a[j];
-            float mm = b1 ? p1 : a[j];
-            const int an = b1 ? q1 : A[j];
-            const bool b2 = skok[j >> 1] & (p2 > mm);
-            mm = b2 ? p2 : mm;
-            A[j] = b2 ? q2 : an;
-            if (b1) bb[j] |= bit;
-            if (b2) bb[K + (j >> 1)] |= bit;
-            a[j] = mm + el[i][j >> 1];
-          }
-        }
+        step_pairs(left, Aleft, eb[i], el[i], bb, bit);
         if (i + 1 < kB) {
           sa[i + 1] = a[K - 1];
           sA[i + 1] = A[K - 1];
@@ -986,37 +985,51 @@ __device__ __forceinline__ void team_job(const FwdJob& J, const FwdParams& P, co
   // ---- tail 2 (every lane of the team): walk the windows in parallel ----
   // Window m covers frames (b, e], b = t_begin + 32m, e = min(b + 32, t_end - 1);
   // its top state is path[e]. The words of a state hold all 32 frames of the
-  // window, and the NW words of a lane hold its K states, so a walk loads a
-  // lane's words together (independent loads, one round trip) and reloads
-  // only when the path leaves that lane's states.
+  // window, and the K + 1 words of a lane hold its K states, so a walk loads a
+  // lane's words together (independent loads, one round trip). The path only
+  // moves down, at most 2 <= K states a frame, so the lane it enters next is
+  // the one below: its words are loaded while the walk is in the current
+  // lane's states.
+  constexpr int kWords = K + 1;
   const int nwalk = max(nwin, 1);
   for (int m = g * 32 + lane; !producer && m < nwalk; m += G * 32) {
     const int b = t_begin + m * kAnchorD;
     const int e = (nwin == 0) ? t_begin : min(b + kAnchorD, t_end - 1);
     const uint32_t* wbase = bp + static_cast<size_t>(m) * G * NW * 32;
-    int sc = path[e];
-    int cur = -1;  // lane (over the team) whose words are in wv
-    uint32_t wv[NW];
+    auto lane_words = [&](const int lg, uint32_t (&dst)[kWords]) {
+      if (lg >= 0) {
+        const uint32_t* w = wbase + static_cast<size_t>(lg >> 5) * NW * 32 + (lg & 31);
 #pragma unroll
-    for (int q = 0; q < NW; ++q) wv[q] = 0u;
+        for (int q = 0; q < kWords; ++q) dst[q] = w[q * 32];
+      } else {
+#pragma unroll
+        for (int q = 0; q < kWords; ++q) dst[q] = 0u;
+      }
+    };
+    int sc = path[e];
+    int cur = sc / K;  // lane (over the team) whose words are in wv; wn: the lane below
+    uint32_t wv[kWords], wn[kWords];
+    lane_words(cur, wv);
+    lane_words(cur - 1, wn);
     for (int f = e; f > b; --f) {
       path[f] = sc;
       const int lg = sc / K;
       if (lg != cur) {
         cur = lg;
-        const int gs = lg / 32;
-        const uint32_t* w = wbase + static_cast<size_t>(gs) * NW * 32 + (lg - gs * 32);
 #pragma unroll
-        for (int q = 0; q < NW; ++q) wv[q] = w[q * 32];
+        for (int q = 0; q < kWords; ++q) wv[q] = wn[q];
+        lane_words(lg - 1, wn);
       }
       const int j = sc - lg * K;
-      uint32_t aw = wv[0], sw = 0u;
+      uint32_t mw = wv[0], bw = 0u;  // the state's word; for a label state, the blank state's below it
 #pragma unroll
-      for (int q = 1; q < K; ++q) aw = (j == q) ? wv[q] : aw;
+      for (int q = 1; q < K; ++q) mw = (j == q) ? wv[q] : mw;
 #pragma unroll
-      for (int q = 0; q < K / 2; ++q) sw = (j == 2 * q + 1) ? wv[K + q] : sw;
+      for (int q = 0; q < K / 2; ++q) bw = (j == 2 * q + 1) ? wv[2 * q] : bw;
       const int i = f - b - 1;
-      sc -= ((sw >> i) & 1u) ? 2 : static_cast<int>((aw >> i) & 1u);
+      int step = static_cast<int>((mw >> i) & 1u);
+      if (step && (j & 1) && ((bw >> i) & 1u) && ((wv[K] >> (j >> 1)) & 1u)) step = 2;
+      sc -= step;
     }
     if (m == 0) path[b] = sc;
   }
@@ -1088,7 +1101,7 @@ __device__ __forceinline__ void init_stage_barriers(const FwdParams& P, bool bul
 
 // One team per job: a thread-block cluster (or one CTA), or a grid team of
 // P.grid_ctas consecutive CTAs of a cooperative launch.
-template <int K, int kB, bool kGrid, bool kNorm>
+template <int K, int kB, bool kGrid, bool kNorm, int kC>
 __global__ void __launch_bounds__(512, 1) trellis_fast_kernel(const FwdJob* __restrict__ jobs, const FwdParams P) {
   const uint32_t ncta = kGrid ? static_cast<uint32_t>(max(P.grid_ctas, 1)) : cluster_nctarank();
   const uint32_t crank = kGrid ? blockIdx.x % ncta : cluster_ctarank();
@@ -1104,7 +1117,7 @@ __global__ void __launch_bounds__(512, 1) trellis_fast_kernel(const FwdJob* __re
   __syncthreads();
   init_stage_barriers(P, (sjob.flags & kJobBulkRows) != 0);
   StageRing ring;
-  team_job<K, kB, kGrid, kNorm>(sjob, P, ncta, crank, ring);
+  team_job<K, kB, kGrid, kNorm, kC>(sjob, P, ncta, crank, ring);
 }
 
 // Persistent launch: every CTA of a cooperative launch (all resident) takes
@@ -1113,7 +1126,7 @@ __global__ void __launch_bounds__(512, 1) trellis_fast_kernel(const FwdJob* __re
 // first_seat); a job of several CTAs links them through global memory as a
 // grid team does. Seats are handed out in order and every CTA is resident,
 // so each team fills: the CTAs of earlier jobs finish and take later seats.
-template <int K, int kB, bool kNorm>
+template <int K, int kB, bool kNorm, int kC>
 __global__ void __launch_bounds__(512, 1) trellis_persist_kernel(const FwdJob* __restrict__ jobs, const FwdParams P,
                                                                  const int32_t* __restrict__ seat_job,
                                                                  int32_t total_seats, int32_t* counter) {
@@ -1134,7 +1147,7 @@ __global__ void __launch_bounds__(512, 1) trellis_persist_kernel(const FwdJob* _
     }
     __syncthreads();
     const FwdJob& J = head->job;
-    team_job<K, kB, true, kNorm>(J, P, static_cast<uint32_t>(J.team_ctas), static_cast<uint32_t>(seat - J.first_seat),
+    team_job<K, kB, true, kNorm, kC>(J, P, static_cast<uint32_t>(J.team_ctas), static_cast<uint32_t>(seat - J.first_seat),
                                  ring);
     // The backtrack used the links and stages as scratch: the next job's
     // bulk copies write there.
@@ -1144,7 +1157,7 @@ __global__ void __launch_bounds__(512, 1) trellis_persist_kernel(const FwdJob* _
   }
 }
 
-template <int K, int kB, bool kGrid, bool kNorm>
+template <int K, int kB, bool kGrid, bool kNorm, int kC>
 cudaError_t launch_fast_k(const LaunchShape& shape, const FwdParams& p, const FwdJob* d_jobs, int njobs,
                           cudaStream_t stream) {
   int dev = 0;
@@ -1156,7 +1169,7 @@ cudaError_t launch_fast_k(const LaunchShape& shape, const FwdParams& p, const Fw
     smem = std::max(smem, smem_max);  // one CTA per SM (see the generic launcher)
     if (njobs != 1) return cudaErrorInvalidValue;
   }
-  auto fn = trellis_fast_kernel<K, kB, kGrid, kNorm>;
+  auto fn = trellis_fast_kernel<K, kB, kGrid, kNorm, kC>;
   e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_max);
   if (e != cudaSuccess) return e;
   if (smem > smem_max) return cudaErrorInvalidValue;
@@ -1186,30 +1199,45 @@ cudaError_t launch_fast_k(const LaunchShape& shape, const FwdParams& p, const Fw
   return cudaLaunchKernelEx(&cfg, fn, d_jobs, p);
 }
 
-template <int K, int kB>
-cudaError_t launch_fast_kb(const LaunchShape& shape, const FwdParams& p, const FwdJob* d_jobs, int njobs,
+template <int K, int kB, int kC>
+cudaError_t launch_fast_kc(const LaunchShape& shape, const FwdParams& p, const FwdJob* d_jobs, int njobs,
                            cudaStream_t s) {
   if (shape.grid) {
-    if (shape.norm) return launch_fast_k<K, kB, true, true>(shape, p, d_jobs, njobs, s);
-    return launch_fast_k<K, kB, true, false>(shape, p, d_jobs, njobs, s);
+    if (shape.norm) return launch_fast_k<K, kB, true, true, kC>(shape, p, d_jobs, njobs, s);
+    return launch_fast_k<K, kB, true, false, kC>(shape, p, d_jobs, njobs, s);
   }
-  if (shape.norm) return launch_fast_k<K, kB, false, true>(shape, p, d_jobs, njobs, s);
-  return launch_fast_k<K, kB, false, false>(shape, p, d_jobs, njobs, s);
+  if (shape.norm) return launch_fast_k<K, kB, false, true, kC>(shape, p, d_jobs, njobs, s);
+  return launch_fast_k<K, kB, false, false, kC>(shape, p, d_jobs, njobs, s);
 }
 
 template <int K, int kB>
-cudaError_t persist_fn(void (**fn)(const FwdJob*, FwdParams, const int32_t*, int32_t, int32_t*)) {
-  *fn = trellis_persist_kernel<K, kB, false>;
+cudaError_t launch_fast_kb(const LaunchShape& shape, const FwdParams& p, const FwdJob* d_jobs, int njobs,
+                           cudaStream_t s) {
+  if constexpr (kB == kAnchorD) {
+    if (p.row_c == 32) return launch_fast_kc<K, kB, 32>(shape, p, d_jobs, njobs, s);
+  }
+  return launch_fast_kc<K, kB, 0>(shape, p, d_jobs, njobs, s);
+}
+
+template <int K, int kB>
+cudaError_t persist_fn(const FwdParams& p, void (**fn)(const FwdJob*, FwdParams, const int32_t*, int32_t, int32_t*)) {
+  if constexpr (kB == kAnchorD) {
+    if (p.row_c == 32) {
+      *fn = trellis_persist_kernel<K, kB, false, 32>;
+      return cudaSuccess;
+    }
+  }
+  *fn = trellis_persist_kernel<K, kB, false, 0>;
   return cudaSuccess;
 }
 
 cudaError_t persist_kernel_of(const LaunchShape& shape, const FwdParams& p,
                               void (**fn)(const FwdJob*, FwdParams, const int32_t*, int32_t, int32_t*)) {
   if (shape.norm || shape.sum) return cudaErrorInvalidValue;  // persistent launches align log-probabilities
-  if (shape.K == 2 && p.kb == kAnchorD) return persist_fn<2, kAnchorD>(fn);
-  if (shape.K == 2 && p.kb == 4) return persist_fn<2, 4>(fn);
-  if (shape.K == 4 && p.kb == kAnchorD) return persist_fn<4, kAnchorD>(fn);
-  if (shape.K == 4 && p.kb == 4) return persist_fn<4, 4>(fn);
+  if (shape.K == 2 && p.kb == kAnchorD) return persist_fn<2, kAnchorD>(p, fn);
+  if (shape.K == 2 && p.kb == 4) return persist_fn<2, 4>(p, fn);
+  if (shape.K == 4 && p.kb == kAnchorD) return persist_fn<4, kAnchorD>(p, fn);
+  if (shape.K == 4 && p.kb == 4) return persist_fn<4, 4>(p, fn);
   return cudaErrorInvalidValue;
 }
 

@@ -953,6 +953,7 @@ FwdParams plan_params(const LaunchShape& shape, int C, int frames_per_stage, uin
     p.gpkgs = (p.kb == kAnchorD) ? kFastWinGridPkgs : kFastGridPkgs;
     p.link_off = static_cast<int>(sizeof(SmemHead));
     p.link_stride = 16 + p.pkgs * p.kb * 8;
+    p.row_c = (p.kb == kAnchorD && C == 32) ? 32 : 0;
     const int hops = std::max(0, shape.warps - 1);
     // Throughput-planned batches with wide rows (packages of 4 frames, stages
     // of 8 KB) keep two stages ahead of the first warp instead of kLead, so
