@@ -139,7 +139,7 @@ inline uint64_t xlink_bytes(int ncta) {
 
 // Fast kernel: package slots per link, and the bytes of a grid team's global
 // links (one per CTA boundary: 16-byte head + slots of kb alphas and kb
-// anchors) followed by the 2-word team barrier.
+// anchors) followed by the team block (barrier, final alphas, timeout flag).
 constexpr int kFastPkgs = 8;       // packages of 4 frames per shared-memory link
 constexpr int kFastGridPkgs = 16;  // packages of 4 frames per global link
 constexpr int kFastWinPkgs = 4;    // 32-frame windows per shared-memory link (window mode)
@@ -147,7 +147,9 @@ constexpr int kFastWinGridPkgs = 8;  // 32-frame windows per global link (window
 inline uint64_t fast_xlink_bytes(int ncta, int kb) {
   const uint64_t slots = (kb == 32) ? kFastWinGridPkgs : kFastGridPkgs;
   const uint64_t gstride = 16ull + slots * kb * 8ull;
-  const uint64_t b = static_cast<uint64_t>(ncta > 1 ? ncta - 1 : 0) * gstride + 16ull;
+  // After the links, the team block: barrier count and generation, the two
+  // final alphas, the team's timeout flag.
+  const uint64_t b = static_cast<uint64_t>(ncta > 1 ? ncta - 1 : 0) * gstride + 32ull;
   return (b + 255) & ~255ull;
 }
 

@@ -126,6 +126,9 @@ struct SmemHead {
   int32_t abort;            // set by any thread of this CTA whose wait hit the limit
   uint32_t unused;
   uint64_t sink;            // scratch slot written by the last warp of the team
+  float fin[2];             // fast kernel, CTA 0 of a cluster team: alpha_{T-1} of states S-2, S-1
+  uint32_t team_bad;        // fast kernel, cluster teams: set in every CTA by a CTA whose wait ran out
+  uint32_t pad;
   FwdJob job;               // fast kernel: this CTA's copy of its job descriptor
 };
 static_assert(sizeof(SmemHead) % 16 == 0, "head size: what follows it is 16-byte aligned");

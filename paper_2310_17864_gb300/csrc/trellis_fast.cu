@@ -303,9 +303,12 @@ __device__ __forceinline__ void team_job(const FwdJob& J, const FwdParams& P, co
     for (int i = threadIdx.x; i < n16; i += blockDim.x) lk[i] = make_uint4(0u, 0u, 0u, 0u);
   }
   const bool bulk = (J.flags & kJobBulkRows) != 0;
-  if (threadIdx.x == 0) head->abort = 0;
+  if (threadIdx.x == 0) {
+    head->abort = 0;
+    head->team_bad = 0u;
+  }
   __syncthreads();
-  if (!kGrid && ncta > 1) cluster_sync();  // every CTA's links are zero before any remote store
+  if (!kGrid && ncta > 1) cluster_sync();  // every CTA's links and flags are zero before any remote store
 
   // ---- emission staging (a dedicated producer warp) ----
   // Chunk c holds the rows of frames t_begin+1+c*F .. t_begin+(c+1)*F in
@@ -344,6 +347,9 @@ __device__ __forceinline__ void team_job(const FwdJob& J, const FwdParams& P, co
   uint32_t* const xbar = kGrid ? reinterpret_cast<uint32_t*>(reinterpret_cast<unsigned char*>(J.xlink) +
                                                             static_cast<size_t>(ncta - 1) * (16 + Rg * kB * 8))
                                : nullptr;
+  // Team block in device memory (grid teams of several CTAs): words 0-1 the
+  // barrier, 2-3 the final alphas, 4 the timeout flag.
+  const bool xteam = kGrid && ncta > 1;
   if (producer) {
     // Every chunk as soon as its stage is free (released by every compute
     // warp); then every copy in flight lands before the shared memory is
@@ -899,22 +905,46 @@ __device__ __forceinline__ void team_job(const FwdJob& J, const FwdParams& P, co
     }
   }
   }
-  // ---- alpha_{T-1} of the two final states ----
-  if (!dead && *abort == 0 && t_end == J.T && J.final2 != nullptr) {
+  // ---- alpha_{T-1} of the two final states, to where tail 1 reads them:
+  // CTA 0's shared memory (over DSMEM from another CTA of a cluster), or the
+  // team block of a grid team (device memory) ----
+  if (!dead && *abort == 0 && t_end == J.T && (J.flags & kJobWriteFinal)) {
 #pragma unroll
     for (int j = 0; j < K; ++j) {
-      if (s0 + j == S - 1) J.final2[1] = a[j];
-      if (s0 + j == S - 2) J.final2[0] = a[j];
+      if (s0 + j == S - 2 || s0 + j == S - 1) {
+        const int k = s0 + j - (S - 2);
+        if (xteam) {
+          reinterpret_cast<float*>(xbar)[2 + k] = a[j];
+        } else if (ncta > 1) {
+          st_remote_u32(mapa_rank(smem_addr(&head->fin[k]), 0), __float_as_uint(a[j]));
+        } else {
+          head->fin[k] = a[j];
+        }
+      }
     }
   }
 
   }  // compute warps
-  // A CTA whose wait ran out marks the request timed out before the team
-  // barrier; after it every CTA reads the same status and leaves together.
+  // Team barrier between the phases, and one decision for the whole team:
+  // carry on unless a CTA's bounded wait ran out. A CTA whose wait ran out
+  // marks the request timed out (the result block may be in host memory:
+  // written, never read back here) and, before the barrier, raises the
+  // team's flag in device-side memory: the team block of a grid team, or the
+  // flag word in every CTA's shared memory in a cluster (pushed over DSMEM
+  // while every CTA still waits at the barrier; after it a CTA reads only its
+  // own shared memory, since another CTA may already have exited). The
+  // cluster barrier orders memory at cluster scope and the grid barrier
+  // fences at GPU scope, so no thread fences on its own.
   auto team_sync_ok = [&]() -> bool {
-    __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0 && *abort != 0) atomicExch(J.status, kStTimeout);
+    const bool mine = *abort != 0;  // no warp of this CTA writes it during the barrier
+    if (threadIdx.x == 0 && mine) {
+      atomicExch(J.status, kStTimeout);
+      if (xteam) atomicExch(xbar + 4, 1u);
+      if (!kGrid && ncta > 1)
+        for (uint32_t r = 0; r < ncta; ++r) st_remote_u32(mapa_rank(smem_addr(&head->team_bad), r), 1u);
+    }
+    bool bad = mine;
     if (ncta > 1) {
       if constexpr (kGrid) {
         team_barrier(xbar, ncta, abort, limit);
@@ -922,29 +952,31 @@ __device__ __forceinline__ void team_job(const FwdJob& J, const FwdParams& P, co
           if (threadIdx.x == 0) atomicExch(J.status, kStTimeout);
           return false;
         }
+        bad = threadIdx.x == 0 && __ldcg(xbar + 4) != 0u;
       } else {
         cluster_sync();
+        bad = *reinterpret_cast<volatile uint32_t*>(&head->team_bad) != 0u;
       }
     }
-    // One decision for the whole CTA (another CTA of the team may mark the
-    // request timed out while this one reads the status).
-    return __syncthreads_or(*reinterpret_cast<const volatile int32_t*>(J.status) == kStTimeout) == 0;
+    return __syncthreads_or(bad) == 0;
   };
   if (!team_sync_ok()) return;
 
   // ---- tail 1 (warp 0 of CTA 0): final state, total, hops back through the anchor rows ----
   const bool chase = (J.flags & kJobChase) != 0;
+  int32_t final_code = kStPending;  // set by the thread that chooses the final state
   unsigned char* tail = smem + P.off_ring;  // links and stages are free now (hop buffer)
   if (crank == 0 && warp == 0) {
     int s_cur;
     if (J.flags & kJobWriteFinal) {
-      const float f_blank = __ldcg(J.final2 + 1);
-      const float f_lab = (S > 1) ? __ldcg(J.final2 + 0) : -INFINITY;
+      const float* fin = xteam ? reinterpret_cast<const float*>(xbar) + 2 : head->fin;
+      const float f_blank = xteam ? __ldcg(fin + 1) : fin[1];
+      const float f_lab = (S > 1) ? (xteam ? __ldcg(fin + 0) : fin[0]) : -INFINITY;
       s_cur = (S > 1 && f_lab > f_blank) ? S - 2 : S - 1;
       const float tot = (S > 1 && f_lab > f_blank) ? f_lab : f_blank;
+      final_code = (tot == -INFINITY) ? kStNoPath : kStOk;
       if (lane == 0) {
         if (J.total && !kNorm) *J.total = tot;  // logits: the score pass writes the total
-        atomicCAS(J.status, kStPending, tot == -INFINITY ? kStNoPath : kStOk);
         if (!chase) *J.state_io = s_cur;
       }
     } else {
@@ -979,7 +1011,15 @@ __device__ __forceinline__ void team_job(const FwdJob& J, const FwdParams& P, co
       if (lane == 0) *J.state_io = s_cur;
     }
   }
-  if (!chase) return;
+  // The request's result code, once its job is done (the last write of the
+  // job to its result block).
+  auto finish = [&]() {
+    if (crank == 0 && threadIdx.x == 0 && final_code != kStPending) atomicCAS(J.status, kStPending, final_code);
+  };
+  if (!chase) {
+    finish();
+    return;
+  }
   if (!team_sync_ok()) return;
 
   // ---- tail 2 (every lane of the team): walk the windows in parallel ----
@@ -1082,6 +1122,7 @@ __device__ __forceinline__ void team_job(const FwdJob& J, const FwdParams& P, co
       *J.total = tot;
     }
   }
+  finish();
 }
 
 // Stage barriers of the emission ring: `full` completes when a stage's rows
