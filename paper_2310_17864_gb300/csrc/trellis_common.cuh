@@ -126,6 +126,8 @@ struct SmemHead {
   int32_t abort;            // set by any thread of this CTA whose wait hit the limit
   uint32_t unused;
   uint64_t sink;            // scratch slot written by the last warp of the team
+  uint64_t tailbar;         // fast kernel: completion of the anchor-row copies of the backtrack
+  uint64_t pad2;
   float fin[2];             // fast kernel, CTA 0 of a cluster team: alpha_{T-1} of states S-2, S-1
   uint32_t team_bad;        // fast kernel, cluster teams: set in every CTA by a CTA whose wait ran out
   uint32_t pad;

@@ -241,6 +241,7 @@ struct StageRing {
   uint32_t p_round = 0;
   int c_stage = 0;
   uint32_t c_round = 0;
+  uint32_t t_round = 0;  // completed phases of the backtrack's copy barrier (warp 0)
 };
 
 // The whole hot path of one job for one CTA of its team: this CTA is rank
@@ -925,6 +926,7 @@ __device__ __forceinline__ void team_job(const FwdJob& J, const FwdParams& P, co
   }
 
   }  // compute warps
+  fence_proxy_async_smem();
   // Team barrier between the phases, and one decision for the whole team:
   // carry on unless a CTA's bounded wait ran out. A CTA whose wait ran out
   // marks the request timed out (the result block may be in host memory:
@@ -963,6 +965,9 @@ __device__ __forceinline__ void team_job(const FwdJob& J, const FwdParams& P, co
   if (!team_sync_ok()) return;
 
   // ---- tail 1 (warp 0 of CTA 0): final state, total, hops back through the anchor rows ----
+  // (The barrier before it also ordered every warp's shared-memory accesses
+  // to links and stages before the bulk copies that reuse them: each thread
+  // fenced them to the asynchronous proxy first.)
   const bool chase = (J.flags & kJobChase) != 0;
   int32_t final_code = kStPending;  // set by the thread that chooses the final state
   unsigned char* tail = smem + P.off_ring;  // links and stages are free now (hop buffer)
@@ -984,29 +989,45 @@ __device__ __forceinline__ void team_job(const FwdJob& J, const FwdParams& P, co
     }
     if (chase) {
       if (lane == 0) path[t_end - 1] = s_cur;
+      // Batches of kHopBatch rows: lane r copies the slice [lo, hi) of row
+      // m - r (16-byte aligned: rows are 16-byte multiples) with one bulk copy
+      // on the tail barrier, then lane 0 hops through them in shared memory;
+      // a hop that leaves the slice (below lo) reads its byte from global
+      // memory in a loop of its own.
       uint8_t* zb = tail;  // [kHopBatch][kHopRowBytes]
+      uint64_t* tbar = &head->tailbar;
+      uint32_t& t_round = ring.t_round;
       for (int m = nwin - 1; m >= 0; m -= kHopBatch) {
         const int nb = min(kHopBatch, m + 1);
         const int lo = max(0, s_cur - kHopSpan) & ~15;
         const int hi = min(zstride, (s_cur + 16) & ~15);
-        const int nchunk = (hi - lo) / 16;
-        for (int c = lane; c < nchunk; c += 32) {  // lane c copies bytes [lo + 16c, lo + 16c + 16) of each row
-          for (int r = 0; r < nb; ++r)
-            cp_async16(zb + r * kHopRowBytes + c * 16, ztab + static_cast<size_t>(m - r) * zstride + lo + c * 16);
-        }
-        cp_async_wait_all();
+        const uint32_t bytes = static_cast<uint32_t>(hi - lo);
+        fence_proxy_async_smem();  // this warp's earlier reads of the buffer before the copies' writes
         __syncwarp();
+        if (lane == 0) mbar_arrive_expect_tx(tbar, bytes * static_cast<uint32_t>(nb));
+        __syncwarp();
+        if (lane < nb) bulk_g2s(zb + lane * kHopRowBytes, ztab + static_cast<size_t>(m - lane) * zstride + lo, bytes, tbar);
+        bool landed = true;
         if (lane == 0) {
-          for (int r = 0; r < nb; ++r) {
+          landed = wait_phase(tbar, t_round & 1u, abort, limit, false);
+          if (!landed) (void)wait_phase(tbar, t_round & 1u, abort, limit, false);  // copies still in flight land first
+        }
+        ++t_round;
+        if (lane == 0 && landed) {
+          int r = 0;
+          for (; r < nb; ++r) {
             const int off = s_cur - lo;
-            const int d = (off >= 0) ? static_cast<int>(zb[r * kHopRowBytes + off])
-                                     : static_cast<int>(__ldcg(ztab + static_cast<size_t>(m - r) * zstride + s_cur));
-            s_cur -= d;
+            if (off < 0) break;
+            s_cur -= static_cast<int>(zb[r * kHopRowBytes + off]);
+            path[t_begin + (m - r) * kAnchorD] = s_cur;
+          }
+          for (; r < nb; ++r) {
+            s_cur -= static_cast<int>(__ldcg(ztab + static_cast<size_t>(m - r) * zstride + s_cur));
             path[t_begin + (m - r) * kAnchorD] = s_cur;
           }
         }
         s_cur = __shfl_sync(kFull, s_cur, 0);
-        __syncwarp();
+        if (__shfl_sync(kFull, landed ? 1 : 0, 0) == 0) break;  // the abort flag is raised
       }
       if (lane == 0) *J.state_io = s_cur;
     }
@@ -1048,6 +1069,27 @@ __device__ __forceinline__ void team_job(const FwdJob& J, const FwdParams& P, co
     };
     int sc = path[e];
     int cur = sc / K;  // lane (over the team) whose words are in wv; wn: the lane below
+    {
+      // The walk stays in the lanes between its bottom state (path[b], from
+      // tail 1) and its top state; word q of 32 consecutive lanes is one
+      // 128-byte line, so the lines of up to two warps of lanes are pulled
+      // into L1 with independent loads and one wait. (Otherwise a lane
+      // switching to new words waits an L2 round trip, and the warp's
+      // scoreboard makes every lane wait for every other lane's loads.)
+      const int hi_g = cur >> 5, lo_g = min((max(path[b], 0) / K) >> 5, hi_g);
+      const uint32_t* l0 = wbase + static_cast<size_t>(lo_g) * NW * 32;
+      const uint32_t* l1 = wbase + static_cast<size_t>(min(lo_g + 1, hi_g)) * NW * 32;
+      uint32_t v[2 * kWords];
+#pragma unroll
+      for (int q = 0; q < kWords; ++q) {
+        v[q] = __ldca(l0 + q * 32);
+        v[kWords + q] = __ldca(l1 + q * 32);
+      }
+      uint32_t acc = 0u;
+#pragma unroll
+      for (int q = 0; q < 2 * kWords; ++q) acc ^= v[q];
+      asm volatile("" ::"r"(acc));
+    }
     uint32_t wv[kWords], wn[kWords];
     lane_words(cur, wv);
     lane_words(cur - 1, wn);
@@ -1135,6 +1177,7 @@ __device__ __forceinline__ void init_stage_barriers(const FwdParams& P, bool bul
       mbar_init(&head->full[st], bulk ? 1u : 32u);
       mbar_init(&head->empty[st], static_cast<uint32_t>((blockDim.x >> 5) - 1));
     }
+    mbar_init(&head->tailbar, 1u);
     fence_barrier_init();
   }
   __syncthreads();
