@@ -728,8 +728,14 @@ __device__ __forceinline__ void team_job(const FwdJob& J, const FwdParams& P, co
       } else {
         const float* rowp = stage_f + c_stage * stage_floats;
         const uint32_t rslot_addr = r_data + static_cast<uint32_t>((m & (R - 1)) * kWin * 8);
-#pragma unroll 1
-        for (int i = 0; i < rem; ++i) do_frame(m, i, rowp, rslot_addr);
+        // The same straight-line frames as a full window, each behind a
+        // warp-uniform guard: a loop over a runtime frame index runs about
+        // three times slower per frame, and every warp of the pipeline waits
+        // for its sender to finish this window, so a slow last window costs
+        // its time once per warp boundary.
+#pragma unroll
+        for (int i = 0; i < kWin - 1; ++i)
+          if (i < rem) do_frame(m, i, rowp, rslot_addr);
         window_end_recv(m);
         end_window(m, t_end - 1);
       }
