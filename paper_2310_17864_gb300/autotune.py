@@ -12,7 +12,10 @@ the fastest. Two criteria:
 The two tables are installed with ``align_set_tuning_bucket_for`` (the
 library plans a batch with the throughput table when it oversubscribes the
 GPU, else with the latency table) and saved as JSON with the GPU name, one
-key per mode, for later runs. Usage:
+key per mode, for later runs. A bucket keeps the shape of the table it
+started from (``prior``) unless another shape is faster by more than
+``margin``: shapes within the run-to-run spread of each other are a tie, and
+a tie does not move the table. Usage:
 
     python -m paper_2310_17864_gb300.autotune --mode both --out tuning.json
 """
@@ -52,10 +55,23 @@ def _device_ms(torch, al, st, items, reps: int) -> tuple[float, list]:
     return statistics.median(times), res
 
 
+def choose(times: dict, prior=None, margin: float = 0.0):
+    """The shape of one bucket from its measured times {(K, cta_warps): ms}:
+    the fastest, unless ``prior`` was measured within ``margin`` (a fraction)
+    of it, which then stays."""
+    best = min(times, key=lambda k: (times[k], k))
+    if prior is not None and prior in times and times[prior] <= times[best] * (1.0 + margin):
+        return prior
+    return best
+
+
 def tune(device: int = 0, mode: str = "latency", buckets=BUCKETS, C: int = 32, reps: int = 3,
-         verbose: bool = False) -> dict:
-    """Measure every candidate per bucket; returns {"table": [(s_max, K, cta_warps)], "trials": {...}}."""
+         verbose: bool = False, prior=None, margin: float = 0.0) -> dict:
+    """Measure every candidate per bucket; returns {"table": [(s_max, K, cta_warps)], "trials": {...}}.
+    ``prior``: a table [(s_max, K, cta_warps)] whose shape a bucket keeps on a tie (see ``choose``)."""
     import torch
+
+    prior_of = {int(s): (int(k), int(w)) for s, k, w in (prior or [])}
 
     table, trials = [], {}
     for bi, s_hi in enumerate(buckets):
@@ -65,7 +81,7 @@ def tune(device: int = 0, mode: str = "latency", buckets=BUCKETS, C: int = 32, r
         specs = [synth.Spec(T, C, L, 0.0, synth.sub_seed(synth.BASE_SEED + 90 + bi, i)) for i in range(n)]
         b = synth.make_batch(specs, device=f"cuda:{device}")
         ref_paths = None
-        best = None
+        times = {}
         for K in KS:
             for cw in CTA_WARPS:
                 try:
@@ -95,9 +111,9 @@ def tune(device: int = 0, mode: str = "latency", buckets=BUCKETS, C: int = 32, r
                 trials[f"S{s_hi}_K{K}_cw{cw}"] = ms
                 if verbose:
                     print(f"S<={s_hi:6d} K={K:2d} cta_warps={cw:2d}: {ms:8.3f} ms", flush=True)
-                if best is None or ms < best[0]:
-                    best = (ms, K, cw)
-        table.append((s_hi, best[1], best[2]))
+                times[(K, cw)] = ms
+        K, cw = choose(times, prior_of.get(s_hi), margin)
+        table.append((s_hi, K, cw))
     return {"mode": mode, "table": table, "trials": trials}
 
 
@@ -143,9 +159,14 @@ def main():
     ap.add_argument("--mode", choices=["latency", "throughput", "both"], default="both")
     ap.add_argument("--out", default=DEFAULT_TABLE)
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--prior", default=DEFAULT_TABLE,
+                    help="table whose shapes a bucket keeps on a tie ('' for none)")
+    ap.add_argument("--margin", type=float, default=0.03,
+                    help="a new shape must be faster than the prior one by this fraction")
     args = ap.parse_args()
     for mode in (("latency", "throughput") if args.mode == "both" else (args.mode,)):
-        res = tune(args.device, mode, reps=args.reps, verbose=True)
+        prior = load(args.prior, mode) if args.prior else None
+        res = tune(args.device, mode, reps=args.reps, verbose=True, prior=prior, margin=args.margin)
         save(res, args.out, args.device)
         print(mode, json.dumps(res["table"]))
 

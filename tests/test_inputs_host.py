@@ -75,3 +75,16 @@ def test_tuning_table_file_round_trip(tmp_path):
     shipped = autotune.load(autotune.DEFAULT_TABLE, "latency")
     assert shipped and all(len(r) == 3 and r[1] in (2, 4, 8, 16) for r in shipped)
     assert [r[0] for r in shipped] == sorted(r[0] for r in shipped)
+
+
+def test_autotune_choice_keeps_the_prior_shape_on_a_tie():
+    """A bucket keeps its prior shape unless another is faster by more than the margin."""
+    from paper_2310_17864_gb300 import autotune
+
+    times = {(4, 2): 0.2638, (4, 4): 0.2659, (2, 4): 0.3171}
+    assert autotune.choose(times) == (4, 2)
+    assert autotune.choose(times, prior=(4, 4), margin=0.03) == (4, 4)
+    assert autotune.choose(times, prior=(4, 4), margin=0.0) == (4, 2)
+    assert autotune.choose(times, prior=(2, 4), margin=0.03) == (4, 2)   # 20 % slower: replaced
+    assert autotune.choose(times, prior=(8, 1), margin=0.03) == (4, 2)   # prior not measured
+    assert autotune.choose({(4, 4): 1.0, (2, 2): 1.0}) == (2, 2)        # exact tie: smaller shape
