@@ -7,8 +7,9 @@ Headline workload (batch64): 64 utterances, T uniform in 500..3000 frames
 One step = the whole hot path (validate, expand, forward max-plus recursion,
 2-bit backpointers and anchor rows, final state, backtrack, scores) for the
 whole batch. Legs measured the same way, each with its own roofline, in
-"legs": longform (one utterance, T=180000, L=45000), ragged32 / ragged500
-(4096 utterances, lognormal lengths, C=32 / C=500). --workload picks the
+"legs": plain1 (one utterance, T=200, L=40), longform (one utterance,
+T=180000, L=45000, also checkpointed), ragged32 / ragged500 (4096 utterances,
+lognormal lengths, C=32 / C=500), and persistent launches of two of them. --workload picks the
 headline workload instead (plain1, batch64, longform, ragged32, ragged500).
 
 Metric: trellis cells per second, cells = sum over utterances of T * (2L+1).
@@ -772,7 +773,8 @@ def main():
     if not args.no_legs:
         legs = {}
         # (leg, workload, forced checkpointed recompute, persistent launch)
-        for name, wname, ck, ps in (("longform", "longform", False, False),
+        for name, wname, ck, ps in (("plain1", "plain1", False, False),
+                                    ("longform", "longform", False, False),
                                     ("longform_checkpointed", "longform", True, False),
                                     ("ragged32", "ragged32", False, False),
                                     ("ragged32_persistent", "ragged32", False, True),
