@@ -15,8 +15,9 @@
 // ring written over distributed shared memory. Warps therefore run as a
 // skewed pipeline: no barrier per frame.
 //
-// Backpointer layout (2 bits of information per cell, packed by warp ballots):
-// for warp g and stored frame row r, NW = 3K/2 32-bit words
+// Backpointer layout of the generic kernel (2 bits of information per cell,
+// packed by warp ballots; the fast kernel's per-window layout is described in
+// trellis_fast.cu): for warp g and stored frame row r, NW = 3K/2 32-bit words
 //   word j      (0 <= j < K): bit l = "advance won" for state 32Kg + Kl + j
 //   word K + i  (0 <= i < K/2): bit l = "skip won" for the label state
 //                               32Kg + Kl + 2i + 1
@@ -60,7 +61,8 @@ struct alignas(16) FwdJob {
   uint32_t* bp;            // packed backpointers (nullptr: none stored)
   float* ckpt;             // alpha rows at frames 0, ck_every, 2*ck_every, ... (nullptr: none)
   const float* alpha_in;   // alpha at t_begin (S floats); nullptr: the t = 0 initialisation
-  float* final2;           // [2] alpha_{T-1}(S-2), alpha_{T-1}(S-1)
+  float* final2;           // [2] alpha_{T-1}(S-2), alpha_{T-1}(S-1) (generic kernel; the fast
+                           // kernel keeps them in shared memory or the team block)
   int32_t* status;         // request status word (see align.h codes)
   int32_t* state_io;       // chase entry state (in) / state at t_begin (out)
   int32_t* path;           // [T] outputs (nullptr when not chasing)

@@ -8,18 +8,21 @@
 //
 //   * a window of 32 frames is one straight-line block of code (blocks of kB
 //     frames, every frame index a compile-time constant);
+//   * one comparison per (blank, label) pair of states decides the blank
+//     state's advance and the label state's best move other than staying;
 //   * backpointers: each lane collects, per state, one bit per frame of the
-//     window ("advance won", and for label states "skip won") in a register
-//     and stores its words once per window (coalesced, 128 bytes per word and
-//     warp), instead of per-frame warp ballots;
-//   * neighbour hand-off: the last lane of a warp keeps the values of its last
-//     state for a block of kB frames in registers and writes them once per
-//     block to the next warp's link (shared memory, the next CTA's shared
-//     memory over DSMEM, or global memory for grid teams), behind a release
-//     store of a package counter; the receiver acquires the counter once per
-//     block and its lane 0 reads the package; a consumption counter written
-//     back bounds the sender's lead (flow control, one check per block);
-//   * emissions of a block are loaded from the staged rows at its start.
+//     window ("advance won" for a blank state, "stay lost" for a label
+//     state) in a register and stores its words once per window (coalesced,
+//     128 bytes per word and warp), instead of per-frame warp ballots;
+//   * neighbour hand-off: the last lane of a warp writes, for each frame, a
+//     64-bit word (alpha of its last state, frame tag, anchor offset) into
+//     the next warp's link (shared memory, the next CTA's shared memory over
+//     DSMEM, or global memory for grid teams), two words per store; the
+//     receiver checks the tags of a whole block once and lane 0 reads one
+//     word per frame; a consumption counter written back bounds the sender's
+//     lead (flow control, one check per block);
+//   * emission rows are staged by a producer warp with bulk copies; rows of
+//     32 classes sit at compile-time offsets (kC).
 //
 // Arithmetic is the definition's (strict '>' in the order stay, advance,
 // skip; one FP32 add after an exact max), so results are bit-identical to the
