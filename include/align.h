@@ -354,9 +354,9 @@ int align_token_spans(const int32_t *states, const float *scores, const int64_t 
    looks up the array's address and, under CUDA's lazy module loading, is where
    the library's device code and the array are loaded onto the device (which
    allocates and may synchronise): make it outside the allocation-sensitive
-   path and before any stream capture on that device. The call itself can
-   never be captured (it copies from host memory and synchronises): on a
-   stream being captured it returns ALIGN_E_INVAL and does nothing. Every
+   path and before any stream capture on that device. The call copies from
+   host memory and synchronises its stream, so on a stream that is being
+   captured it returns ALIGN_E_INVAL and does nothing. Every
    call shares the array and keeps the previous call's contents: calls that
    overlap on the GPU race, so never issue two at once. The call synchronises
    `cuda_stream` before it returns and writes the request's result code

@@ -119,7 +119,7 @@ extern "C" int align_forced_noalloc(const float* log_probs, int64_t T, int64_t C
     if (cudaStreamIsCapturing(static_cast<cudaStream_t>(cuda_stream), &cs) != cudaSuccess) {
       (void)cudaGetLastError();
     } else if (cs != cudaStreamCaptureStatusNone) {
-      return fail(ALIGN_E_INVAL, "align_forced_noalloc: the stream is being captured (the call cannot be captured)");
+      return fail(ALIGN_E_INVAL, "align_forced_noalloc: the stream is being captured");
     }
   }
   int64_t R = 0;

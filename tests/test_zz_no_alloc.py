@@ -86,9 +86,9 @@ def test_noalloc_rejects_requests_beyond_its_scratch():
 
 
 def test_noalloc_refuses_a_capturing_stream():
-    """The call copies from host memory and synchronises its stream, so it can
-    never be captured: on a stream under capture it returns ALIGN_E_INVAL with
-    a message and records nothing."""
+    """The call copies from host memory and synchronises its stream, so on a
+    stream under capture it returns ALIGN_E_INVAL with a message and records
+    nothing."""
     build.build()
     u = synth.make_utterance(7, 100, 32, 20)
     path, scores, total, states = _outs(u.T)
